@@ -1,0 +1,139 @@
+"""Textbook Krylov solvers for G W = S (Section 3.2, hybrid method step 2).
+
+The paper solves the SPD system of transient Stokes by "a simple
+preconditioned conjugate gradient" and the nonsymmetric systems of the
+Newton steps by GMRES (Section 4.3).  These are the standard algorithms
+(Saad, Iterative Methods for Sparse Linear Systems: Algorithm 9.1,
+preconditioned CG; Algorithm 9.5, right-preconditioned restarted GMRES with
+Givens rotations), written plainly; the preconditioner is Jacobi (the
+inverse of the diagonal of G).  ``refine`` is classical mixed-precision
+iterative refinement: inner solves in float32, residual and update in float64.
+"""
+
+import numpy as np
+
+
+def jacobi(G):
+    """Inverse of the diagonal of G."""
+    return 1.0 / G.diagonal()
+
+
+def pcg(G, b, minv, x0=None, rtol=1e-10, maxit=100000):
+    """Jacobi-preconditioned CG; stops when ||r||_2 <= rtol ||b||_2 (recursive r)."""
+    dt = b.dtype
+    x = np.zeros_like(b) if x0 is None else x0.astype(dt).copy()
+    r = b - G @ x
+    bn = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / bn if bn > 0 else 0.0]
+    if bn == 0.0:
+        return x, 0, hist
+    z = minv * r
+    p = z.copy()
+    rz = np.dot(r, z)
+    it = 0
+    while it < maxit:
+        q = G @ p
+        alpha = rz / np.dot(p, q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        rn = np.linalg.norm(r) / bn
+        hist.append(rn)
+        if rn <= rtol:
+            break
+        z = minv * r
+        rz_new = np.dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, hist
+
+
+def gmres(G, b, minv, x0=None, restart=30, rtol=1e-10, maxit=100000):
+    """Right-Jacobi-preconditioned restarted GMRES(m) with modified Gram-Schmidt."""
+    dt = b.dtype
+    n = b.shape[0]
+    x = np.zeros_like(b) if x0 is None else x0.astype(dt).copy()
+    bn = np.linalg.norm(b)
+    hist = []
+    if bn == 0.0:
+        return x, 0, [0.0]
+    it = 0
+    while it < maxit:
+        r = b - G @ x
+        beta = np.linalg.norm(r)
+        hist.append(beta / bn)
+        if beta / bn <= rtol:
+            break
+        V = np.zeros((restart + 1, n), dtype=dt)
+        H = np.zeros((restart + 1, restart), dtype=np.float64)
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(restart):
+            w = G @ (minv * V[j])
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            it += 1
+            hist.append(abs(g[j + 1]) / bn)
+            if abs(g[j + 1]) / bn <= rtol or it >= maxit:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - np.dot(H[i, i + 1:k], y[i + 1:k])) / H[i, i]
+        x = x + (minv * (V[:k].T @ y.astype(dt))).astype(dt)
+        if hist[-1] <= rtol:
+            r = b - G @ x
+            if np.linalg.norm(r) / bn <= rtol:
+                hist.append(np.linalg.norm(r) / bn)
+                break
+    return x, it, hist
+
+
+def refine(G, b, inner="pcg", rtol=1e-10, inner_rtol=1e-4, max_outer=60, restart=30,
+           inner_maxit=100000):
+    """float64 iterative refinement around a float32 inner Krylov solve.
+
+    x = 0; repeat: r = b - G x (float64); solve G d = r in float32 to a
+    relative residual inner_rtol; x += d (float64); until ||r|| <= rtol ||b||.
+    Returns (x, outer steps, total inner iterations, history of ||r||/||b||).
+    """
+    G32 = G.astype(np.float32)
+    minv32 = jacobi(G).astype(np.float32)
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    hist = []
+    inner_total = 0
+    outer = 0
+    while True:
+        r = b - G @ x
+        rn = np.linalg.norm(r) / bn if bn > 0 else 0.0
+        hist.append(rn)
+        if rn <= rtol or outer >= max_outer:
+            break
+        r32 = r.astype(np.float32)
+        if inner == "pcg":
+            dx, k, _ = pcg(G32, r32, minv32, rtol=inner_rtol, maxit=inner_maxit)
+        else:
+            dx, k, _ = gmres(G32, r32, minv32, restart=restart, rtol=inner_rtol, maxit=inner_maxit)
+        x += dx.astype(np.float64)
+        inner_total += k
+        outer += 1
+    return x, outer, inner_total, hist

@@ -1,0 +1,83 @@
+"""Pins for the oracle's Krylov solvers and iterative refinement.
+
+Each solver is checked against a library direct solve (scipy's sparse LU)
+on matrices of the kinds the method produces: the SPD hybridised matrix of
+transient Stokes and the nonsymmetric one of a Newton step.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import hybrid, krylov, pipeline
+
+
+def hybridised(dim, n, nu, mu, conv="none"):
+    if dim == 2:
+        coords, elems = synth.mesh2d_square(n, 0.2, 1)
+    else:
+        coords, elems = synth.mesh3d_kuhn(n)
+    modes = synth.fourier_modes(dim, 1)
+    fbar = synth.element_means(lambda x: synth.fourier_force(x, modes), coords, elems, order=3)
+    w = None
+    if conv != "none":
+        from oracle import topology
+        t = topology.build_faces(elems)
+        w = synth.stream_velocity(coords[t["face_vertices"]].mean(axis=1), seed=3)
+    topo, geom, A_K, D_K, R_K = pipeline.setup(coords, elems, nu, mu, fbar, conv, w)
+    h = hybrid.hybridise(topo, A_K, D_K, R_K, mu)
+    return h["G"], h["S"]
+
+
+def test_pcg_matches_direct():
+    G, S = hybridised(2, 12, 1.0, 1000.0)
+    ref = spla.spsolve(G.tocsc(), S)
+    x, it, hist = krylov.pcg(G, S, krylov.jacobi(G), rtol=1e-13)
+    assert hist[-1] <= 1e-13 and it > 0
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-10
+    # the recursive residual tracks the true residual
+    assert np.linalg.norm(S - G @ x) / np.linalg.norm(S) < 1e-12
+
+
+def test_pcg_zero_rhs_and_warm_start():
+    G, S = hybridised(2, 6, 1.0, 100.0)
+    x, it, _ = krylov.pcg(G, np.zeros_like(S), krylov.jacobi(G))
+    assert it == 0 and not np.any(x)
+    ref = spla.spsolve(G.tocsc(), S)
+    x, it, _ = krylov.pcg(G, S, krylov.jacobi(G), x0=ref, rtol=1e-10)
+    assert it <= 1
+
+
+@pytest.mark.parametrize("conv,mu,restart", [("newton", 100.0, 30), ("oseen", 100.0, 30),
+                                             ("newton", 0.0, 400), ("none", 0.0, 400)])
+def test_gmres_matches_direct(conv, mu, restart):
+    """Restarted GMRES on transient Newton/Oseen steps; full GMRES (restart >= N)
+    on the steady (mu = 0) systems, where Jacobi-preconditioned GMRES(30)
+    stagnates because the spectrum lies on both sides of zero."""
+    G, S = hybridised(2, 8, 0.01 if conv != "none" else 1.0, mu, conv)
+    assert restart == 30 or restart >= G.shape[0]
+    ref = spla.spsolve(G.tocsc(), S)
+    x, it, hist = krylov.gmres(G, S, krylov.jacobi(G), restart=restart, rtol=1e-12, maxit=5000)
+    assert np.linalg.norm(S - G @ x) / np.linalg.norm(S) <= 1e-11
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("inner", ["pcg", "gmres"])
+def test_refinement_reaches_fp64_accuracy(inner):
+    G, S = hybridised(2, 10, 1.0, 1000.0)
+    ref = spla.spsolve(G.tocsc(), S)
+    x, outer, tot, hist = krylov.refine(G, S, inner=inner, rtol=1e-13, inner_rtol=1e-4)
+    assert hist[-1] <= 1e-13 and outer >= 2
+    # error <= cond(G) * residual; cond(G) is a few thousand here
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-9
+
+
+def test_hybrid_pipeline_methods_agree():
+    coords, elems = synth.mesh2d_square(10, 0.2, 0)
+    modes = synth.fourier_modes(2, 1)
+    fbar = synth.element_means(lambda x: synth.fourier_force(x, modes), coords, elems, order=3)
+    a = pipeline.hybrid(coords, elems, 1.0, 1000.0, fbar, method="direct")
+    for m in ("pcg", "gmres", "ir-pcg"):
+        b = pipeline.hybrid(coords, elems, 1.0, 1000.0, fbar, method=m, rtol=1e-13)
+        assert np.linalg.norm(a["U"] - b["U"]) / np.linalg.norm(a["U"]) < 1e-10
