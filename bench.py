@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the hybridised Crouzeix-Raviart solve on one GB300 per rank.
+
+A step is one pass of the hot path over one synthetic problem: the coupled
+element blocks (cr_assemble_coupled), the element-wise condensation into
+G W = S (cr_hybridise), the Krylov solve to a relative residual of 1e-10
+(cr_solve) and the element-wise recovery of U and P (cr_recover_up).  The
+mesh topology (cr_mesh_load, host) is set up once and reported separately.
+
+Metric: time to solution (seconds per step, lower is better).  `value` is the
+FP64 Jacobi-PCG solve of the default workload (2D transient Stokes, 512x512
+squares split into 524,288 perturbed triangles, nu = 1, dt = 1e-3); the same
+steps in mixed precision (FP32 PCG inside FP64 iterative refinement) are
+reported beside it.  Each timed step is bracketed by CUDA events on the
+caller's stream; a 512 MB buffer is written between steps to flush L2.
+
+With --gpus N > 1 (torchrun), every rank solves its own replica of the
+workload (the path has no exchange step: replicas only); the time is the
+maximum over ranks.  `--impl reference` times the CPU FP64 oracle instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cfg1": "2D transient Stokes, 16x16 squares -> 512 triangles, nu=1, dt=1e-2, manufactured source",
+    "cfg2": "2D transient Stokes, 512x512 squares -> 524,288 triangles perturbed +-0.2h, nu=1, dt=1e-3, "
+            "8-mode Fourier source",
+    "cfg3": "3D transient Stokes, 64^3 cubes -> 1,572,864 Kuhn tetrahedra, nu=1, dt=1e-3, Fourier source",
+    "cfg5": "2D Navier-Stokes Newton step, 1024x1024 squares -> 2,097,152 triangles, Re=100, dt=1e-3, "
+            "linearised about a seeded stream-function field",
+}
+METRIC = "time-to-solution at relative residual 1e-10 (hybridise + solve + recover)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--sample-iters", type=int, default=30)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def load_problem(name):
+    """Mesh, coefficients, sources and (for Navier-Stokes) the linearisation field."""
+    import numpy as np
+    import synth
+    p = synth.config_problem(name)
+    if name == "cfg5":
+        p["mu"] = 1000.0   # transient Newton step (dt = 1e-3); see the design notes on mu = 0
+        p["conv"] = "newton"
+    return p, np
+
+
+def solve_opts(prec, tol, graph, profile):
+    if prec == "fp64":
+        return dict(method="pcg", prec="fp64", tol=tol, max_iter=200000, use_graph=graph, profile=profile)
+    return dict(method="pcg", prec="mixed", tol=tol, max_iter=400000, inner_tol=1e-4, use_graph=graph,
+                profile=profile)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (run in a child process with one BLAS thread)
+# ---------------------------------------------------------------------------
+def cpu_sample(name, iters):
+    """Time the oracle on the full mesh: set-up + hybridisation, `iters` PCG
+    iterations, recovery; scale the PCG time to the oracle's own iteration
+    count to a relative residual of 1e-10 (oracle/iteration_counts.json)."""
+    import numpy as np
+    import synth
+    from oracle import hybrid, krylov, pipeline
+    counts = json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))
+    full = counts[name]["pcg_iterations"]
+    p = synth.config_problem(name)
+    t0 = time.perf_counter()
+    topo, geom, A_K, D_K, R_K = pipeline.setup(p["coords"], p["elems"], p["nu"], p["mu"], p["fbar"][0], p["conv"])
+    h = hybrid.hybridise(topo, A_K, D_K, R_K, p["mu"])
+    t1 = time.perf_counter()
+    x, it, _ = krylov.pcg(h["G"], h["S"], krylov.jacobi(h["G"]), rtol=1e-30, maxit=iters)
+    t2 = time.perf_counter()
+    hybrid.recover(h, topo, x)
+    t3 = time.perf_counter()
+    per_it = (t2 - t1) / max(it, 1)
+    total = (t1 - t0) + per_it * full + (t3 - t2)
+    return {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"{name} full mesh: set-up + hybridise {t1 - t0:.2f} s, {it} Jacobi-PCG iterations "
+                      f"({per_it * 1e3:.1f} ms each) scaled to the oracle's {full} iterations to 1e-10, "
+                      f"recover {t3 - t2:.2f} s; numpy/scipy with 1 BLAS thread on a {os.cpu_count()}-core host",
+            "measured_s": t3 - t0}
+
+
+def run_cpu_sample_child(name, iters):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name, "--sample-iters", str(iters)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("CPU oracle sample failed: " + r.stderr[-2000:])
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def algorithmic_spmv_bytes(mesh_faces_elems, nf, d, vbytes, xbytes):
+    """Bytes one SpMV must move: nnz*v + blocks*4 (int32 column) + N*(x + y)."""
+    import numpy as np
+    fe = mesh_faces_elems
+    s = np.bincount(fe.ravel())
+    blocks = int((s.astype(np.int64) ** 2).sum() - nf)     # sum_K s_K (s_K - 1) + F_int
+    nnz = blocks * d * d
+    N = nf * d
+    return nnz * vbytes + blocks * 4 + N * 2 * xbytes, blocks, nnz
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2101_03777_gb300 import build, crhyb
+
+    build.build_library()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    p, _ = load_problem(args.workload)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    w_dev = None
+    tm0 = time.perf_counter()
+    mesh = crhyb.cr_mesh_load(p["coords"], p["elems"], need_mis=(p["mu"] == 0.0))
+    mesh_load_s = time.perf_counter() - tm0
+    if p["conv"] != "none":
+        import synth
+        xs = p["coords"][crhyb.cr_mesh_faces(mesh)].mean(axis=1)
+        w_dev = torch.from_numpy(synth.stream_velocity(xs, seed=3)).cuda()
+    d, nf, ne = mesh.dim, mesh.nf, mesh.ne
+    n = nf * d
+    fe, _ = crhyb.cr_mesh_face_elements(mesh)
+    fbar_host = torch.from_numpy(p["fbar"]).pin_memory()
+    fbar_dev = fbar_host.cuda()
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    U = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(ne, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(prec, fb, Wt, Ut, Pt, profile=False):
+        system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=w_dev)
+        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec != "fp64"), keep_bf16=False)
+        st = crhyb.cr_solve(hyb, Wt, **solve_opts(prec, args.tol, args.graph, profile))
+        crhyb.cr_recover_up(hyb, Wt, Ut, Pt, normalise_p=True)
+        return st
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(prec, profile):
+        for _ in range(args.warmup):
+            step(prec, fbar_dev, W, U, P)
+        torch.cuda.synchronize()
+        times, stats = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step(prec, fbar_dev, W, U, P, profile)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            stats.append(st)
+        return times, stats
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t64, s64 = timed("fp64", True)
+    if not args.no_mixed:
+        tmx, smx = timed("mixed", True)
+    clk = clocks.stop()
+
+    # end-to-end through the C-ABI with host buffers: pinned fbar in, U and P out to pinned host memory
+    Uh = torch.empty(n, dtype=torch.float64).pin_memory()
+    Ph = torch.empty(ne, dtype=torch.float64).pin_memory()
+    Wh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step("fp64", fbar_host, Wh, Uh, Ph)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+
+    def agg(v):
+        x = torch.tensor([v], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        return float(x.item())
+
+    tts64 = agg(statistics.mean(t64))
+    tts_e2e = agg(statistics.mean(e2e))
+    it64 = s64[-1]["iterations"]
+    bytes64, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, 8, 8)
+    spmv_ms = sum(s["spmv_ms"] for s in s64) / max(sum(s["spmv_launches"] for s in s64), 1)
+    achieved = bytes64 / (spmv_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": tts64, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tts64 * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generators in synth/)",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nf_int": nf, "unknowns": n,
+                   "elements": ne, "solver": "Jacobi-PCG FP64", "tol": args.tol, "iterations": it64,
+                   "relres": s64[-1]["relres"], "mesh_load_s": mesh_load_s, "l2": "512 MB flush between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "graph": bool(args.graph)},
+        "roofline": {"kernel": "k_pcg_spmv<FP64> (block-ELL SpMV + p.q)", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "bytes_per_launch": bytes64, "avg_launch_ms": spmv_ms, "peak_note": peak_note,
+                     "launches_timed": sum(s["spmv_launches"] for s in s64)},
+        "e2e": {"value": tts_e2e, "unit": "s", "h2d_bytes_per_step": int(p["fbar"].nbytes),
+                "d2h_bytes_per_step": int(8 * (n + ne))},
+        "gpu_launches": int(sum(3 * s["iterations"] + 8 for s in s64) / len(s64)),
+        "clocks": clk,
+    }
+    if not args.no_mixed:
+        ttsmx = agg(statistics.mean(tmx))
+        bytes32, _, _ = algorithmic_spmv_bytes(fe, nf, d, 4, 4)
+        ms32 = sum(s["spmv_ms"] for s in smx) / max(sum(s["spmv_launches"] for s in smx), 1)
+        out["mixed"] = {"value": ttsmx, "unit": "s", "speedup_vs_fp64": tts64 / ttsmx,
+                        "iterations": smx[-1]["iterations"], "outer": smx[-1]["outer"],
+                        "relres": smx[-1]["relres"],
+                        "roofline": {"kernel": "k_pcg_spmv<FP32>", "achieved": bytes32 / (ms32 * 1e-3) / 1e9,
+                                     "peak": hbm_peak, "frac": bytes32 / (ms32 * 1e-3) / 1e9 / hbm_peak,
+                                     "bytes_per_launch": bytes32, "avg_launch_ms": ms32}}
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    vals = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        info = run_cpu_sample_child(args.workload, args.sample_iters)
+        if k >= args.warmup:
+            vals.append(info["value"])
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators in synth/)",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "solver": "Jacobi-PCG FP64",
+                       "tol": args.tol},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample, args.sample_iters)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                out["cpu_baseline"] = run_cpu_sample_child(args.workload, args.sample_iters)
+            except Exception as e:  # reported, not fatal
+                out["cpu_baseline"] = {"error": str(e)[:300]}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

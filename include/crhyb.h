@@ -1,0 +1,218 @@
+/*
+ * crhyb.h - C interface of the GB300 library for the exact pressure
+ * elimination (algebraic hybridisation) of the Crouzeix-Raviart P1
+ * nonconforming / P0 discretisation of the Stokes and Navier-Stokes problems
+ * (Chenier & Eymard, "Exact pressure elimination for the Crouzeix-Raviart
+ * scheme applied to the Stokes and Navier-Stokes problems", arXiv 2101.03777).
+ *
+ * The library computes, on one GPU:
+ *   1. the element blocks S_K, A_K, D_K, R_K of the coupled system
+ *      [A D^t; D 0][U; P] = [R; 0]                       (Section 3.1, Eq. 10)
+ *   2. the hybridised face system G W = S, element by element
+ *      (Section 3.2, items 4 and 5):
+ *        B_K = D_K^t Â_K^{-1} D_K,
+ *        G_K = C_K (Â_K^{-1} - Â_K^{-1} D_K D_K^t Â_K^{-1} / B_K) C_K, K != K_0,
+ *        G_{K_0} = C_{K_0} Â_{K_0}^{-1} C_{K_0},
+ *        G = sum_K H_K G_K H_K^t,  S = sum_K H_K C_K M_K R_K;
+ *   3. the Krylov solve of G W = S (Jacobi-PCG when G is symmetric positive
+ *      definite, Section 3.2 item 6; restarted GMRES otherwise, Section 4.3),
+ *      in FP64 or in FP32 inside FP64 iterative refinement;
+ *   4. the element-local recovery of P and U (Section 3.2, items 2 and 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns CR_OK (0) or a negative CR_ERR_* code; the text of
+ *   the last error of the calling thread is returned by cr_last_error().  No
+ *   C++ exception crosses this interface.
+ * - Handles (cr_mesh, cr_system, cr_hybrid) are owned by the library and
+ *   released by the matching cr_destroy_* call; destroying a handle that
+ *   others were created from is the caller's error (destroy in reverse order).
+ * - Array arguments are owned by the caller.  Unless stated otherwise an array
+ *   argument may be a device pointer or a host pointer: the library asks the
+ *   CUDA driver which one it is and copies host data through its own staging
+ *   buffers (the copies are part of the call and are stream ordered).
+ * - All device work is ordered on the CUDA stream given to cr_mesh_load (NULL
+ *   = the legacy default stream).  Calls that return results to the host
+ *   (statistics, host output arrays) synchronise that stream before returning.
+ * - Faces: only interior faces carry unknowns (homogeneous Dirichlet, Section
+ *   2).  They are numbered in the lexicographic order of their sorted vertex
+ *   tuples; cr_mesh_faces reports that order.  Velocity-like arrays U, W, S are
+ *   laid out [nrhs][nf_int][d] (face major, component fastest), pressures
+ *   [nrhs][ne], element sources fbar [nrhs][ne][d].
+ * - Local face l of a simplex is the face opposite its local vertex l.
+ */
+#ifndef CRHYB_H
+#define CRHYB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define CR_OK                  0
+#define CR_ERR_ARG            -1  /* invalid argument (NULL handle, bad size, bad option) */
+#define CR_ERR_MESH           -2  /* invalid mesh: index out of range, face in > 2 simplices, flat simplex */
+#define CR_ERR_SINGULAR       -3  /* an element matrix Â_K or B_K is singular (Section 3.2, item 3) */
+#define CR_ERR_NOT_CONVERGED  -4  /* the solve hit its iteration limit before the tolerance */
+#define CR_ERR_BREAKDOWN      -5  /* Krylov breakdown: p.Gp <= 0 in PCG, NaN, zero Arnoldi norm */
+#define CR_ERR_TIMEOUT        -6  /* a bounded device wait gave up */
+#define CR_ERR_CUDA           -7  /* a CUDA runtime call failed (text in cr_last_error) */
+#define CR_ERR_OOM            -8  /* device allocation failed */
+
+/* ---- opaque handles ----------------------------------------------------- */
+typedef struct cr_mesh cr_mesh;
+typedef struct cr_system cr_system;
+typedef struct cr_hybrid cr_hybrid;
+
+/* ---- options and parameters --------------------------------------------- */
+typedef struct cr_mesh_opts {
+    int32_t k0;        /* index of the simplex K_0 whose pressure is fixed to 0 (Section 2, item 5); default 0 */
+    int32_t need_mis;  /* 1: build the maximal independent set M_1 used for E_K when mu = 0 (Section 3.2, item 7) */
+} cr_mesh_opts;
+
+enum cr_conv { CR_CONV_NONE = 0, CR_CONV_NEWTON = 1, CR_CONV_OSEEN = 2 };
+
+typedef struct cr_params {
+    double nu;         /* viscosity, the inverse of the Reynolds number (Eq. 1) */
+    double mu;         /* 1/dt for a transient step, 0 for a steady problem (Eq. 1) */
+    int32_t conv;      /* enum cr_conv: b_h = 0 (Stokes), Newton or Oseen linearisation of Eq. 9 */
+    double lambda_scale; /* mu = 0 only: lambda_K = lambda_scale * ||A_K||_inf on M_1 (Section 3.2, item 7); <= 0 selects 2 */
+} cr_params;
+
+enum cr_prec { CR_PREC_FP64 = 0, CR_PREC_MIXED_FP32 = 1, CR_PREC_MIXED_BF16 = 2 };
+enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1 };
+
+typedef struct cr_hyb_opts {
+    int32_t keep_fp32;  /* also keep FP32 values of G (needed by CR_PREC_MIXED_FP32) */
+    int32_t keep_bf16;  /* also keep BF16 values of G (needed by CR_PREC_MIXED_BF16) */
+} cr_hyb_opts;
+
+typedef struct cr_solve_opts {
+    int32_t method;     /* enum cr_method */
+    int32_t prec;       /* enum cr_prec */
+    double tol;         /* stop when ||S - G W||_2 <= tol ||S||_2 (FP64 residual for the mixed paths,
+                           the recursively updated residual for plain FP64 PCG/GMRES) */
+    int32_t max_iter;   /* limit on Krylov iterations (inner iterations summed for the mixed paths) */
+    int32_t restart;    /* GMRES restart length m (1..CR_MAX_RESTART) */
+    double inner_tol;   /* mixed paths: relative residual of each inner FP32 solve (e.g. 1e-4) */
+    int32_t max_outer;  /* mixed paths: limit on refinement steps */
+    int32_t use_x0;     /* 1: W holds the initial guess on entry; 0: start from W = 0 */
+    int32_t check_every;/* iterations between host convergence checks (0 selects 16) */
+    int32_t use_graph;  /* 1: replay the iteration chunk as a captured CUDA graph */
+    int32_t profile;    /* 1: time every SpMV launch of the iteration with CUDA events (no graph) */
+} cr_solve_opts;
+
+#define CR_MAX_RESTART 64
+
+typedef struct cr_solve_stats {
+    int32_t iterations;  /* Krylov iterations (inner iterations summed for the mixed paths) */
+    int32_t outer;       /* refinement steps (0 for plain FP64) */
+    double relres;       /* final ||S - G W||_2 / ||S||_2 computed in FP64 from the returned W */
+    int32_t status;      /* CR_OK or the error code the solve returned */
+    int32_t spmv_launches; /* profile = 1: SpMV launches timed */
+    double spmv_ms;      /* profile = 1: their summed device time (ms) */
+} cr_solve_stats;
+
+/* ---- mesh --------------------------------------------------------------- */
+
+/* Build the mesh topology (Section 2, item 1): faces from sorted vertex tuples,
+ * interior/exterior faces, for each interior face its two simplices (owner =
+ * lower simplex index, C = +1; the other C = -1; Section 3.2, Eq. 12), K_0,
+ * the block ELL structure of G (stencil of A, Section 3.2 item 5) and, if
+ * asked, the maximal independent set M_1 (greedy in increasing simplex index).
+ *   dim     2 (triangles) or 3 (tetrahedra)
+ *   coords  host, float64 [nv][dim]
+ *   elems   host, int32 [ne][dim+1], vertex indices in [0, nv)
+ *   opts    may be NULL (defaults)
+ *   stream  cudaStream_t on which all later work of this mesh is ordered
+ * Errors: CR_ERR_ARG, CR_ERR_MESH (index out of range, a face shared by more
+ * than two simplices, a simplex of zero measure), CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_mesh_load(int dim, const double* coords, int64_t nv, const int32_t* elems, int64_t ne,
+                 const cr_mesh_opts* opts, void* stream, cr_mesh** out);
+
+/* Sizes of a loaded mesh (any output pointer may be NULL). */
+int cr_mesh_info(const cr_mesh* m, int32_t* dim, int64_t* ne, int64_t* nf_int, int64_t* nf_ext);
+
+/* Sorted vertex tuples of the interior faces, int32 [nf_int][dim], in the
+ * face order used by every face array; host or device pointer. */
+int cr_mesh_faces(const cr_mesh* m, int32_t* face_vertices);
+
+/* Face-adjacency structure: per interior face its two simplices (owner first)
+ * and its local face index in each, int32 [nf_int][2] each; host or device. */
+int cr_mesh_face_elements(const cr_mesh* m, int32_t* face_elems, int32_t* face_local);
+
+/* M_1 flags (uint8 [ne], 1 = in M_1); CR_ERR_ARG if the mesh was loaded without need_mis. */
+int cr_mesh_mis(const cr_mesh* m, uint8_t* in_m1);
+
+void cr_destroy_mesh(cr_mesh* m);
+
+/* ---- coupled system ----------------------------------------------------- */
+
+/* Record the coefficients and sources of the coupled system (Section 3.1) and,
+ * if blocks_out is not NULL, export its element blocks.
+ *   fbar        float64 [nrhs][ne][dim]: element means of the source,
+ *               (1/|K|) int_K f, as used by R_K (Eq. 8); copied by the library
+ *   nrhs        >= 1 right-hand sides sharing the matrix
+ *   w           float64 [nf_int][dim] face velocities about which the convection
+ *               term is linearised (conv != NONE), else NULL; copied
+ *   blocks_out  NULL or float64 [ne][L*L + L + nrhs*L], L = (dim+1)*dim, per
+ *               simplex: A_K (row major), D_K, then R_K per right-hand side,
+ *               local unknown (l, i) at l*dim + i, zero rows/columns on exterior
+ *               faces; with conv = NEWTON, R_K includes the Newton term c_K(w)
+ * Errors: CR_ERR_ARG, CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double* fbar, int nrhs,
+                        const double* w, cr_system** out, double* blocks_out);
+
+void cr_destroy_system(cr_system* s);
+
+/* ---- hybridisation ------------------------------------------------------ */
+
+/* Compute G (block ELL, FP64 plus the FP32/BF16 copies asked for), S for every
+ * right-hand side and the Jacobi preconditioner 1/diag(G) (Section 3.2, items
+ * 4, 5, 7).  Atomic free: every off-diagonal block of G belongs to one simplex;
+ * the two contributions to a diagonal block and to S are summed per face.
+ * Errors: CR_ERR_SINGULAR (an Â_K or B_K with a vanishing pivot; the
+ * handle is not created), CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out);
+
+/* Export G as block ELL: cols int32 [nslot][nf_int] (slot 0 is the diagonal),
+ * vals float64 [nslot][dim][dim][nf_int], nslot = 2*dim + 1; padding slots have
+ * col = row and zero values.  S float64 [nrhs][nf_int][dim].  Any pointer may
+ * be NULL; host or device pointers. */
+int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S);
+
+/* Solve G W = S for right-hand side `rhs` (0 <= rhs < nrhs).
+ *   W   float64 [nf_int][dim]: initial guess on entry if opts->use_x0, solution
+ *       on exit.  Host or device pointer.
+ *   st  host, may be NULL.
+ * Returns CR_OK, CR_ERR_NOT_CONVERGED (W holds the last iterate),
+ * CR_ERR_BREAKDOWN, CR_ERR_ARG (e.g. a precision whose values were not kept),
+ * CR_ERR_CUDA. */
+int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st);
+
+/* y = G x in FP64 (x, y float64 [nf_int][dim], device pointers). */
+int cr_apply_G(cr_hybrid* h, const double* x, double* y);
+
+/* Recover P and U from W for right-hand side `rhs` (Section 3.2, items 2, 4):
+ * y_K = R_K - C_K W_K, P_K = D_K^t Â_K^{-1} y_K / B_K (K != K_0), P_{K_0} = 0,
+ * Û_K = Â_K^{-1}(y_K - D_K P_K), U_sigma = Û_{K,sigma} from the owner K.
+ *   W  float64 [nf_int][dim]; U float64 [nf_int][dim]; P float64 [ne]
+ *   normalise_p  1: return P - (1/|Omega|) int P (zero mean, Section 2 item 5)
+ *   jump  NULL, or host double receiving max |Û_K - Û_L| over interior faces
+ *         (Eq. 15 makes it vanish for the exact W)
+ * Host or device pointers. */
+int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise_p,
+                  double* jump);
+
+void cr_destroy_hybrid(cr_hybrid* h);
+
+/* ---- errors ------------------------------------------------------------- */
+const char* cr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRHYB_H */

@@ -1,0 +1,363 @@
+// C interface of the crhyb library: handles, argument checks, host/device
+// staging, stream ordering and error reporting.  The numerical work is in
+// hybridise.cu (element kernels) and solve.cu (Krylov kernels).
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace crhyb {
+
+size_t kscal_bytes();
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    const int code = (e == cudaErrorMemoryAllocation) ? CR_ERR_OOM : CR_ERR_CUDA;
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return code;
+}
+
+bool is_device_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int DevArena::alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    ptrs.push_back(*p);
+    return CR_OK;
+}
+
+void DevArena::release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+}
+
+int ensure_stage(cr_hybrid* h, size_t bytes) {
+    if (h->stage_bytes >= bytes) return CR_OK;
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    CR_CUDA(cudaMalloc(&h->stage, bytes));
+    h->stage_bytes = bytes;
+    return CR_OK;
+}
+
+namespace {
+
+// Orders the library stream after the caller's stream on entry and the
+// caller's stream after the library stream on exit.
+struct StreamScope {
+    cr_mesh* m;
+    explicit StreamScope(cr_mesh* mm) : m(mm) {
+        cudaEventRecord(m->ev_in, m->user_stream);
+        cudaStreamWaitEvent(m->stream, m->ev_in, 0);
+    }
+    ~StreamScope() {
+        cudaEventRecord(m->ev_out, m->stream);
+        cudaStreamWaitEvent(m->user_stream, m->ev_out, 0);
+    }
+};
+
+// Copy n doubles from a host or device source into a device buffer.
+int copy_in(double* dst, const double* src, size_t n, cudaStream_t st) {
+    CR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, st));
+    return CR_OK;
+}
+
+int ensure_workspace(cr_hybrid* h, bool gmres, int restart, int prec) {
+    cr_mesh* m = h->m;
+    const size_t n = size_t(m->nf) * m->d;
+    if (!h->ws_ready) {
+        CR_TRY(h->arena.alloc_n(&h->x64, n));
+        CR_TRY(h->arena.alloc_n(&h->r64, n));
+        CR_TRY(h->arena.alloc_n(&h->p64, n));
+        CR_TRY(h->arena.alloc_n(&h->q64, n));
+        CR_TRY(h->arena.alloc_n(&h->x32, n));
+        CR_TRY(h->arena.alloc_n(&h->r32, n));
+        CR_TRY(h->arena.alloc_n(&h->p32, n));
+        CR_TRY(h->arena.alloc_n(&h->q32, n));
+        CR_TRY(h->arena.alloc(&h->scal, kscal_bytes()));
+        CR_CUDA(cudaMallocHost(&h->h_scal, kscal_bytes()));
+        h->ws_ready = true;
+    }
+    if (gmres && restart > h->ws_restart) {
+        if (h->V32) cudaFree(h->V32);
+        if (h->V64) cudaFree(h->V64);
+        if (h->Z32) cudaFree(h->Z32);
+        if (h->Z64) cudaFree(h->Z64);
+        h->V32 = nullptr;
+        h->V64 = nullptr;
+        h->Z32 = nullptr;
+        h->Z64 = nullptr;
+        h->ws_restart = 0;
+        CR_CUDA(cudaMalloc(&h->V32, sizeof(float) * n * (restart + 1)));
+        CR_CUDA(cudaMalloc(&h->Z32, sizeof(float) * n));
+        CR_CUDA(cudaMalloc(&h->Z64, sizeof(double) * n));
+        h->ws_restart = restart;
+    }
+    if (gmres && prec == CR_PREC_FP64 && !h->V64)
+        CR_CUDA(cudaMalloc(&h->V64, sizeof(double) * n * (h->ws_restart + 1)));
+    return CR_OK;
+}
+
+}  // namespace
+}  // namespace crhyb
+
+using namespace crhyb;
+
+extern "C" const char* cr_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+extern "C" int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double* fbar, int nrhs, const double* w,
+                                   cr_system** out, double* blocks_out) {
+    if (!out) return fail(CR_ERR_ARG, "cr_assemble_coupled: out is NULL");
+    *out = nullptr;
+    if (!m || !p || !fbar) return fail(CR_ERR_ARG, "cr_assemble_coupled: NULL argument");
+    if (nrhs < 1) return fail(CR_ERR_ARG, "cr_assemble_coupled: nrhs must be >= 1");
+    if (!(p->nu > 0.0) || !(p->mu >= 0.0)) return fail(CR_ERR_ARG, "cr_assemble_coupled: need nu > 0 and mu >= 0");
+    if (p->conv != CR_CONV_NONE && p->conv != CR_CONV_NEWTON && p->conv != CR_CONV_OSEEN)
+        return fail(CR_ERR_ARG, "cr_assemble_coupled: unknown convection option");
+    if (p->conv != CR_CONV_NONE && (m->d != 2 || !w))
+        return fail(CR_ERR_ARG, "cr_assemble_coupled: the convection term needs dim 2 and the field w");
+    if (p->mu == 0.0 && !m->has_mis)
+        return fail(CR_ERR_ARG, "cr_assemble_coupled: mu = 0 needs a mesh loaded with need_mis = 1");
+    cr_system* s = new cr_system();
+    s->m = m;
+    s->nu = p->nu;
+    s->mu = p->mu;
+    s->conv = p->conv;
+    s->lam_scale = p->lambda_scale > 0 ? p->lambda_scale : 2.0;
+    s->nrhs = nrhs;
+    StreamScope scope(m);
+    const size_t nfb = size_t(nrhs) * m->ne * m->d;
+    int rc;
+    if ((rc = s->arena.alloc_n(&s->fbar, nfb)) || (rc = copy_in(s->fbar, fbar, nfb, m->stream))) {
+        cr_destroy_system(s);
+        return rc;
+    }
+    if (p->conv != CR_CONV_NONE) {
+        const size_t nw = size_t(m->nf) * m->d;
+        if ((rc = s->arena.alloc_n(&s->w, nw)) || (rc = copy_in(s->w, w, nw, m->stream))) {
+            cr_destroy_system(s);
+            return rc;
+        }
+    }
+    if (blocks_out) {
+        const int L = (m->d + 1) * m->d;
+        const size_t nb = size_t(m->ne) * (size_t(L) * L + L + size_t(nrhs) * L);
+        double* dst = blocks_out;
+        const bool dev = is_device_pointer(blocks_out);
+        if (!dev && (rc = s->arena.alloc_n(&dst, nb))) {
+            cr_destroy_system(s);
+            return rc;
+        }
+        if ((rc = launch_assemble_export(s, dst, m->stream))) {
+            cr_destroy_system(s);
+            return rc;
+        }
+        if (!dev) {
+            cudaError_t e = cudaMemcpyAsync(blocks_out, dst, nb * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+            if (e != cudaSuccess) {
+                cr_destroy_system(s);
+                return cuda_fail(e, "cr_assemble_coupled: export copy");
+            }
+        }
+    }
+    *out = s;
+    return CR_OK;
+}
+
+extern "C" void cr_destroy_system(cr_system* s) {
+    if (!s) return;
+    s->arena.release();
+    delete s;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out) {
+    if (!out) return fail(CR_ERR_ARG, "cr_hybridise: out is NULL");
+    *out = nullptr;
+    if (!s) return fail(CR_ERR_ARG, "cr_hybridise: NULL system");
+    cr_mesh* m = s->m;
+    const int d = m->d;
+    cr_hybrid* h = new cr_hybrid();
+    h->s = s;
+    h->m = m;
+    h->nslot = 2 * d + 1;
+    const size_t nv = size_t(h->nslot) * d * d * m->nf;
+    const size_t n = size_t(m->nf) * d;
+    StreamScope scope(m);
+    DevArena tmp;
+    int rc = CR_OK;
+    auto bail = [&](int code) {
+        tmp.release();
+        cr_destroy_hybrid(h);
+        return code;
+    };
+    if ((rc = h->arena.alloc_n(&h->val64, nv))) return bail(rc);
+    if (o && o->keep_fp32 && (rc = h->arena.alloc_n(&h->val32, nv))) return bail(rc);
+    if (o && o->keep_bf16 && (rc = h->arena.alloc_n(&h->val16, nv))) return bail(rc);
+    if ((rc = h->arena.alloc_n(&h->S, n * s->nrhs)) || (rc = h->arena.alloc_n(&h->minv64, n)) ||
+        (rc = h->arena.alloc_n(&h->minv32, n)) || (rc = h->arena.alloc_n(&h->status, 1)) ||
+        (rc = h->arena.alloc_n(&h->red.partial, size_t(kRedSlots) * kMaxRedBlocks)) ||
+        (rc = h->arena.alloc_n(&h->red.count, 1)) || (rc = h->arena.alloc_n(&h->pvol, 4)) ||
+        (rc = h->arena.alloc_n(&h->ualt, n)))
+        return bail(rc);
+    if (s->mu == 0.0 && (rc = h->arena.alloc_n(&h->lam, size_t(m->ne)))) return bail(rc);
+    if ((rc = tmp.alloc_n(&h->dpart, size_t(2) * d * d * m->nf)) ||
+        (rc = tmp.alloc_n(&h->spart, size_t(s->nrhs) * 2 * d * m->nf)))
+        return bail(rc);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->red.count, 0, sizeof(unsigned), m->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    if ((rc = launch_hybridise(h, m->stream))) return bail(rc);
+    int32_t status = 0;
+    if ((e = cudaMemcpyAsync(&status, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cr_hybridise"));
+    tmp.release();
+    h->dpart = nullptr;
+    h->spart = nullptr;
+    if (status != 0) return bail(fail(CR_ERR_SINGULAR, "cr_hybridise: a singular element matrix (A_K or B_K)"));
+    *out = h;
+    return CR_OK;
+}
+
+extern "C" int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S) {
+    if (!h) return fail(CR_ERR_ARG, "cr_hybrid_export: NULL handle");
+    cr_mesh* m = h->m;
+    const size_t nf = size_t(m->nf);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(m->stream)) != cudaSuccess) return cuda_fail(e, "cr_hybrid_export");
+    if (cols) {
+        // slot 0 is the diagonal: its column is the row itself
+        std::vector<int32_t> c0(nf);
+        for (size_t f = 0; f < nf; ++f) c0[f] = int32_t(f);
+        if ((e = cudaMemcpy(cols, c0.data(), nf * sizeof(int32_t), cudaMemcpyDefault)) != cudaSuccess ||
+            (e = cudaMemcpy(cols + nf, m->cols, size_t(2 * m->d) * nf * sizeof(int32_t), cudaMemcpyDefault)) !=
+                cudaSuccess)
+            return cuda_fail(e, "cr_hybrid_export (cols)");
+    }
+    if (vals && (e = cudaMemcpy(vals, h->val64, size_t(h->nslot) * m->d * m->d * nf * sizeof(double),
+                                cudaMemcpyDefault)) != cudaSuccess)
+        return cuda_fail(e, "cr_hybrid_export (vals)");
+    if (S && (e = cudaMemcpy(S, h->S, size_t(h->s->nrhs) * nf * m->d * sizeof(double), cudaMemcpyDefault)) !=
+                 cudaSuccess)
+        return cuda_fail(e, "cr_hybrid_export (S)");
+    return CR_OK;
+}
+
+extern "C" int cr_apply_G(cr_hybrid* h, const double* x, double* y) {
+    if (!h || !x || !y) return fail(CR_ERR_ARG, "cr_apply_G: NULL argument");
+    if (!is_device_pointer(x) || !is_device_pointer(y)) return fail(CR_ERR_ARG, "cr_apply_G: device pointers expected");
+    StreamScope scope(h->m);
+    return launch_spmv64(h, x, y, h->m->stream);
+}
+
+extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
+    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve: rhs out of range");
+    if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve: bad method");
+    if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_MIXED_FP32 && o->prec != CR_PREC_MIXED_BF16)
+        return fail(CR_ERR_ARG, "cr_solve: bad precision");
+    if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve: tol must be > 0");
+    const int restart = o->restart > 0 ? o->restart : 30;
+    if (o->method == CR_METHOD_GMRES && (restart < 1 || restart > CR_MAX_RESTART))
+        return fail(CR_ERR_ARG, "cr_solve: restart must be in [1, CR_MAX_RESTART]");
+    cr_mesh* m = h->m;
+    const size_t n = size_t(m->nf) * m->d;
+    StreamScope scope(m);
+    CR_TRY(ensure_workspace(h, o->method == CR_METHOD_GMRES, restart, o->prec));
+    double* Wd = W;
+    const bool host = !is_device_pointer(W);
+    if (host) {
+        CR_TRY(ensure_stage(h, n * sizeof(double)));
+        Wd = h->stage;
+        if (o->use_x0) CR_CUDA(cudaMemcpyAsync(Wd, W, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    }
+    int rc = solve_impl(h, rhs, o, Wd, st);
+    if (host) {
+        cudaError_t e = cudaMemcpyAsync(W, Wd, n * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess && rc == CR_OK) rc = cuda_fail(e, "cr_solve: copy of W");
+    }
+    return rc;
+}
+
+extern "C" int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise_p,
+                             double* jump) {
+    if (!h || !W || !U || !P) return fail(CR_ERR_ARG, "cr_recover_up: NULL argument");
+    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_recover_up: rhs out of range");
+    cr_mesh* m = h->m;
+    const size_t n = size_t(m->nf) * m->d, ne = size_t(m->ne);
+    StreamScope scope(m);
+    const bool hw = !is_device_pointer(W), hu = !is_device_pointer(U), hp = !is_device_pointer(P);
+    size_t need = 0;
+    if (hw) need += n;
+    if (hu) need += n;
+    if (hp) need += ne;
+    need += 1;   // jump
+    CR_TRY(ensure_stage(h, need * sizeof(double)));
+    double* cur = h->stage;
+    const double* Wd = W;
+    double* Ud = U;
+    double* Pd = P;
+    if (hw) {
+        CR_CUDA(cudaMemcpyAsync(cur, W, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+        Wd = cur;
+        cur += n;
+    }
+    if (hu) { Ud = cur; cur += n; }
+    if (hp) { Pd = cur; cur += ne; }
+    double* jd = jump ? cur : nullptr;
+    CR_TRY(launch_recover(h, rhs, Wd, Ud, Pd, normalise_p, jd, m->stream));
+    if (hu) CR_CUDA(cudaMemcpyAsync(U, Ud, n * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    if (hp) CR_CUDA(cudaMemcpyAsync(P, Pd, ne * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    if (jump) CR_CUDA(cudaMemcpyAsync(jump, jd, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    if (hu || hp || jump) CR_CUDA(cudaStreamSynchronize(m->stream));
+    return CR_OK;
+}
+
+extern "C" void cr_destroy_hybrid(cr_hybrid* h) {
+    if (!h) return;
+    // cudaFree waits for the device; the mesh (and its stream) is not touched here,
+    // so handles may be destroyed in any order.
+    for (auto& g : h->graph_exec)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto e : h->prof_ev) cudaEventDestroy(e);
+    h->arena.release();
+    if (h->V32) cudaFree(h->V32);
+    if (h->V64) cudaFree(h->V64);
+    if (h->Z32) cudaFree(h->Z32);
+    if (h->Z64) cudaFree(h->Z64);
+    if (h->stage) cudaFree(h->stage);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    delete h;
+}

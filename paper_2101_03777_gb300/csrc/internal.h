@@ -1,0 +1,154 @@
+// Internal declarations of the crhyb library (not part of the C interface).
+//
+// Device data layout (all arrays in HBM, allocated once per handle):
+//   mesh    coords f64 [nv][d], elems i32 [ne][d+1], elem_face i32 [ne][d+1]
+//           (-1: exterior face), elem_side u8 [ne][d+1] (0: the simplex owns
+//           the face, C = +1; 1: C = -1), face_elems / face_local i32 [nf][2],
+//           cols i32 [2d][nf] (ELL columns of slots 1..2d).
+//   G       block ELL with NSLOT = 2d+1 slots per face row.  Slot 0 is the
+//           diagonal block; slots 1..d are the other local faces of the
+//           owner simplex of the row face, in increasing local index; slots
+//           d+1..2d those of the second simplex.  A slot whose face is
+//           exterior keeps col = row and zero values.  Values are stored
+//           structure-of-arrays, vals[((slot*d + i)*d + j)*nf + f], so that
+//           consecutive face rows are consecutive in memory for every (slot,
+//           i, j): the SpMV's loads are fully coalesced.
+//   vectors [nf][d], face major, component fastest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/crhyb.h"
+
+namespace crhyb {
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CR_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::crhyb::cuda_fail(_e, #call);    \
+    } while (0)
+
+#define CR_TRY(call)                                                    \
+    do {                                                                \
+        int _rc = (call);                                               \
+        if (_rc != CR_OK) return _rc;                                   \
+    } while (0)
+
+bool is_device_pointer(const void* p);
+
+// Device allocation helper: records the pointer for release by the owner.
+struct DevArena {
+    std::vector<void*> ptrs;
+    int alloc(void** p, size_t bytes);
+    template <typename T>
+    int alloc_n(T** p, size_t n) { return alloc(reinterpret_cast<void**>(p), n * sizeof(T)); }
+    void release();
+};
+
+// Deterministic two-level reductions: per-block partial sums, then the last
+// block to finish sums the partials in block order.
+constexpr int kRedSlots = 4;          // up to 4 simultaneous dot products
+constexpr int kMaxRedBlocks = 65536;  // capacity of the partial-sum buffer (blocks per reduction)
+
+struct RedBuf {
+    double* partial;      // [kRedSlots][kMaxRedBlocks]
+    unsigned int* count;  // completion counter (reset by the last block)
+};
+
+}  // namespace crhyb
+
+struct cr_mesh {
+    int d = 0;
+    int64_t ne = 0, nv = 0, nf = 0, nf_ext = 0;
+    int k0 = 0;
+    bool has_mis = false;
+    cudaStream_t user_stream = nullptr;  // the caller's stream
+    cudaStream_t stream = nullptr;       // library-owned stream (graph capture needs a non-default stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // host copies for export
+    std::vector<int32_t> h_face_vertices, h_face_elems, h_face_local;
+    std::vector<uint8_t> h_mis;
+    // device
+    crhyb::DevArena arena;
+    double* coords = nullptr;
+    int32_t* elems = nullptr;
+    int32_t* elem_face = nullptr;
+    uint8_t* elem_side = nullptr;
+    int32_t* face_elems = nullptr;
+    int32_t* face_local = nullptr;
+    int32_t* cols = nullptr;
+    uint8_t* mis = nullptr;
+};
+
+struct cr_system {
+    cr_mesh* m = nullptr;
+    double nu = 0, mu = 0, lam_scale = 2.0;
+    int conv = CR_CONV_NONE;
+    int nrhs = 1;
+    crhyb::DevArena arena;
+    double* fbar = nullptr;   // [nrhs][ne][d]
+    double* w = nullptr;      // [nf][d] or null
+};
+
+struct cr_hybrid {
+    cr_system* s = nullptr;
+    cr_mesh* m = nullptr;
+    int nslot = 0;
+    crhyb::DevArena arena;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+    __nv_bfloat16* val16 = nullptr;
+    double* S = nullptr;          // [nrhs][nf][d]
+    double* minv64 = nullptr;     // [nf*d]
+    float* minv32 = nullptr;
+    double* lam = nullptr;        // [ne] lambda_K on M_1 (mu = 0)
+    double* dpart = nullptr;      // [2][d][d][nf] diagonal contributions per side
+    double* spart = nullptr;      // [nrhs][2][d][nf] S contributions per side
+    int32_t* status = nullptr;    // device status word
+    crhyb::RedBuf red{};
+    // Krylov workspace (allocated on first solve)
+    bool ws_ready = false;
+    int ws_restart = 0;
+    double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float* V32 = nullptr;         // GMRES basis [restart+1][N]
+    double* V64 = nullptr;        // GMRES basis FP64 [restart+1][N]
+    float* Z32 = nullptr;         // GMRES scratch vector
+    double* Z64 = nullptr;
+    void* scal = nullptr;         // device Krylov scalars
+    void* h_scal = nullptr;       // pinned host mirror
+    double* pvol = nullptr;       // recovery scratch
+    double* ualt = nullptr;       // recovery: velocity from the non-owner side
+    double* stage = nullptr;      // host<->device staging
+    size_t stage_bytes = 0;
+    cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> prof_ev;   // profile = 1: event pairs around SpMV launches
+    double prof_ms = 0.0;
+    int prof_n = 0;
+    int graph_key[4] = {-1, -1, -1, -1};
+};
+
+namespace crhyb {
+
+// ---- kernels launched from the API layer (defined in the .cu files) ----
+int launch_assemble_export(cr_system* s, double* blocks, cudaStream_t st);
+int launch_hybridise(cr_hybrid* h, cudaStream_t st);
+int launch_recover(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise,
+                   double* jump_dev, cudaStream_t st);
+int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st);
+int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st);
+size_t kscal_bytes();
+
+// staging buffer for host arguments (api.cu)
+int ensure_stage(cr_hybrid* h, size_t bytes);
+
+}  // namespace crhyb

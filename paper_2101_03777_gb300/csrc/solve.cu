@@ -1,0 +1,740 @@
+// Krylov solve of the hybridised system G W = S (hybrid method, step 2).
+//
+//   * Jacobi-PCG (G symmetric positive definite for mu > 0, b_h = 0,
+//     Section 3.2 item 6) in FP64, or in FP32 (FP32 or BF16 matrix values)
+//     inside FP64 iterative refinement;
+//   * restarted GMRES(m) with right Jacobi preconditioning for the
+//     nonsymmetric or indefinite systems (Section 4.3), same precisions.
+//
+// Every scalar of the iteration lives in device memory; the host only reads
+// a status record every `check_every` iterations.  Kernels of an iteration
+// return at once when the solve has finished, so a chunk of iterations may be
+// launched (or replayed as a CUDA graph) without knowing where it stops, and
+// the iteration count stays exact.  All dot products are deterministic
+// two-level reductions (no floating-point atomics).
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "device_common.cuh"
+
+namespace crhyb {
+
+// Scalars of a solve, in device memory (mirrored to pinned host memory).
+struct KScal {
+    double rz, alpha, beta, rr, bb, tol2, pq;   // inner Krylov state
+    double orr, obb;                            // FP64 residual of the outer iteration
+    double rz_prev;                             // r.M^{-1}r before the last update
+    int it, max_it, done, status;
+    int conv;                                   // the FP64 true residual met the tolerance
+    // GMRES
+    double beta0;                               // ||r0|| of the current cycle
+    int j;                                      // Arnoldi step within the cycle
+    int m;                                      // restart length
+    int stop;                                   // the current GMRES cycle has ended
+    int pad_;
+    double hb[CR_MAX_RESTART + 1];              // Gram-Schmidt coefficients of the current step
+    double H[(CR_MAX_RESTART + 1) * CR_MAX_RESTART];
+    double cs[CR_MAX_RESTART], sn[CR_MAX_RESTART], g[CR_MAX_RESTART + 1];
+    double y[CR_MAX_RESTART];
+};
+
+namespace {
+
+int g_num_sms = 0;
+
+int grid_for(int64_t n) {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    const int64_t want = (n + kBlock - 1) / kBlock;
+    const int64_t cap = int64_t(g_num_sms) * 8;   // 8 resident 256-thread blocks per SM
+    return int(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// streaming (evict-first) loads of matrix data
+__device__ __forceinline__ double ld_val(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16* p) {
+    const unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(unsigned(u) << 16);
+}
+
+// y_f = sum over the 2d+1 slots of block(slot) * x[col(slot)]  (one face row)
+template <int D, typename VT, typename XT, typename AT>
+__device__ __forceinline__ void ell_row(int64_t f, int64_t nf, const int32_t* __restrict__ cols,
+                                        const VT* __restrict__ vals, const XT* __restrict__ x, AT (&y)[D]) {
+    constexpr int NS = 2 * D + 1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i] = AT(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + size_t(s - 1) * nf + f));
+        AT xv[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) xv[j] = AT(__ldg(x + c * D + j));
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                y[i] = fma(AT(ld_val(vals + ((size_t(s) * D + i) * D + j) * nf + f)), xv[j], y[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG kernels
+// ---------------------------------------------------------------------------
+
+// q = G p, pq = p.q; last block: alpha = rz/pq (breakdown if pq <= 0 or NaN).
+template <int D, typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv(int64_t nf, const int32_t* __restrict__ cols,
+                                                     const VT* __restrict__ vals, const XT* __restrict__ p,
+                                                     XT* __restrict__ q, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    double part[1] = {0.0};
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        XT y[D];
+        ell_row<D, VT, XT, XT>(f, nf, cols, vals, p, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            q[f * D + i] = y[i];
+            part[0] += double(p[f * D + i]) * double(y[i]);
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        sc->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rz / pq;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, rz' = r.M^{-1}r, rr = r.r; last block: beta,
+// iteration count, convergence (rr <= tol2) and the iteration limit.
+template <int D, typename XT>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(int64_t n, XT* __restrict__ x, XT* __restrict__ r,
+                                                       const XT* __restrict__ p, const XT* __restrict__ q,
+                                                       const XT* __restrict__ minv, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const XT alpha = XT(sc->alpha);
+    double part[2] = {0.0, 0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const XT xn = fma(alpha, p[k], x[k]);
+        const XT rn = fma(-alpha, q[k], r[k]);
+        x[k] = xn;
+        r[k] = rn;
+        const double rd = double(rn);
+        part[0] += rd * double(minv[k]) * rd;
+        part[1] += rd * rd;
+    }
+    double tot[2];
+    if (grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        const double rz = tot[0];
+        sc->rz_prev = sc->rz;
+        sc->beta = rz / sc->rz;
+        sc->rz = rz;
+        sc->rr = tot[1];
+        sc->it += 1;
+        if (!isfinite(tot[1])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// p = M^{-1} r + beta p   (first: p = M^{-1} r)
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_pcg_dir(int64_t n, XT* __restrict__ p, const XT* __restrict__ r,
+                                                    const XT* __restrict__ minv, const KScal* sc, int first) {
+    if (sc->done) return;
+    const XT beta = XT(first ? 0.0 : sc->beta);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const XT z = minv[k] * r[k];
+        p[k] = first ? z : fma(beta, p[k], z);
+    }
+}
+
+// r = b - G x in FP64 (x optional: NULL means x = 0), optionally r32 = float(r);
+// sums rr, bb, r.M^{-1}r.  Last block:
+//   mode 0: outer residual only (orr, obb);
+//   mode 1: start of a PCG solve: rz, rr, bb, tol2 = tol^2 bb, done;
+//   mode 2: reliable update of the mixed-precision PCG: the iterated residual
+//           is replaced by the true one; beta = rz_true / rz_prev continues the
+//           same search direction; the next update is due after a reduction
+//           by `delta` or at the target (tol2 = max(delta^2 rr, (tol/2)^2 bb));
+//           conv/done when the true residual meets the tolerance.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t* __restrict__ cols,
+                                                       const double* __restrict__ vals, const double* __restrict__ b,
+                                                       const double* __restrict__ x, double* __restrict__ r,
+                                                       float* __restrict__ r32, const double* __restrict__ minv,
+                                                       KScal* sc, RedBuf red, int mode, double tol, double delta) {
+    double part[3] = {0.0, 0.0, 0.0};
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        double y[D];
+        if (x) ell_row<D, double, double, double>(f, nf, cols, vals, x, y);
+        else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const double bi = b[f * D + i];
+            const double ri = bi - y[i];
+            if (r) r[f * D + i] = ri;
+            if (r32) r32[f * D + i] = __double2float_rn(ri);
+            part[0] += ri * ri;
+            part[1] += bi * bi;
+            part[2] += ri * minv[f * D + i] * ri;
+        }
+    }
+    double tot[3];
+    if (grid_sum<3>(part, red, tot) && threadIdx.x == 0) {
+        sc->orr = tot[0];
+        sc->obb = tot[1];
+        if (mode == 1) {
+            sc->rr = tot[0];
+            sc->bb = tot[1];
+            sc->rz = tot[2];
+            sc->tol2 = tol * tol * tot[1];
+            sc->status = CR_OK;
+            sc->done = (tot[0] <= sc->tol2) ? 1 : 0;
+            if (!isfinite(tot[0])) {
+                sc->done = 1;
+                sc->status = CR_ERR_BREAKDOWN;
+            }
+        } else if (mode == 2) {
+            const double target = tol * tol * tot[1];
+            sc->rr = tot[0];
+            sc->bb = tot[1];
+            sc->beta = sc->rz_prev > 0.0 ? tot[2] / sc->rz_prev : 0.0;
+            sc->rz = tot[2];
+            sc->tol2 = fmax(delta * delta * tot[0], 0.25 * target);
+            sc->conv = (tot[0] <= target) ? 1 : 0;
+            sc->done = sc->conv;
+            sc->status = CR_OK;
+            if (!isfinite(tot[0])) {
+                sc->done = 1;
+                sc->status = CR_ERR_BREAKDOWN;
+            }
+        }
+    }
+}
+
+// Inner FP32 solve start for refinement: x = 0, p = M^{-1} r; rz, rr; the
+// inner target is ||r_k|| <= inner_tol ||r_0||.
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_inner_start(int64_t n, XT* __restrict__ x, const XT* __restrict__ r,
+                                                        XT* __restrict__ p, const XT* __restrict__ minv, KScal* sc,
+                                                        RedBuf red, double inner_tol) {
+    double part[2] = {0.0, 0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] = XT(0);
+        const XT z = minv[k] * r[k];
+        if (p) p[k] = z;
+        part[0] += double(r[k]) * double(z);
+        part[1] += double(r[k]) * double(r[k]);
+    }
+    double tot[2];
+    if (grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        sc->rz = tot[0];
+        sc->rr = tot[1];
+        sc->bb = tot[1];
+        sc->tol2 = inner_tol * inner_tol * tot[1];
+        sc->status = CR_OK;
+        sc->done = (tot[1] == 0.0) ? 1 : 0;
+        if (sc->it >= sc->max_it) {
+            sc->done = 1;
+            sc->status = CR_ERR_NOT_CONVERGED;
+        }
+    }
+}
+
+// x64 += x32
+__global__ void __launch_bounds__(kBlock) k_add32(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        x[k] += double(d[k]);
+}
+
+// plain FP64 SpMV (no reduction)
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_spmv64(int64_t nf, const int32_t* __restrict__ cols,
+                                                   const double* __restrict__ vals, const double* __restrict__ x,
+                                                   double* __restrict__ y) {
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        double v[D];
+        ell_row<D, double, double, double>(f, nf, cols, vals, x, v);
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[f * D + i] = v[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(m) kernels: Arnoldi with classical Gram-Schmidt applied twice (CGS2),
+// right Jacobi preconditioning: G M^{-1} z_j, x = x0 + M^{-1} V y.
+// ---------------------------------------------------------------------------
+
+// V_0 = r / ||r||; beta0 = ||r||, g = (beta0, 0, ...), j = 0.  r holds r0.
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_norm_start(int64_t n, const XT* __restrict__ r, KScal* sc,
+                                                          RedBuf red) {
+    if (sc->done) return;
+    double part[1] = {0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        part[0] += double(r[k]) * double(r[k]);
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double b = sqrt(tot[0]);
+        sc->beta0 = b;
+        sc->g[0] = b;
+        sc->j = 0;
+        sc->stop = 0;
+        sc->rr = tot[0];
+        if (!isfinite(b)) { sc->status = CR_ERR_BREAKDOWN; sc->done = 1; }
+        else if (tot[0] <= sc->tol2) sc->done = 1;
+        else if (sc->it >= sc->max_it) { sc->status = CR_ERR_NOT_CONVERGED; sc->done = 1; }
+    }
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_scale_v0(int64_t n, const XT* __restrict__ r, XT* __restrict__ V,
+                                                        const KScal* sc) {
+    if (sc->done) return;
+    const double inv = 1.0 / sc->beta0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        V[k] = XT(double(r[k]) * inv);
+}
+
+// w = G (M^{-1} V_j) into V_{j+1} (unnormalised)
+template <int D, typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_precond(int64_t n, const XT* __restrict__ V, const XT* __restrict__ minv,
+                                                       XT* __restrict__ z, const KScal* sc) {
+    if (sc->done || sc->stop) return;
+    const XT* vj = V + size_t(sc->j) * n;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        z[k] = minv[k] * vj[k];
+}
+
+template <int D, typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_spmv(int64_t nf, const int32_t* __restrict__ cols,
+                                                    const VT* __restrict__ vals, const XT* __restrict__ z,
+                                                    XT* __restrict__ V, const KScal* sc) {
+    if (sc->done || sc->stop) return;
+    XT* w = V + size_t(sc->j + 1) * nf * D;
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        XT y[D];
+        ell_row<D, VT, XT, XT>(f, nf, cols, vals, z, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) w[f * D + i] = y[i];
+    }
+}
+
+// h_i = V_i . w for i = 0..j (one pass over w and V_0..V_j); `pass` 0 or 1 (CGS2).
+// The (j+1) dots go through the partial buffer in groups of kRedSlots.
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_dots(int64_t n, const XT* __restrict__ V, int i0, KScal* sc,
+                                                    RedBuf red) {
+    if (sc->done || sc->stop) return;
+    const int j = sc->j;
+    if (i0 > j) return;
+    const XT* w = V + size_t(j + 1) * n;
+    double part[kRedSlots] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double wk = double(w[k]);
+#pragma unroll
+        for (int t = 0; t < kRedSlots; ++t)
+            if (i0 + t <= j) part[t] += double(V[size_t(i0 + t) * n + k]) * wk;
+    }
+    double tot[kRedSlots];
+    if (grid_sum<kRedSlots>(part, red, tot) && threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < kRedSlots; ++t)
+            if (i0 + t <= j) sc->hb[i0 + t] = tot[t];
+    }
+}
+
+// w -= sum_i h_i V_i; accumulate h into H(:, j); ||w||^2 on the second pass.
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_orth(int64_t n, XT* __restrict__ V, KScal* sc, RedBuf red, int pass) {
+    if (sc->done || sc->stop) return;
+    const int j = sc->j;
+    XT* w = V + size_t(j + 1) * n;
+    double part[1] = {0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        double wk = double(w[k]);
+        for (int i = 0; i <= j; ++i) wk -= sc->hb[i] * double(V[size_t(i) * n + k]);
+        w[k] = XT(wk);
+        part[0] += wk * wk;
+    }
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const int m = sc->m;
+        for (int i = 0; i <= j; ++i) sc->H[i * m + j] = (pass == 0 ? 0.0 : sc->H[i * m + j]) + sc->hb[i];
+        if (pass == 1) {
+            // H(j+1, j) = ||w||; Givens rotations; residual estimate |g_{j+1}|
+            const double hn = sqrt(tot[0]);
+            sc->H[(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double a = sc->H[i * m + j], b = sc->H[(i + 1) * m + j];
+                sc->H[i * m + j] = sc->cs[i] * a + sc->sn[i] * b;
+                sc->H[(i + 1) * m + j] = -sc->sn[i] * a + sc->cs[i] * b;
+            }
+            const double a = sc->H[j * m + j], b = sc->H[(j + 1) * m + j];
+            const double den = hypot(a, b);
+            const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+            sc->cs[j] = c;
+            sc->sn[j] = s;
+            sc->H[j * m + j] = den;
+            sc->H[(j + 1) * m + j] = 0.0;
+            sc->g[j + 1] = -s * sc->g[j];
+            sc->g[j] = c * sc->g[j];
+            sc->it += 1;
+            sc->rr = sc->g[j + 1] * sc->g[j + 1];
+            sc->j = j + 1;
+            sc->pq = hn;   // ||w|| before normalisation
+            if (!isfinite(hn) || !(den > 0.0)) { sc->status = CR_ERR_BREAKDOWN; sc->done = 1; }
+            if (sc->rr <= sc->tol2 || sc->it >= sc->max_it || j + 1 == m) sc->stop = 1;
+        }
+    }
+}
+
+// V_{j} /= H(j, j-1) (j already advanced); skipped on a happy breakdown.
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_normalise(int64_t n, XT* __restrict__ V, const KScal* sc) {
+    if (sc->done || sc->stop) return;   // the last vector of a cycle is never used
+    const double hn = sc->pq;
+    if (!(hn > 0.0)) return;
+    XT* w = V + size_t(sc->j) * n;
+    const double inv = 1.0 / hn;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        w[k] = XT(double(w[k]) * inv);
+}
+
+// Back substitution H y = g (upper triangular, size j) by one thread.
+__global__ void k_gm_solve_y(KScal* sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (sc->status != CR_OK) { sc->j = 0; return; }
+    const int k = sc->j, m = sc->m;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = sc->g[i];
+        for (int t = i + 1; t < k; ++t) s -= sc->H[i * m + t] * sc->y[t];
+        sc->y[i] = s / sc->H[i * m + i];
+    }
+}
+
+// x += M^{-1} V y
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_gm_update(int64_t n, XT* __restrict__ x, const XT* __restrict__ V,
+                                                      const XT* __restrict__ minv, const KScal* sc) {
+    const int k = sc->j;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += sc->y[i] * double(V[size_t(i) * n + q]);
+        x[q] = XT(double(x[q]) + double(minv[q]) * s);
+    }
+}
+
+// r = b - G x in the working precision (for GMRES restarts)
+template <int D, typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_residual_w(int64_t nf, const int32_t* __restrict__ cols,
+                                                       const VT* __restrict__ vals, const XT* __restrict__ b,
+                                                       const XT* __restrict__ x, XT* __restrict__ r, const KScal* sc) {
+    if (sc->done) return;
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        XT y[D];
+        ell_row<D, VT, XT, XT>(f, nf, cols, vals, x, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) r[f * D + i] = b[f * D + i] - y[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+struct Ctx {
+    cr_hybrid* h;
+    cudaStream_t st;
+    KScal* sc;    // device
+    KScal* hs;    // pinned host
+    int64_t nf, n;
+    int d;
+    bool profile;
+};
+
+int read_scal(Ctx& c) {
+    CR_CUDA(cudaMemcpyAsync(c.hs, c.sc, offsetof(KScal, H), cudaMemcpyDeviceToHost, c.st));
+    CR_CUDA(cudaStreamSynchronize(c.st));
+    return CR_OK;
+}
+
+template <int D, typename VT, typename XT>
+void pcg_iteration(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q, cudaEvent_t e0 = nullptr,
+                   cudaEvent_t e1 = nullptr) {
+    const int g = grid_for(c.nf), gn = grid_for(c.n);
+    if (e0) cudaEventRecord(e0, c.st);
+    k_pcg_spmv<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, c.h->m->cols, vals, p, q, c.sc, c.h->red);
+    if (e1) cudaEventRecord(e1, c.st);
+    k_pcg_update<D, XT><<<gn, kBlock, 0, c.st>>>(c.n, x, r, p, q, minv, c.sc, c.h->red);
+    k_pcg_dir<XT><<<gn, kBlock, 0, c.st>>>(c.n, p, r, minv, c.sc, 0);
+}
+
+// Run PCG iterations until sc->done, in chunks of `chunk` iterations,
+// replayed as a CUDA graph when asked.  Assumes x, r, p, rz, tol2 are set.
+template <int D, typename VT, typename XT>
+int pcg_loop(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q, int chunk, bool graph, int gkey) {
+    cr_hybrid* h = c.h;
+    if (graph && (h->graph_key[gkey] != chunk || !h->graph_exec[gkey])) {
+        if (h->graph_exec[gkey]) { cudaGraphExecDestroy(h->graph_exec[gkey]); h->graph_exec[gkey] = nullptr; }
+        cudaGraph_t gr;
+        CR_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < chunk; ++k) pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q);
+        CR_CUDA(cudaStreamEndCapture(c.st, &gr));
+        cudaError_t e = cudaGraphInstantiate(&h->graph_exec[gkey], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        h->graph_key[gkey] = chunk;
+    }
+    const bool prof = c.profile && !graph;
+    if (prof && int(h->prof_ev.size()) < 2 * chunk) {
+        for (int k = int(h->prof_ev.size()); k < 2 * chunk; ++k) {
+            cudaEvent_t e;
+            CR_CUDA(cudaEventCreate(&e));
+            h->prof_ev.push_back(e);
+        }
+    }
+    int it_before = -1;
+    for (;;) {
+        CR_TRY(read_scal(c));
+        if (prof && it_before >= 0) {
+            // the SpMV of an iteration runs in full exactly when that iteration is counted
+            const int ran = c.hs->it - it_before + (c.hs->status == CR_ERR_BREAKDOWN ? 1 : 0);
+            for (int k = 0; k < ran && k < chunk; ++k) {
+                float ms = 0.f;
+                CR_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
+                h->prof_ms += ms;
+                h->prof_n += 1;
+            }
+        }
+        if (c.hs->done) break;
+        it_before = c.hs->it;
+        if (graph) {
+            CR_CUDA(cudaGraphLaunch(h->graph_exec[gkey], c.st));
+        } else {
+            for (int k = 0; k < chunk; ++k) {
+                if (prof) pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]);
+                else pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q);
+            }
+            CR_CUDA(cudaGetLastError());
+        }
+    }
+    return CR_OK;
+}
+
+// One GMRES(m) cycle set: iterate until the residual target or the limit.
+// b, x, r, V, z in the working precision; the recursive residual estimate
+// |g_{j+1}| drives the inner stop, the true residual is recomputed per cycle.
+template <int D, typename VT, typename XT>
+int gmres_loop(Ctx& c, const VT* vals, const XT* minv, const XT* b, XT* x, XT* r, XT* V, XT* z) {
+    cr_hybrid* h = c.h;
+    const int g = grid_for(c.nf), gn = grid_for(c.n);
+    for (;;) {
+        // true residual of the current iterate starts every cycle
+        k_residual_w<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, h->m->cols, vals, b, x, r, c.sc);
+        k_gm_norm_start<XT><<<gn, kBlock, 0, c.st>>>(c.n, r, c.sc, h->red);
+        k_gm_scale_v0<XT><<<gn, kBlock, 0, c.st>>>(c.n, r, V, c.sc);
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->done) break;
+        const int m = c.hs->m;
+        for (int j = 0; j < m; ++j) {
+            k_gm_precond<D, VT, XT><<<gn, kBlock, 0, c.st>>>(c.n, V, minv, z, c.sc);
+            k_gm_spmv<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, h->m->cols, vals, z, V, c.sc);
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i0 = 0; i0 <= j; i0 += kRedSlots)
+                    k_gm_dots<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, i0, c.sc, h->red);
+                k_gm_orth<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc, h->red, pass);
+            }
+            k_gm_normalise<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc);
+            CR_CUDA(cudaGetLastError());
+            if ((j + 1) % 8 == 0 || j + 1 == m) {
+                CR_TRY(read_scal(c));
+                if (c.hs->done || c.hs->stop) break;
+            }
+        }
+        // x += M^{-1} V y over the steps taken in this cycle
+        k_gm_solve_y<<<1, 32, 0, c.st>>>(c.sc);
+        k_gm_update<XT><<<gn, kBlock, 0, c.st>>>(c.n, x, V, minv, c.sc);
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->status != CR_OK) break;
+    }
+    return CR_OK;
+}
+
+template <int D>
+int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    cr_mesh* m = h->m;
+    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D,
+          o->profile != 0};
+    h->prof_ms = 0.0;
+    h->prof_n = 0;
+    const double* b = h->S + size_t(rhs) * c.n;
+    const int chunk = o->check_every > 0 ? o->check_every : 16;
+    const bool graph = o->use_graph != 0;
+    const int gmax = o->max_iter > 0 ? o->max_iter : 100000;
+    const int max_outer = o->max_outer > 0 ? o->max_outer : 60;
+    const int ggrid = grid_for(c.nf), gn = grid_for(c.n);
+    const double* x0 = o->use_x0 ? h->x64 : nullptr;
+
+    std::memset(c.hs, 0, sizeof(KScal));
+    c.hs->max_it = gmax;
+    c.hs->m = o->restart > 0 ? o->restart : 30;
+    CR_CUDA(cudaMemcpyAsync(c.sc, c.hs, sizeof(KScal), cudaMemcpyHostToDevice, c.st));
+    if (o->use_x0) CR_CUDA(cudaMemcpyAsync(h->x64, W, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    else CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
+
+    int status = CR_OK;   // decided on the host; device statuses are folded in below
+    int outer = 0;
+    if (o->prec == CR_PREC_FP64) {
+        k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, nullptr, h->minv64, c.sc,
+                                                    h->red, 1, o->tol, 0.0);
+        CR_CUDA(cudaGetLastError());
+        if (o->method == CR_METHOD_PCG) {
+            k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
+            CR_TRY((pcg_loop<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, chunk, graph, 0)));
+        } else {
+            CR_TRY((gmres_loop<D, double, double>(c, h->val64, h->minv64, b, h->x64, h->r64, h->V64, h->Z64)));
+        }
+        CR_TRY(read_scal(c));
+        status = c.hs->status;
+    } else if (o->method == CR_METHOD_PCG) {
+        // FP32 (or BF16-value) PCG with reliable updates: the search direction is
+        // kept across updates; each update adds the FP32 correction to the FP64
+        // iterate and replaces the iterated residual by the FP64 true residual.
+        const bool bf = o->prec == CR_PREC_MIXED_BF16;
+        if ((bf && !h->val16) || (!bf && !h->val32))
+            return fail(CR_ERR_ARG, "cr_solve: the values for this precision were not kept by cr_hybridise");
+        const double delta = o->inner_tol > 0 ? o->inner_tol : 0.1;
+        CR_CUDA(cudaMemsetAsync(h->x32, 0, sizeof(float) * c.n, c.st));
+        k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, h->r32, h->minv64, c.sc,
+                                                    h->red, 2, o->tol, delta);
+        k_pcg_dir<float><<<gn, kBlock, 0, c.st>>>(c.n, h->p32, h->r32, h->minv32, c.sc, 1);
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        double last_rr = c.hs->rr;
+        int it_mark = 0;
+        while (!c.hs->conv) {
+            if (bf) CR_TRY((pcg_loop<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->x32, h->r32, h->p32, h->q32, chunk, graph, 2)));
+            else CR_TRY((pcg_loop<D, float, float>(c, h->val32, h->minv32, h->x32, h->r32, h->p32, h->q32, chunk, graph, 1)));
+            CR_TRY(read_scal(c));
+            const int dev_status = c.hs->status;
+            if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }
+            // reliable update
+            k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
+            CR_CUDA(cudaMemsetAsync(h->x32, 0, sizeof(float) * c.n, c.st));
+            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, h->r32, h->minv64,
+                                                        c.sc, h->red, 2, o->tol, delta);
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            ++outer;
+            it_mark = c.hs->it;
+            if (c.hs->status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+            if (c.hs->conv) break;
+            if (c.hs->it >= gmax || outer >= max_outer * 16) { status = CR_ERR_NOT_CONVERGED; break; }
+            if (c.hs->rr > 100.0 * last_rr) { status = CR_ERR_BREAKDOWN; break; }   // diverging (rounded values)
+            last_rr = c.hs->rr;
+            k_pcg_dir<float><<<gn, kBlock, 0, c.st>>>(c.n, h->p32, h->r32, h->minv32, c.sc, dev_status == CR_OK ? 0 : 1);
+            CR_CUDA(cudaGetLastError());
+        }
+    } else {
+        // GMRES in FP32 (or BF16 values) inside FP64 iterative refinement
+        const bool bf = o->prec == CR_PREC_MIXED_BF16;
+        if ((bf && !h->val16) || (!bf && !h->val32))
+            return fail(CR_ERR_ARG, "cr_solve: the values for this precision were not kept by cr_hybridise");
+        const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+        double last = -1.0;
+        for (;;) {
+            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, h->r32, h->minv64,
+                                                        c.sc, h->red, 0, o->tol, 0.0);
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            const double rel2 = c.hs->obb > 0 ? c.hs->orr / c.hs->obb : 0.0;
+            if (!std::isfinite(rel2)) { status = CR_ERR_BREAKDOWN; break; }
+            if (rel2 <= o->tol * o->tol) break;
+            if (outer >= max_outer || c.hs->it >= gmax) { status = CR_ERR_NOT_CONVERGED; break; }
+            if (last >= 0.0 && rel2 > 100.0 * last) { status = CR_ERR_BREAKDOWN; break; }
+            last = rel2;
+            const int it_start = c.hs->it;
+            k_inner_start<float><<<gn, kBlock, 0, c.st>>>(c.n, h->x32, h->r32, nullptr, h->minv32, c.sc, h->red, itol);
+            CR_CUDA(cudaMemcpyAsync(h->q32, h->r32, sizeof(float) * c.n, cudaMemcpyDeviceToDevice, c.st));
+            CR_CUDA(cudaGetLastError());
+            if (bf) CR_TRY((gmres_loop<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->q32, h->x32, h->r32, h->V32, h->Z32)));
+            else CR_TRY((gmres_loop<D, float, float>(c, h->val32, h->minv32, h->q32, h->x32, h->r32, h->V32, h->Z32)));
+            CR_TRY(read_scal(c));
+            if (c.hs->status == CR_ERR_BREAKDOWN && c.hs->it == it_start) { status = CR_ERR_BREAKDOWN; break; }
+            k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
+            CR_CUDA(cudaGetLastError());
+            ++outer;
+        }
+    }
+    CR_TRY(read_scal(c));
+    const int iters = c.hs->it;
+    // W = x; final FP64 residual of the returned W
+    CR_CUDA(cudaMemcpyAsync(W, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, nullptr, nullptr, h->minv64, c.sc,
+                                                h->red, 0, o->tol, 0.0);
+    CR_CUDA(cudaGetLastError());
+    CR_TRY(read_scal(c));
+    const double relres = c.hs->obb > 0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
+    if (status == CR_OK && !(relres <= o->tol)) {
+        // the recursive residual can sit slightly below the true one
+        if (iters >= gmax) status = CR_ERR_NOT_CONVERGED;
+        else if (!(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->outer = outer;
+        st->relres = relres;
+        st->status = status;
+        st->spmv_launches = h->prof_n;
+        st->spmv_ms = h->prof_ms;
+    }
+    if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve: iteration limit reached before the tolerance");
+    if (status == CR_ERR_BREAKDOWN)
+        return fail(status, "cr_solve: Krylov breakdown or divergence (p.Gp <= 0, NaN, zero Arnoldi vector, "
+                            "or the low-precision values made the iteration diverge)");
+    return status;
+}
+
+}  // namespace
+
+size_t kscal_bytes() { return sizeof(KScal); }
+
+int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st) {
+    const int g = grid_for(h->m->nf);
+    if (h->m->d == 2) k_spmv64<2><<<g, kBlock, 0, st>>>(h->m->nf, h->m->cols, h->val64, x, y);
+    else k_spmv64<3><<<g, kBlock, 0, st>>>(h->m->nf, h->m->cols, h->val64, x, y);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {
+    return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);
+}
+
+}  // namespace crhyb

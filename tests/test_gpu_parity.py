@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA library against the CPU FP64 oracle, through the C-ABI.
+
+Tolerances (relative L2 unless stated):
+  * G and S after hybridisation: 1e-12 of max |G|, |S| (same FP64 formulas,
+    different rounding order);
+  * U and P (P normalised to zero mean) after an FP64 solve to a relative
+    residual of 1e-13: 1e-9; after mixed-precision refinement to 1e-13: 1e-8;
+  * element blocks A_K, D_K, R_K: 1e-12 of the largest entry.
+Meshes span several thread blocks and a ragged tail (element and face counts
+that are not multiples of the block sizes).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import coupled, pipeline, topology
+from paper_2101_03777_gb300 import crhyb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_case(name):
+    """(coords, elems, nu, mu, conv, fbar [nrhs, ne, d], w or None)."""
+    if name == "cfg1":
+        p = synth.config_problem("cfg1")
+        return p["coords"], p["elems"], p["nu"], p["mu"], "none", p["fbar"], None
+    if name == "2d_perturbed_37":
+        p = synth.config_problem("cfg2", n=37, nrhs=2)
+        return p["coords"], p["elems"], p["nu"], p["mu"], "none", p["fbar"], None
+    if name == "3d_kuhn_5":
+        p = synth.config_problem("cfg3", n=5)
+        return p["coords"], p["elems"], p["nu"], p["mu"], "none", p["fbar"], None
+    if name in ("ns_newton_9", "ns_oseen_9"):
+        coords, elems = synth.mesh2d_square(9, 0.1, 4)
+        t = topology.build_faces(elems)
+        w = synth.stream_velocity(coords[t["face_vertices"]].mean(axis=1), seed=3)
+        modes = synth.fourier_modes(2, 1)
+        fbar = synth.element_means(lambda x: synth.fourier_force(x, modes), coords, elems, order=3)[None]
+        return coords, elems, 0.01, 100.0, name.split("_")[1], fbar, w
+    if name == "steady_stokes_3":
+        coords, elems = synth.mesh2d_square(3, 0.2, 2)
+        modes = synth.fourier_modes(2, 1)
+        fbar = synth.element_means(lambda x: synth.fourier_force(x, modes), coords, elems, order=3)[None]
+        return coords, elems, 1.0, 0.0, "none", fbar, None
+    if name == "steady_newton_3":
+        coords, elems = synth.mesh2d_square(3, 0.2, 2)
+        t = topology.build_faces(elems)
+        w = synth.stream_velocity(coords[t["face_vertices"]].mean(axis=1), seed=3)
+        modes = synth.fourier_modes(2, 1)
+        fbar = synth.element_means(lambda x: synth.fourier_force(x, modes), coords, elems, order=3)[None]
+        return coords, elems, 0.05, 0.0, "newton", fbar, w
+    raise ValueError(name)
+
+
+def gpu_setup(case, keep_bf16=False, k0=0):
+    coords, elems, nu, mu, conv, fbar, w = case
+    mesh = crhyb.cr_mesh_load(coords, elems, k0=k0, need_mis=(mu == 0.0))
+    fb = torch.from_numpy(np.ascontiguousarray(fbar)).cuda()
+    wt = torch.from_numpy(np.ascontiguousarray(w)).cuda() if w is not None else None
+    system = crhyb.cr_assemble_coupled(mesh, nu, mu, fb, conv=conv, w=wt)
+    hyb = crhyb.cr_hybridise(system, keep_fp32=True, keep_bf16=keep_bf16)
+    return mesh, system, hyb
+
+
+def oracle_hybrid(case, rhs=0, k0=0):
+    coords, elems, nu, mu, conv, fbar, w = case
+    return pipeline.hybrid(coords, elems, nu, mu, fbar[rhs], conv, w, k0=k0, method="direct")
+
+
+CASES = ["cfg1", "2d_perturbed_37", "3d_kuhn_5", "ns_newton_9", "ns_oseen_9", "steady_stokes_3", "steady_newton_3"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_topology_matches_oracle(name):
+    case = make_case(name)
+    mesh, _, _ = gpu_setup(case)
+    t = topology.build_faces(case[1])
+    assert mesh.nf == t["nf"] and mesh.nf_ext == t["n_exterior"]
+    assert np.array_equal(crhyb.cr_mesh_faces(mesh), t["face_vertices"])
+    fe, fl = crhyb.cr_mesh_face_elements(mesh)
+    assert np.array_equal(fe, t["face_elems"]) and np.array_equal(fl, t["face_local"])
+    if case[3] == 0.0:
+        assert np.array_equal(crhyb.cr_mesh_mis(mesh), topology.maximal_independent_set(t))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_element_blocks_match_oracle(name):
+    coords, elems, nu, mu, conv, fbar, w = case = make_case(name)
+    mesh = crhyb.cr_mesh_load(coords, elems, need_mis=(mu == 0.0))
+    d = coords.shape[1]
+    L = (d + 1) * d
+    nrhs = fbar.shape[0]
+    out = np.zeros((elems.shape[0], L * L + L + nrhs * L))
+    crhyb.cr_assemble_coupled(mesh, nu, mu, fbar, conv=conv, w=w, blocks_out=out)
+    topo, geom, A_K, D_K, R_K = pipeline.setup(coords, elems, nu, mu, fbar[0], conv, w)
+    A = out[:, :L * L].reshape(-1, L, L)
+    assert np.abs(A - A_K).max() <= 1e-12 * np.abs(A_K).max()
+    assert np.abs(out[:, L * L:L * L + L] - D_K).max() <= 1e-12 * np.abs(D_K).max()
+    for r in range(nrhs):
+        _, _, _, _, Rr = pipeline.setup(coords, elems, nu, mu, fbar[r], conv, w)
+        got = out[:, L * L + L + r * L:L * L + L + (r + 1) * L]
+        assert np.abs(got - Rr).max() <= 1e-12 * np.abs(Rr).max()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_hybridised_system_matches_oracle(name):
+    case = make_case(name)
+    _, system, hyb = gpu_setup(case)
+    cols, vals, S = crhyb.cr_hybrid_export(hyb)
+    G = crhyb.ell_to_csr(cols, vals)
+    for r in range(system.nrhs):
+        o = oracle_hybrid(case, rhs=r)
+        Go = o["hyb"]["G"]
+        if r == 0:
+            assert abs(G - Go).max() <= 1e-12 * abs(Go).max()
+            # every ELL padding slot is zero and points at its own row
+            pad = cols[1:] == np.arange(cols.shape[1])[None, :]
+            assert np.all(vals[1:][np.broadcast_to(pad[:, None, None, :], vals[1:].shape)] == 0.0)
+        So = o["hyb"]["S"].reshape(-1, case[0].shape[1])
+        assert np.abs(S[r] - So).max() <= 1e-12 * np.abs(So).max()
+
+
+def solve_and_recover(hyb, rhs, **opts):
+    n, ne = hyb.n, hyb.mesh.ne
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve(hyb, W, rhs=rhs, **opts)
+    U = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(ne, dtype=torch.float64, device="cuda")
+    jump = crhyb.cr_recover_up(hyb, W, U, P, rhs=rhs, normalise_p=True, jump=True)
+    return st, W.cpu().numpy(), U.cpu().numpy(), P.cpu().numpy(), jump
+
+
+SOLVE_CASES = [
+    ("cfg1", dict(method="pcg", prec="fp64"), 1e-9),
+    ("cfg1", dict(method="pcg", prec="mixed"), 1e-8),
+    ("cfg1", dict(method="pcg", prec="fp64", use_graph=True), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="fp64"), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="mixed", use_graph=True), 1e-8),
+    ("2d_perturbed_37", dict(method="gmres", prec="fp64"), 1e-9),
+    ("3d_kuhn_5", dict(method="pcg", prec="fp64"), 1e-9),
+    ("3d_kuhn_5", dict(method="pcg", prec="mixed"), 1e-8),
+    ("3d_kuhn_5", dict(method="pcg", prec="mixed_bf16", inner_tol=1e-2), 1e-8),
+    ("ns_newton_9", dict(method="gmres", prec="fp64"), 1e-9),
+    ("ns_newton_9", dict(method="gmres", prec="mixed"), 1e-8),
+    ("ns_oseen_9", dict(method="gmres", prec="mixed"), 1e-8),
+    # steady (mu = 0): full GMRES (restart >= N = 42), Jacobi-GMRES(30) stagnates there
+    ("steady_stokes_3", dict(method="gmres", prec="fp64", restart=64), 1e-9),
+    ("steady_newton_3", dict(method="gmres", prec="fp64", restart=64), 1e-9),
+]
+
+
+@pytest.mark.parametrize("name,opts,tol", SOLVE_CASES, ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}-{i}"
+                                                            for i, c in enumerate(SOLVE_CASES)])
+def test_solution_matches_coupled_direct_solve(name, opts, tol):
+    case = make_case(name)
+    coords, elems, nu, mu, conv, fbar, w = case
+    _, system, hyb = gpu_setup(case, keep_bf16=opts.get("prec") == "mixed_bf16")
+    ref = pipeline.direct(coords, elems, nu, mu, fbar[0], conv, w, dense=elems.shape[0] < 3000)
+    vol = ref["geom"]["vol"]
+    st, W, U, P, jump = solve_and_recover(hyb, 0, tol=1e-13, max_iter=200000, **opts)
+    assert st["status"] == 0 and st["relres"] <= 2e-13
+    assert rel(U, ref["U"].ravel()) <= tol
+    assert rel(P, coupled.normalise_pressure(ref["P"], vol)) <= tol
+    assert jump <= 1e-8 * np.abs(U).max()
+    # discrete divergence-free element by element (Section 3.2, item 2)
+    t, g = ref["topo"], ref["geom"]
+    Ul = np.where((t["elem_face"] >= 0)[:, :, None], U.reshape(-1, coords.shape[1])[np.maximum(t["elem_face"], 0)], 0)
+    div = np.einsum("kld,kld->k", Ul, g["a"])
+    assert np.abs(div).max() <= 1e-9 * np.abs(g["a"]).max() * np.abs(U).max()
+
+
+def test_second_rhs_and_host_buffers():
+    case = make_case("2d_perturbed_37")
+    coords, elems, nu, mu, conv, fbar, w = case
+    _, system, hyb = gpu_setup(case)
+    ref = pipeline.direct(coords, elems, nu, mu, fbar[1], conv, w, dense=True)
+    n, ne = hyb.n, hyb.mesh.ne
+    W = np.zeros(n)
+    st = crhyb.cr_solve(hyb, W, rhs=1, tol=1e-13, method="pcg", prec="fp64")
+    U, P = np.zeros(n), np.zeros(ne)
+    crhyb.cr_recover_up(hyb, W, U, P, rhs=1)
+    assert st["status"] == 0
+    assert rel(U, ref["U"].ravel()) <= 1e-9
+    assert rel(P, coupled.normalise_pressure(ref["P"], ref["geom"]["vol"])) <= 1e-9
+    # warm start from the solution converges at once
+    st2 = crhyb.cr_solve(hyb, W, rhs=1, tol=1e-10, method="pcg", prec="fp64", use_x0=True)
+    assert st2["iterations"] <= 1
+
+
+def test_k0_choice_does_not_change_normalised_pressure():
+    case = make_case("cfg1")
+    _, _, h0 = gpu_setup(case, k0=0)
+    _, _, h1 = gpu_setup(case, k0=case[1].shape[0] - 1)
+    _, _, U0, P0, _ = solve_and_recover(h0, 0, tol=1e-13)
+    _, _, U1, P1, _ = solve_and_recover(h1, 0, tol=1e-13)
+    assert rel(U1, U0) <= 1e-9 and rel(P1, P0) <= 1e-9
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_constant_source_closed_form(dim):
+    """Section 4.1: a constant source gives U = 0 and P_K - P_{K_0} = f.(x_K - x_{K_0})."""
+    coords, elems = synth.mesh2d_square(11, 0.2, 3) if dim == 2 else synth.mesh3d_kuhn(3)
+    c = np.array([0.7, -1.3, 0.4][:dim])
+    fbar = np.tile(c, (elems.shape[0], 1))[None].copy()
+    mesh = crhyb.cr_mesh_load(coords, elems)
+    hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 1.0, 100.0, fbar))
+    W = np.zeros(hyb.n)
+    crhyb.cr_solve(hyb, W, tol=1e-14)
+    U, P = np.zeros(hyb.n), np.zeros(hyb.mesh.ne)
+    crhyb.cr_recover_up(hyb, W, U, P, normalise_p=False)
+    xK = coords[elems].mean(axis=1)
+    assert np.abs(U).max() <= 1e-11
+    assert np.abs(P - (xK - xK[0]) @ c).max() <= 1e-11
+
+
+def test_tiny_mesh_and_error_paths():
+    coords, elems = synth.mesh2d_square(1)          # 2 triangles, 1 interior face
+    fbar = np.ones((1, 2, 2))
+    mesh = crhyb.cr_mesh_load(coords, elems)
+    assert mesh.nf == 1
+    hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 1.0, 10.0, fbar))
+    W = np.zeros(2)
+    st = crhyb.cr_solve(hyb, W, tol=1e-14)
+    assert st["status"] == 0
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, rhs=3)
+    assert ei.value.name == "CR_ERR_ARG"
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, prec="mixed_bf16")      # BF16 values not kept
+    assert ei.value.name == "CR_ERR_ARG"
+    # iteration limit
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    W = np.zeros(hyb.n)
+    st = crhyb.cr_solve(hyb, W, tol=1e-13, max_iter=5, raise_on_error=False)
+    assert st["status"] == -4 and st["iterations"] == 5
+    # mu = 0 needs the independent set
+    with pytest.raises(crhyb.CrError):
+        crhyb.cr_assemble_coupled(mesh, 1.0, 0.0, fbar)
+
+
+def test_determinism():
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    a = solve_and_recover(hyb, 0, tol=1e-12, prec="mixed")
+    b = solve_and_recover(hyb, 0, tol=1e-12, prec="mixed")
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3]) and a[0] == b[0]

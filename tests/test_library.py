@@ -1,0 +1,57 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+entry point that include/crhyb.h declares, and rejects invalid meshes in its
+host-side topology (these paths run before any CUDA call)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2101_03777_gb300 import build, crhyb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return crhyb.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "crhyb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cr_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(crhyb.EXPORTED) == names
+
+
+@pytest.mark.parametrize("case", ["three_simplices_share_a_face", "index_out_of_range", "flat_simplex"])
+def test_invalid_meshes_are_rejected(lib, case):
+    if case == "three_simplices_share_a_face":
+        coords = np.array([[0, 0], [1, 0], [0, 1], [0, -1], [1, 1]], dtype=np.float64)
+        elems = np.array([[0, 1, 2], [0, 1, 3], [0, 1, 4]], dtype=np.int32)
+    elif case == "index_out_of_range":
+        coords = np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.float64)
+        elems = np.array([[0, 1, 2], [1, 3, 7]], dtype=np.int32)
+    else:
+        coords = np.array([[0, 0], [1, 0], [2, 0], [0, 1]], dtype=np.float64)
+        elems = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_mesh_load(coords, elems)
+    assert ei.value.name == "CR_ERR_MESH"
+
+
+def test_bad_arguments_are_rejected(lib):
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_mesh_load(np.zeros((4, 2)), np.zeros((2, 3), dtype=np.int32), k0=5)
+    assert ei.value.name == "CR_ERR_ARG"
+    rc = lib.cr_solve(None, 0, None, None, None)
+    assert rc == -1 and b"NULL" in lib.cr_last_error()
