@@ -7,11 +7,12 @@ G W = S (cr_hybridise), the Krylov solve to a relative residual of 1e-10
 (cr_solve) and the element-wise recovery of U and P (cr_recover_up).  The
 mesh topology (cr_mesh_load, host) is set up once and reported separately.
 
-Metric: time to solution (seconds per step, lower is better).  `value` is the
-FP64 Jacobi-PCG solve of the default workload (2D transient Stokes, 512x512
-squares split into 524,288 perturbed triangles, nu = 1, dt = 1e-3); the same
-steps in mixed precision (FP32 PCG inside FP64 iterative refinement) are
-reported beside it.  Each timed step is bracketed by CUDA events on the
+Metric: time to solution (seconds per step, lower is better) on the default
+workload (2D transient Stokes, 512x512 squares split into 524,288 perturbed
+triangles, nu = 1, dt = 1e-3).  `value` is the first precision of --precs
+(float-float Jacobi-PCG with FP64 reliable updates by default); every timed
+precision (native FP64, float-float, float-float with BF16 low parts, FP32
+inside FP64 refinement) is reported under "precisions" with its SpMV roofline.  Each timed step is bracketed by CUDA events on the
 caller's stream; a 512 MB buffer is written between steps to flush L2.
 
 With --gpus N > 1 (torchrun), every rank solves its own replica of the
@@ -50,11 +51,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--graph", type=int, default=0)
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--precs", default="ff,fp64,ff_bf16",
+                    help="comma-separated solve precisions to time (the first is the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=30)
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="profiling runs only: stop every solve after this many iterations (no convergence check)")
     return ap.parse_args()
 
 
@@ -72,11 +76,26 @@ def load_problem(name):
     return p, np
 
 
+PRECS = {
+    # name: (cr_solve options, matrix value bytes, vector bytes, description)
+    "fp64": (dict(prec="fp64", max_iter=200000), 8, 8, "Jacobi-PCG, native FP64"),
+    "ff": (dict(prec="ff", max_iter=200000, inner_tol=0.01), 8, 8,
+           "Jacobi-PCG in float-float (FP32 pairs, 48-bit significand) with FP64 reliable updates"),
+    "ff_bf16": (dict(prec="ff_bf16", max_iter=200000, inner_tol=0.1), 6, 8,
+                "Jacobi-PCG in float-float, G low plane in BF16 (6 B/value), FP64 reliable updates"),
+    "mixed": (dict(prec="mixed", max_iter=400000, inner_tol=1e-4), 4, 4,
+              "FP32 Jacobi-PCG restarted inside FP64 iterative refinement"),
+}
+SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
+               "mixed": "k_pcg_spmv<FP32>"}
+DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
+         "mixed": "f32 (f64 refinement)"}
+
+
 def solve_opts(prec, tol, graph, profile):
-    if prec == "fp64":
-        return dict(method="pcg", prec="fp64", tol=tol, max_iter=200000, use_graph=graph, profile=profile)
-    return dict(method="pcg", prec="mixed", tol=tol, max_iter=400000, inner_tol=1e-4, use_graph=graph,
-                profile=profile)
+    o = dict(PRECS[prec][0])
+    o.update(method="pcg", tol=tol, use_graph=graph, profile=profile)
+    return o
 
 
 # ---------------------------------------------------------------------------
@@ -220,8 +239,12 @@ def run_ours(args, rank, world):
 
     def step(prec, fb, Wt, Ut, Pt, profile=False):
         system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=w_dev)
-        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec != "fp64"), keep_bf16=False)
-        st = crhyb.cr_solve(hyb, Wt, **solve_opts(prec, args.tol, args.graph, profile))
+        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_bf16=False, keep_ff=(prec == "ff"),
+                                 keep_ff_bf16=(prec == "ff_bf16"))
+        o = solve_opts(prec, args.tol, args.graph, profile)
+        if args.max_iter:
+            o["max_iter"] = args.max_iter
+        st = crhyb.cr_solve(hyb, Wt, raise_on_error=not args.max_iter, **o)
         crhyb.cr_recover_up(hyb, Wt, Ut, Pt, normalise_p=True)
         return st
 
@@ -248,11 +271,11 @@ def run_ours(args, rank, world):
             stats.append(st)
         return times, stats
 
+    precs = [x for x in args.precs.split(",") if x]
+    head = precs[0]
     clocks = ClockSampler(dev)
     clocks.start()
-    t64, s64 = timed("fp64", True)
-    if not args.no_mixed:
-        tmx, smx = timed("mixed", True)
+    runs = {prec: timed(prec, True) for prec in precs}
     clk = clocks.stop()
 
     # end-to-end through the C-ABI with host buffers: pinned fbar in, U and P out to pinned host memory
@@ -265,7 +288,7 @@ def run_ours(args, rank, world):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step("fp64", fbar_host, Wh, Uh, Ph)
+        step(head, fbar_host, Wh, Uh, Ph)
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e.append(time.perf_counter() - t0)
@@ -276,39 +299,42 @@ def run_ours(args, rank, world):
             torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
         return float(x.item())
 
-    tts64 = agg(statistics.mean(t64))
+    def summary(prec):
+        times, stats = runs[prec]
+        tts = agg(statistics.mean(times))
+        nbytes, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, PRECS[prec][1], PRECS[prec][2])
+        nl = max(sum(s["spmv_launches"] for s in stats), 1)
+        ms = sum(s["spmv_ms"] for s in stats) / nl
+        ach = nbytes / (ms * 1e-3) / 1e9
+        return tts, {
+            "value": tts, "unit": "s", "solver": PRECS[prec][3], "iterations": stats[-1]["iterations"],
+            "outer": stats[-1]["outer"], "relres": stats[-1]["relres"],
+            "kernel_launches_per_step": int(statistics.mean(s["kernel_launches"] for s in stats)) + 4,
+            "roofline": {"kernel": SPMV_KERNEL[prec], "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None, "bytes_per_launch": nbytes,
+                         "avg_launch_ms": ms, "peak_note": peak_note, "launches_timed": nl}}
+
+    sums = {prec: summary(prec) for prec in precs}
+    tts, hs = sums[head]
     tts_e2e = agg(statistics.mean(e2e))
-    it64 = s64[-1]["iterations"]
-    bytes64, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, 8, 8)
-    spmv_ms = sum(s["spmv_ms"] for s in s64) / max(sum(s["spmv_launches"] for s in s64), 1)
-    achieved = bytes64 / (spmv_ms * 1e-3) / 1e9
     out = {
-        "metric": METRIC, "value": tts64, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tts64 * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded generators in synth/)",
+        "metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[head], "data": "synthetic (seeded generators in synth/)",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nf_int": nf, "unknowns": n,
-                   "elements": ne, "solver": "Jacobi-PCG FP64", "tol": args.tol, "iterations": it64,
-                   "relres": s64[-1]["relres"], "mesh_load_s": mesh_load_s, "l2": "512 MB flush between steps",
+                   "elements": ne, "solver": hs["solver"], "tol": args.tol, "iterations": hs["iterations"],
+                   "outer": hs["outer"], "relres": hs["relres"], "mesh_load_s": mesh_load_s,
+                   "l2": "512 MB flush between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "graph": bool(args.graph)},
-        "roofline": {"kernel": "k_pcg_spmv<FP64> (block-ELL SpMV + p.q)", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                     "bytes_per_launch": bytes64, "avg_launch_ms": spmv_ms, "peak_note": peak_note,
-                     "launches_timed": sum(s["spmv_launches"] for s in s64)},
+        "roofline": hs["roofline"],
         "e2e": {"value": tts_e2e, "unit": "s", "h2d_bytes_per_step": int(p["fbar"].nbytes),
                 "d2h_bytes_per_step": int(8 * (n + ne))},
-        "gpu_launches": int(sum(3 * s["iterations"] + 8 for s in s64) / len(s64)),
+        "gpu_launches": hs["kernel_launches_per_step"],
         "clocks": clk,
+        "precisions": {prec: sums[prec][1] for prec in precs},
     }
-    if not args.no_mixed:
-        ttsmx = agg(statistics.mean(tmx))
-        bytes32, _, _ = algorithmic_spmv_bytes(fe, nf, d, 4, 4)
-        ms32 = sum(s["spmv_ms"] for s in smx) / max(sum(s["spmv_launches"] for s in smx), 1)
-        out["mixed"] = {"value": ttsmx, "unit": "s", "speedup_vs_fp64": tts64 / ttsmx,
-                        "iterations": smx[-1]["iterations"], "outer": smx[-1]["outer"],
-                        "relres": smx[-1]["relres"],
-                        "roofline": {"kernel": "k_pcg_spmv<FP32>", "achieved": bytes32 / (ms32 * 1e-3) / 1e9,
-                                     "peak": hbm_peak, "frac": bytes32 / (ms32 * 1e-3) / 1e9 / hbm_peak,
-                                     "bytes_per_launch": bytes32, "avg_launch_ms": ms32}}
+    if "fp64" in sums and head != "fp64":
+        out["speedup_vs_fp64"] = sums["fp64"][0] / tts
     return out
 
 

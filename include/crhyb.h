@@ -81,12 +81,24 @@ typedef struct cr_params {
     double lambda_scale; /* mu = 0 only: lambda_K = lambda_scale * ||A_K||_inf on M_1 (Section 3.2, item 7); <= 0 selects 2 */
 } cr_params;
 
-enum cr_prec { CR_PREC_FP64 = 0, CR_PREC_MIXED_FP32 = 1, CR_PREC_MIXED_BF16 = 2 };
+/* Precision of the Krylov solve (every path returns an FP64 W whose FP64 residual is checked):
+ *   FP64        native FP64 iteration;
+ *   MIXED_FP32  FP32 PCG/GMRES on FP32 values of G, restarted inside FP64 iterative refinement;
+ *   MIXED_BF16  the same on BF16 values of G (kept only where the refinement still converges);
+ *   FF          float-float PCG: G = hi + lo with FP32 hi and lo planes, vectors as FP32 pairs
+ *               (about 48 significant bits), all iteration arithmetic on FP32 units, with FP64
+ *               reliable updates (the FP64 true residual, rescaled to unit norm, replaces the
+ *               iterated one each time the latter has fallen by inner_tol);
+ *   FF_BF16     the same with the low plane of G stored in BF16 (6 bytes per value). */
+enum cr_prec { CR_PREC_FP64 = 0, CR_PREC_MIXED_FP32 = 1, CR_PREC_MIXED_BF16 = 2, CR_PREC_FF = 3,
+               CR_PREC_FF_BF16 = 4 };
 enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1 };
 
 typedef struct cr_hyb_opts {
     int32_t keep_fp32;  /* also keep FP32 values of G (needed by CR_PREC_MIXED_FP32) */
     int32_t keep_bf16;  /* also keep BF16 values of G (needed by CR_PREC_MIXED_BF16) */
+    int32_t keep_lo_fp32; /* also keep the FP32 plane and the FP32 low plane G - fp32(G) (CR_PREC_FF) */
+    int32_t keep_lo_bf16; /* also keep the FP32 plane and the BF16 low plane (CR_PREC_FF_BF16) */
 } cr_hyb_opts;
 
 typedef struct cr_solve_opts {
@@ -96,7 +108,10 @@ typedef struct cr_solve_opts {
                            the recursively updated residual for plain FP64 PCG/GMRES) */
     int32_t max_iter;   /* limit on Krylov iterations (inner iterations summed for the mixed paths) */
     int32_t restart;    /* GMRES restart length m (1..CR_MAX_RESTART) */
-    double inner_tol;   /* mixed paths: relative residual of each inner FP32 solve (e.g. 1e-4) */
+    double inner_tol;   /* MIXED_*: relative residual of each inner FP32 solve (1e-4 if <= 0);
+                           FF*: residual reduction between reliable updates (if <= 0 or >= 1:
+                           0.01 for FF, 0.1 for FF_BF16, whose rounded low parts need more
+                           frequent updates) */
     int32_t max_outer;  /* mixed paths: limit on refinement steps */
     int32_t use_x0;     /* 1: W holds the initial guess on entry; 0: start from W = 0 */
     int32_t check_every;/* iterations between host convergence checks (0 selects 16) */
@@ -113,6 +128,8 @@ typedef struct cr_solve_stats {
     int32_t status;      /* CR_OK or the error code the solve returned */
     int32_t spmv_launches; /* profile = 1: SpMV launches timed */
     double spmv_ms;      /* profile = 1: their summed device time (ms) */
+    int64_t kernel_launches; /* kernels this solve launched (iterations after convergence return at once
+                                but still count) */
 } cr_solve_stats;
 
 /* ---- mesh --------------------------------------------------------------- */

@@ -24,7 +24,7 @@ CR_ERR = {
     -5: "CR_ERR_BREAKDOWN", -6: "CR_ERR_TIMEOUT", -7: "CR_ERR_CUDA", -8: "CR_ERR_OOM",
 }
 CONV = {"none": 0, "newton": 1, "oseen": 2}
-PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_bf16": 2}
+PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_bf16": 2, "ff": 3, "ff_bf16": 4}
 METHOD = {"pcg": 0, "gmres": 1}
 CR_MAX_RESTART = 64
 
@@ -48,7 +48,8 @@ class cr_params(ctypes.Structure):
 
 
 class cr_hyb_opts(ctypes.Structure):
-    _fields_ = [("keep_fp32", ctypes.c_int32), ("keep_bf16", ctypes.c_int32)]
+    _fields_ = [("keep_fp32", ctypes.c_int32), ("keep_bf16", ctypes.c_int32),
+                ("keep_lo_fp32", ctypes.c_int32), ("keep_lo_bf16", ctypes.c_int32)]
 
 
 class cr_solve_opts(ctypes.Structure):
@@ -60,7 +61,8 @@ class cr_solve_opts(ctypes.Structure):
 
 class cr_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("status", ctypes.c_int32), ("spmv_launches", ctypes.c_int32), ("spmv_ms", ctypes.c_double)]
+                ("status", ctypes.c_int32), ("spmv_launches", ctypes.c_int32), ("spmv_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p
@@ -246,9 +248,10 @@ def cr_assemble_coupled(mesh, nu, mu, fbar, conv="none", w=None, lambda_scale=0.
     return System(h, mesh, nrhs)
 
 
-def cr_hybridise(system, keep_fp32=True, keep_bf16=False):
+def cr_hybridise(system, keep_fp32=True, keep_bf16=False, keep_ff=False, keep_ff_bf16=False):
+    """G and S; keep_* select the extra value planes the low-precision solves need."""
     lib = load_library()
-    o = cr_hyb_opts(int(bool(keep_fp32)), int(bool(keep_bf16)))
+    o = cr_hyb_opts(int(bool(keep_fp32)), int(bool(keep_bf16)), int(bool(keep_ff)), int(bool(keep_ff_bf16)))
     h = _vp()
     _check(lib.cr_hybridise(system.handle, ctypes.byref(o), ctypes.byref(h)))
     return Hybrid(h, system)
@@ -266,7 +269,7 @@ def cr_hybrid_export(hyb):
     return cols, vals, S
 
 
-def make_solve_opts(method="pcg", prec="fp64", tol=1e-10, max_iter=100000, restart=30, inner_tol=1e-4,
+def make_solve_opts(method="pcg", prec="fp64", tol=1e-10, max_iter=100000, restart=30, inner_tol=0.0,
                     max_outer=60, use_x0=False, check_every=16, use_graph=False, profile=False):
     return cr_solve_opts(METHOD[method], PREC[prec], float(tol), int(max_iter), int(restart), float(inner_tol),
                          int(max_outer), int(bool(use_x0)), int(check_every), int(bool(use_graph)),
@@ -283,7 +286,7 @@ def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):
                                  ctypes.byref(st))
     stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
              "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
-             "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms}
+             "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
     if rc != CR_OK and raise_on_error:
         _check(rc)
     return stats

@@ -119,6 +119,12 @@ int ensure_workspace(cr_hybrid* h, bool gmres, int restart, int prec) {
         CR_CUDA(cudaMalloc(&h->Z64, sizeof(double) * n));
         h->ws_restart = restart;
     }
+    if ((prec == CR_PREC_FF || prec == CR_PREC_FF_BF16) && !h->xf) {
+        CR_TRY(h->arena.alloc_n(&h->xf, n));
+        CR_TRY(h->arena.alloc_n(&h->rf, n));
+        CR_TRY(h->arena.alloc_n(&h->pf, n));
+        CR_TRY(h->arena.alloc_n(&h->qf, n));
+    }
     if (gmres && prec == CR_PREC_FP64 && !h->V64)
         CR_CUDA(cudaMalloc(&h->V64, sizeof(double) * n * (h->ws_restart + 1)));
     return CR_OK;
@@ -220,8 +226,11 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
         return code;
     };
     if ((rc = h->arena.alloc_n(&h->val64, nv))) return bail(rc);
-    if (o && o->keep_fp32 && (rc = h->arena.alloc_n(&h->val32, nv))) return bail(rc);
+    const bool lo32 = o && o->keep_lo_fp32, lo16 = o && o->keep_lo_bf16;
+    if (o && (o->keep_fp32 || lo32 || lo16) && (rc = h->arena.alloc_n(&h->val32, nv))) return bail(rc);
     if (o && o->keep_bf16 && (rc = h->arena.alloc_n(&h->val16, nv))) return bail(rc);
+    if (lo32 && (rc = h->arena.alloc_n(&h->vlo32, nv))) return bail(rc);
+    if (lo16 && (rc = h->arena.alloc_n(&h->vlo16, nv))) return bail(rc);
     if ((rc = h->arena.alloc_n(&h->S, n * s->nrhs)) || (rc = h->arena.alloc_n(&h->minv64, n)) ||
         (rc = h->arena.alloc_n(&h->minv32, n)) || (rc = h->arena.alloc_n(&h->status, 1)) ||
         (rc = h->arena.alloc_n(&h->red.partial, size_t(kRedSlots) * kMaxRedBlocks)) ||
@@ -285,7 +294,8 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
     if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve: rhs out of range");
     if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve: bad method");
-    if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_MIXED_FP32 && o->prec != CR_PREC_MIXED_BF16)
+    if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_MIXED_FP32 && o->prec != CR_PREC_MIXED_BF16 &&
+        o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve: bad precision");
     if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve: tol must be > 0");
     const int restart = o->restart > 0 ? o->restart : 30;

@@ -38,6 +38,8 @@ struct Outputs {
     double* val64;
     float* val32;
     __nv_bfloat16* val16;
+    float* vlo32;
+    __nv_bfloat16* vlo16;
     double* dpart;
     double* spart;
     int32_t* status;
@@ -245,8 +247,12 @@ __device__ __forceinline__ void rhs_local(const Geom<D>& g, const Topo<D>& t, co
 
 __device__ __forceinline__ void store_val(const Outputs& o, size_t idx, double v) {
     o.val64[idx] = v;
-    if (o.val32) o.val32[idx] = __double2float_rn(v);
+    const float hi = __double2float_rn(v);
+    if (o.val32) o.val32[idx] = hi;
     if (o.val16) o.val16[idx] = __double2bfloat16(v);
+    // float-float low parts: v - hi is exact in FP64, then rounded once
+    if (o.vlo32) o.vlo32[idx] = __double2float_rn(v - double(hi));
+    if (o.vlo16) o.vlo16[idx] = __double2bfloat16(v - double(hi));
 }
 
 // lambda_K = scale * ||A_K||_inf on M_1 (Stokes: A_K = S_K (x) Id).
@@ -776,7 +782,7 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st) {
         CR_CUDA(cudaGetLastError());
         lam = h->lam;
     }
-    Outputs o{h->val64, h->val32, h->val16, h->dpart, h->spart, h->status};
+    Outputs o{h->val64, h->val32, h->val16, h->vlo32, h->vlo16, h->dpart, h->spart, h->status};
     if (s->conv != CR_CONV_NONE)
         k_condense_conv2<<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, lam, s->fbar, s->nrhs, o);
     else if (m->d == 2)

@@ -107,6 +107,8 @@ struct cr_hybrid {
     double* val64 = nullptr;
     float* val32 = nullptr;
     __nv_bfloat16* val16 = nullptr;
+    float* vlo32 = nullptr;       // float-float low part: G - val32, rounded to FP32
+    __nv_bfloat16* vlo16 = nullptr; // the same rounded to BF16
     double* S = nullptr;          // [nrhs][nf][d]
     double* minv64 = nullptr;     // [nf*d]
     float* minv32 = nullptr;
@@ -120,6 +122,7 @@ struct cr_hybrid {
     int ws_restart = 0;
     double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
     float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float2 *xf = nullptr, *rf = nullptr, *pf = nullptr, *qf = nullptr;  // float-float PCG vectors
     float* V32 = nullptr;         // GMRES basis [restart+1][N]
     double* V64 = nullptr;        // GMRES basis FP64 [restart+1][N]
     float* Z32 = nullptr;         // GMRES scratch vector
@@ -130,11 +133,13 @@ struct cr_hybrid {
     double* ualt = nullptr;       // recovery: velocity from the non-owner side
     double* stage = nullptr;      // host<->device staging
     size_t stage_bytes = 0;
-    cudaGraphExec_t graph_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    static constexpr int kGraphs = 8;   // one captured iteration chunk per solver variant
+    cudaGraphExec_t graph_exec[kGraphs] = {};
     std::vector<cudaEvent_t> prof_ev;   // profile = 1: event pairs around SpMV launches
     double prof_ms = 0.0;
     int prof_n = 0;
-    int graph_key[4] = {-1, -1, -1, -1};
+    int graph_key[kGraphs] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int64_t graph_launches[kGraphs] = {};   // kernels in each captured chunk
 };
 
 namespace crhyb {

@@ -16,9 +16,12 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "device_common.cuh"
+#include "ff.cuh"
 
 namespace crhyb {
 
@@ -35,6 +38,8 @@ struct KScal {
     int m;                                      // restart length
     int stop;                                   // the current GMRES cycle has ended
     int pad_;
+    float2 alpha_ff, beta_ff;                   // alpha and beta in float-float for the FF iteration
+    double sigma;                               // FF vectors hold sigma * (the FP64 quantities)
     double hb[CR_MAX_RESTART + 1];              // Gram-Schmidt coefficients of the current step
     double H[(CR_MAX_RESTART + 1) * CR_MAX_RESTART];
     double cs[CR_MAX_RESTART], sn[CR_MAX_RESTART], g[CR_MAX_RESTART + 1];
@@ -173,17 +178,22 @@ __global__ void __launch_bounds__(kBlock) k_pcg_dir(int64_t n, XT* __restrict__ 
 // sums rr, bb, r.M^{-1}r.  Last block:
 //   mode 0: outer residual only (orr, obb);
 //   mode 1: start of a PCG solve: rz, rr, bb, tol2 = tol^2 bb, done;
-//   mode 2: reliable update of the mixed-precision PCG: the iterated residual
-//           is replaced by the true one; beta = rz_true / rz_prev continues the
-//           same search direction; the next update is due after a reduction
-//           by `delta` or at the target (tol2 = max(delta^2 rr, (tol/2)^2 bb));
-//           conv/done when the true residual meets the tolerance.
+//   mode 2: reliable update of the float-float PCG, whose vectors carry the
+//           scale sigma (r_ff = sigma r): the new scale makes ||r_ff|| = 1;
+//           beta = r.z(true) / r.z(previous, unscaled) continues the search
+//           direction (times sigma_new / sigma_old for the rescaled p); the
+//           next update is due after a reduction by `delta` or at the target
+//           (tol2 = max(delta^2 rr, (tol/2)^2 bb), scaled); conv/done when the
+//           true residual meets the tolerance.
+//   minv32 (optional) replaces minv in r.M^{-1}r so that it matches the
+//   float-float iteration's preconditioner.
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t* __restrict__ cols,
                                                        const double* __restrict__ vals, const double* __restrict__ b,
                                                        const double* __restrict__ x, double* __restrict__ r,
                                                        float* __restrict__ r32, const double* __restrict__ minv,
-                                                       KScal* sc, RedBuf red, int mode, double tol, double delta) {
+                                                       KScal* sc, RedBuf red, int mode, double tol, double delta,
+                                                       const float* __restrict__ minv32 = nullptr) {
     double part[3] = {0.0, 0.0, 0.0};
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         double y[D];
@@ -200,7 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t
             if (r32) r32[f * D + i] = __double2float_rn(ri);
             part[0] += ri * ri;
             part[1] += bi * bi;
-            part[2] += ri * minv[f * D + i] * ri;
+            part[2] += ri * (minv32 ? double(minv32[f * D + i]) : minv[f * D + i]) * ri;
         }
     }
     double tot[3];
@@ -219,16 +229,22 @@ __global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t
                 sc->status = CR_ERR_BREAKDOWN;
             }
         } else if (mode == 2) {
-            const double target = tol * tol * tot[1];
-            sc->rr = tot[0];
-            sc->bb = tot[1];
-            sc->beta = sc->rz_prev > 0.0 ? tot[2] / sc->rz_prev : 0.0;
-            sc->rz = tot[2];
-            sc->tol2 = fmax(delta * delta * tot[0], 0.25 * target);
-            sc->conv = (tot[0] <= target) ? 1 : 0;
+            const double rr = tot[0], bb = tot[1], rz = tot[2];
+            const double target = tol * tol * bb;
+            const double s_old = sc->sigma > 0.0 ? sc->sigma : 1.0;
+            const double s_new = rr > 0.0 && isfinite(rr) ? 1.0 / sqrt(rr) : s_old;
+            const double rz_prev = sc->rz_prev / (s_old * s_old);
+            sc->bb = bb;
+            sc->beta = rz_prev > 0.0 ? rz / rz_prev * (s_new / s_old) : 0.0;
+            sc->beta_ff = ff_from_double(sc->beta);
+            sc->rz = rz * s_new * s_new;
+            sc->rr = rr * s_new * s_new;
+            sc->tol2 = fmax(delta * delta * rr, 0.25 * target) * s_new * s_new;
+            sc->sigma = s_new;
+            sc->conv = (rr <= target) ? 1 : 0;
             sc->done = sc->conv;
             sc->status = CR_OK;
-            if (!isfinite(tot[0])) {
+            if (!isfinite(rr)) {
                 sc->done = 1;
                 sc->status = CR_ERR_BREAKDOWN;
             }
@@ -282,6 +298,207 @@ __global__ void __launch_bounds__(kBlock) k_spmv64(int64_t nf, const int32_t* __
 #pragma unroll
         for (int i = 0; i < D; ++i) y[f * D + i] = v[i];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Float-float PCG kernels.  Vectors are float2 (hi, lo) per unknown; G is the
+// FP32 plane val32 (hi) plus a low plane (FP32 or BF16) holding G - hi.
+// Dot products are Dot2 sums reduced in float-float through the block and
+// across blocks; only the last block converts its totals to FP64.
+// ---------------------------------------------------------------------------
+
+// Sum NV float-float values over the grid (two-level, deterministic, like
+// grid_sum); the last block returns true with the FP64 totals in thread 0.
+template <int NV>
+__device__ __forceinline__ bool ff_grid_sum(float2 (&v)[NV], RedBuf red, double (&tot)[NV]) {
+    __shared__ float2 sh[NV * 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto warp_reduce = [&](float2 a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 b;
+            b.x = __shfl_down_sync(0xffffffffu, a.x, o);
+            b.y = __shfl_down_sync(0xffffffffu, a.y, o);
+            a = ff_add(a, b);
+        }
+        return a;
+    };
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float2 a = warp_reduce(v[k]);
+        if (lane == 0) sh[k * 32 + warp] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float2 a = warp_reduce(lane < nw ? sh[k * 32 + lane] : make_float2(0.f, 0.f));
+            if (lane == 0) reinterpret_cast<float2*>(red.partial)[k * kMaxRedBlocks + blockIdx.x] = a;
+        }
+        if (lane == 0) {
+            __threadfence();
+            const unsigned t = atomicAdd(red.count, 1u);
+            last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const float2* part = reinterpret_cast<const float2*>(red.partial);
+    float2 acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float2 a = make_float2(0.f, 0.f);
+        for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x) a = ff_add(a, __ldcg(part + k * kMaxRedBlocks + b));
+        acc[k] = warp_reduce(a);
+    }
+    __syncthreads();   // sh is reused below
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + warp] = acc[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float2 a = warp_reduce(lane < nw ? sh[k * 32 + lane] : make_float2(0.f, 0.f));
+            if (lane == 0) tot[k] = ff_to_double(a);
+        }
+        if (lane == 0) *red.count = 0u;
+    }
+    return true;
+}
+
+// y_f = sum over the 2d+1 slots of block(slot) * x[col(slot)], float-float
+template <int D, typename LT>
+__device__ __forceinline__ void ff_ell_row(int64_t f, int64_t nf, const int32_t* __restrict__ cols,
+                                           const float* __restrict__ vh, const LT* __restrict__ vl,
+                                           const float2* __restrict__ x, float2 (&y)[D]) {
+    constexpr int NS = 2 * D + 1;
+    FFAcc acc[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) acc[i].zero();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + size_t(s - 1) * nf + f));
+        float2 xv[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) xv[j] = __ldg(x + c * D + j);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const size_t idx = ((size_t(s) * D + i) * D + j) * nf + f;
+                acc[i].mad(__ldcs(vh + idx), lo_val(vl + idx), xv[j].x, xv[j].y);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i] = acc[i].result();
+}
+
+// q = G p, pq = p.q; last block: alpha = rz/pq (breakdown if pq <= 0 or NaN).
+template <int D, typename LT>
+__global__ void __launch_bounds__(kBlock) kf_spmv(int64_t nf, const int32_t* __restrict__ cols,
+                                                  const float* __restrict__ vh, const LT* __restrict__ vl,
+                                                  const float2* __restrict__ p, float2* __restrict__ q, KScal* sc,
+                                                  RedBuf red) {
+    if (sc->done) return;
+    FFAcc dot;
+    dot.zero();
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        float2 y[D];
+        ff_ell_row<D, LT>(f, nf, cols, vh, vl, p, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            q[f * D + i] = y[i];
+            const float2 pi = p[f * D + i];
+            dot.mad(pi.x, pi.y, y[i].x, y[i].y);
+        }
+    }
+    float2 part[1] = {dot.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        sc->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rz / pq;
+            sc->alpha_ff = ff_from_double(sc->alpha);
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, rz' = r.M^{-1}r, rr = r.r; last block: beta,
+// iteration count, the reliable-update target (rr <= tol2) and the limit.
+__global__ void __launch_bounds__(kBlock) kf_update(int64_t n, float2* __restrict__ x, float2* __restrict__ r,
+                                                   const float2* __restrict__ p, const float2* __restrict__ q,
+                                                   const float* __restrict__ minv, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const float2 alpha = sc->alpha_ff;
+    FFAcc rz, rr;
+    rz.zero();
+    rr.zero();
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float2 xn = ff_add(x[k], ff_mul(alpha, p[k]));
+        const float2 rn = ff_add(r[k], ff_neg(ff_mul(alpha, q[k])));
+        x[k] = xn;
+        r[k] = rn;
+        const float2 z = ff_mul1(minv[k], rn);
+        rz.mad(rn.x, rn.y, z.x, z.y);
+        rr.mad(rn.x, rn.y, rn.x, rn.y);
+    }
+    float2 part[2] = {rz.result(), rr.result()};
+    double tot[2];
+    if (ff_grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        const double rzn = tot[0];
+        sc->rz_prev = sc->rz;
+        sc->beta = rzn / sc->rz;
+        sc->beta_ff = ff_from_double(sc->beta);
+        sc->rz = rzn;
+        sc->rr = tot[1];
+        sc->it += 1;
+        if (!isfinite(tot[1])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// p = M^{-1} r + beta p   (first: p = M^{-1} r)
+__global__ void __launch_bounds__(kBlock) kf_dir(int64_t n, float2* __restrict__ p, const float2* __restrict__ r,
+                                                const float* __restrict__ minv, const KScal* sc, int first) {
+    if (sc->done) return;
+    const float2 beta = sc->beta_ff;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float2 z = ff_mul1(minv[k], r[k]);
+        p[k] = first ? z : ff_add(z, ff_mul(beta, p[k]));
+    }
+}
+
+// x64 += x_ff / sigma; x_ff = 0   (the reliable update of the iterate)
+__global__ void __launch_bounds__(kBlock) k_add_ff(int64_t n, double* __restrict__ x, float2* __restrict__ d,
+                                                  const KScal* sc) {
+    const double inv = 1.0 / sc->sigma;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] += ff_to_double(d[k]) * inv;
+        d[k] = make_float2(0.f, 0.f);
+    }
+}
+
+// r_ff = sigma r64 in float-float (after a reliable update set sigma)
+__global__ void __launch_bounds__(kBlock) k_ff_from64(int64_t n, const double* __restrict__ r, float2* __restrict__ rf,
+                                                     const KScal* sc) {
+    const double s = sc->sigma;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        rf[k] = ff_from_double(r[k] * s);
 }
 
 // ---------------------------------------------------------------------------
@@ -474,6 +691,7 @@ struct Ctx {
     int64_t nf, n;
     int d;
     bool profile;
+    int64_t launches = 0;   // kernels launched by this solve (graph replays counted per kernel)
 };
 
 int read_scal(Ctx& c) {
@@ -482,28 +700,47 @@ int read_scal(Ctx& c) {
     return CR_OK;
 }
 
+// One PCG iteration: SpMV (+ p.q), update (+ r.z, r.r), new direction.
+// e0/e1 (optional) bracket the SpMV launch for the profile mode.
 template <int D, typename VT, typename XT>
-void pcg_iteration(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q, cudaEvent_t e0 = nullptr,
-                   cudaEvent_t e1 = nullptr) {
+void pcg_iteration(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q, cudaEvent_t e0,
+                   cudaEvent_t e1) {
     const int g = grid_for(c.nf), gn = grid_for(c.n);
     if (e0) cudaEventRecord(e0, c.st);
     k_pcg_spmv<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, c.h->m->cols, vals, p, q, c.sc, c.h->red);
     if (e1) cudaEventRecord(e1, c.st);
     k_pcg_update<D, XT><<<gn, kBlock, 0, c.st>>>(c.n, x, r, p, q, minv, c.sc, c.h->red);
     k_pcg_dir<XT><<<gn, kBlock, 0, c.st>>>(c.n, p, r, minv, c.sc, 0);
+    c.launches += 3;
+}
+
+// The same iteration in float-float (values hi = val32, lo = vl).
+template <int D, typename LT>
+void ff_iteration(Ctx& c, const LT* vl, float2* x, float2* r, float2* p, float2* q, cudaEvent_t e0, cudaEvent_t e1) {
+    const int g = grid_for(c.nf), gn = grid_for(c.n);
+    if (e0) cudaEventRecord(e0, c.st);
+    kf_spmv<D, LT><<<g, kBlock, 0, c.st>>>(c.nf, c.h->m->cols, c.h->val32, vl, p, q, c.sc, c.h->red);
+    if (e1) cudaEventRecord(e1, c.st);
+    kf_update<<<gn, kBlock, 0, c.st>>>(c.n, x, r, p, q, c.h->minv32, c.sc, c.h->red);
+    kf_dir<<<gn, kBlock, 0, c.st>>>(c.n, p, r, c.h->minv32, c.sc, 0);
+    c.launches += 3;
 }
 
 // Run PCG iterations until sc->done, in chunks of `chunk` iterations,
-// replayed as a CUDA graph when asked.  Assumes x, r, p, rz, tol2 are set.
-template <int D, typename VT, typename XT>
-int pcg_loop(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q, int chunk, bool graph, int gkey) {
+// replayed as a CUDA graph when asked.  `iter(e0, e1)` launches one
+// iteration.  Assumes x, r, p, rz, tol2 are set.
+template <typename Iter>
+int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey) {
     cr_hybrid* h = c.h;
     if (graph && (h->graph_key[gkey] != chunk || !h->graph_exec[gkey])) {
         if (h->graph_exec[gkey]) { cudaGraphExecDestroy(h->graph_exec[gkey]); h->graph_exec[gkey] = nullptr; }
         cudaGraph_t gr;
+        const int64_t before = c.launches;
         CR_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < chunk; ++k) pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q);
+        for (int k = 0; k < chunk; ++k) iter(nullptr, nullptr);
         CR_CUDA(cudaStreamEndCapture(c.st, &gr));
+        h->graph_launches[gkey] = c.launches - before;
+        c.launches = before;
         cudaError_t e = cudaGraphInstantiate(&h->graph_exec[gkey], gr, 0);
         cudaGraphDestroy(gr);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
@@ -534,10 +771,11 @@ int pcg_loop(Ctx& c, const VT* vals, const XT* minv, XT* x, XT* r, XT* p, XT* q,
         it_before = c.hs->it;
         if (graph) {
             CR_CUDA(cudaGraphLaunch(h->graph_exec[gkey], c.st));
+            c.launches += h->graph_launches[gkey];
         } else {
             for (int k = 0; k < chunk; ++k) {
-                if (prof) pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]);
-                else pcg_iteration<D, VT, XT>(c, vals, minv, x, r, p, q);
+                if (prof) iter(h->prof_ev[2 * k], h->prof_ev[2 * k + 1]);
+                else iter(nullptr, nullptr);
             }
             CR_CUDA(cudaGetLastError());
         }
@@ -555,21 +793,30 @@ int gmres_loop(Ctx& c, const VT* vals, const XT* minv, const XT* b, XT* x, XT* r
     for (;;) {
         // true residual of the current iterate starts every cycle
         k_residual_w<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, h->m->cols, vals, b, x, r, c.sc);
+        ++c.launches;
         k_gm_norm_start<XT><<<gn, kBlock, 0, c.st>>>(c.n, r, c.sc, h->red);
+        ++c.launches;
         k_gm_scale_v0<XT><<<gn, kBlock, 0, c.st>>>(c.n, r, V, c.sc);
+        ++c.launches;
         CR_CUDA(cudaGetLastError());
         CR_TRY(read_scal(c));
         if (c.hs->done) break;
         const int m = c.hs->m;
         for (int j = 0; j < m; ++j) {
             k_gm_precond<D, VT, XT><<<gn, kBlock, 0, c.st>>>(c.n, V, minv, z, c.sc);
+            ++c.launches;
             k_gm_spmv<D, VT, XT><<<g, kBlock, 0, c.st>>>(c.nf, h->m->cols, vals, z, V, c.sc);
+            ++c.launches;
             for (int pass = 0; pass < 2; ++pass) {
-                for (int i0 = 0; i0 <= j; i0 += kRedSlots)
+                for (int i0 = 0; i0 <= j; i0 += kRedSlots) {
                     k_gm_dots<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, i0, c.sc, h->red);
+                    ++c.launches;
+                }
                 k_gm_orth<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc, h->red, pass);
+                ++c.launches;
             }
             k_gm_normalise<XT><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc);
+            ++c.launches;
             CR_CUDA(cudaGetLastError());
             if ((j + 1) % 8 == 0 || j + 1 == m) {
                 CR_TRY(read_scal(c));
@@ -578,7 +825,9 @@ int gmres_loop(Ctx& c, const VT* vals, const XT* minv, const XT* b, XT* x, XT* r
         }
         // x += M^{-1} V y over the steps taken in this cycle
         k_gm_solve_y<<<1, 32, 0, c.st>>>(c.sc);
+        ++c.launches;
         k_gm_update<XT><<<gn, kBlock, 0, c.st>>>(c.n, x, V, minv, c.sc);
+        ++c.launches;
         CR_CUDA(cudaGetLastError());
         CR_TRY(read_scal(c));
         if (c.hs->status != CR_OK) break;
@@ -613,53 +862,120 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     if (o->prec == CR_PREC_FP64) {
         k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, nullptr, h->minv64, c.sc,
                                                     h->red, 1, o->tol, 0.0);
+        ++c.launches;
         CR_CUDA(cudaGetLastError());
         if (o->method == CR_METHOD_PCG) {
             k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
-            CR_TRY((pcg_loop<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, chunk, graph, 0)));
+            ++c.launches;
+            auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, e0, e1);
+            };
+            CR_TRY(pcg_loop(c, iter, chunk, graph, 0));
         } else {
             CR_TRY((gmres_loop<D, double, double>(c, h->val64, h->minv64, b, h->x64, h->r64, h->V64, h->Z64)));
         }
         CR_TRY(read_scal(c));
         status = c.hs->status;
-    } else if (o->method == CR_METHOD_PCG) {
-        // FP32 (or BF16-value) PCG with reliable updates: the search direction is
-        // kept across updates; each update adds the FP32 correction to the FP64
-        // iterate and replaces the iterated residual by the FP64 true residual.
-        const bool bf = o->prec == CR_PREC_MIXED_BF16;
-        if ((bf && !h->val16) || (!bf && !h->val32))
-            return fail(CR_ERR_ARG, "cr_solve: the values for this precision were not kept by cr_hybridise");
-        const double delta = o->inner_tol > 0 ? o->inner_tol : 0.1;
-        CR_CUDA(cudaMemsetAsync(h->x32, 0, sizeof(float) * c.n, c.st));
-        k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, h->r32, h->minv64, c.sc,
-                                                    h->red, 2, o->tol, delta);
-        k_pcg_dir<float><<<gn, kBlock, 0, c.st>>>(c.n, h->p32, h->r32, h->minv32, c.sc, 1);
+    } else if (o->prec == CR_PREC_FF || o->prec == CR_PREC_FF_BF16) {
+        // Float-float PCG with reliable updates (FP32 pipes only inside the
+        // iteration).  Each time the iterated residual has fallen by `delta`,
+        // the correction is added to the FP64 iterate, the residual is
+        // replaced by the FP64 true residual b - G x (FP64 values), and the
+        // search direction is continued with beta = r.z(true) / r.z(previous).
+        if (o->method != CR_METHOD_PCG)
+            return fail(CR_ERR_ARG, "cr_solve: the float-float precisions are implemented for PCG");
+        const bool bf = o->prec == CR_PREC_FF_BF16;
+        if (!h->val32 || (bf && !h->vlo16) || (!bf && !h->vlo32))
+            return fail(CR_ERR_ARG, "cr_solve: the float-float values were not kept by cr_hybridise");
+        const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (bf ? 0.1 : 0.01);
+        const bool trace = std::getenv("CRHYB_TRACE") != nullptr;
+        c.hs->sigma = 1.0;
+        CR_CUDA(cudaMemcpyAsync(&c.sc->sigma, &c.hs->sigma, sizeof(double), cudaMemcpyHostToDevice, c.st));
+        CR_CUDA(cudaMemsetAsync(h->xf, 0, sizeof(float2) * c.n, c.st));
+        // the reliable update: r64 = b - G x64 (FP64), new scale, r_ff = sigma r64
+        auto true_residual = [&](const double* x) {
+            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x, h->r64, nullptr, h->minv64,
+                                                        c.sc, h->red, 2, o->tol, delta, h->minv32);
+            k_ff_from64<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->rf, c.sc);
+            c.launches += 2;
+        };
+        true_residual(x0);
+        kf_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, h->rf, h->minv32, c.sc, 1);
+        ++c.launches;
         CR_CUDA(cudaGetLastError());
         CR_TRY(read_scal(c));
-        double last_rr = c.hs->rr;
+        if (c.hs->status == CR_ERR_BREAKDOWN) status = CR_ERR_BREAKDOWN;
+        double last_rr = c.hs->orr;
         int it_mark = 0;
-        while (!c.hs->conv) {
-            if (bf) CR_TRY((pcg_loop<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->x32, h->r32, h->p32, h->q32, chunk, graph, 2)));
-            else CR_TRY((pcg_loop<D, float, float>(c, h->val32, h->minv32, h->x32, h->r32, h->p32, h->q32, chunk, graph, 1)));
+        auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+            if (bf) ff_iteration<D, __nv_bfloat16>(c, h->vlo16, h->xf, h->rf, h->pf, h->qf, e0, e1);
+            else ff_iteration<D, float>(c, h->vlo32, h->xf, h->rf, h->pf, h->qf, e0, e1);
+        };
+        while (status == CR_OK && !c.hs->conv) {
+            CR_TRY(pcg_loop(c, iter, chunk, graph, bf ? 4 : 3));
             CR_TRY(read_scal(c));
             const int dev_status = c.hs->status;
+            const double it_rr = c.hs->rr / (c.hs->sigma * c.hs->sigma);
             if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }
             // reliable update
-            k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
-            CR_CUDA(cudaMemsetAsync(h->x32, 0, sizeof(float) * c.n, c.st));
-            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, h->r32, h->minv64,
-                                                        c.sc, h->red, 2, o->tol, delta);
+            k_add_ff<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->xf, c.sc);
+            ++c.launches;
+            true_residual(h->x64);
             CR_CUDA(cudaGetLastError());
             CR_TRY(read_scal(c));
             ++outer;
+            if (trace)
+                std::fprintf(stderr, "[crhyb] ff update %d: it %d, iterated relres %.3e, true relres %.3e, status %d\n",
+                             outer, c.hs->it, std::sqrt(it_rr / c.hs->obb), std::sqrt(c.hs->orr / c.hs->obb),
+                             dev_status);
             it_mark = c.hs->it;
             if (c.hs->status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
             if (c.hs->conv) break;
-            if (c.hs->it >= gmax || outer >= max_outer * 16) { status = CR_ERR_NOT_CONVERGED; break; }
-            if (c.hs->rr > 100.0 * last_rr) { status = CR_ERR_BREAKDOWN; break; }   // diverging (rounded values)
-            last_rr = c.hs->rr;
-            k_pcg_dir<float><<<gn, kBlock, 0, c.st>>>(c.n, h->p32, h->r32, h->minv32, c.sc, dev_status == CR_OK ? 0 : 1);
+            if (c.hs->it >= gmax) { status = CR_ERR_NOT_CONVERGED; break; }
+            if (c.hs->orr > 100.0 * last_rr) { status = CR_ERR_BREAKDOWN; break; }   // diverging
+            last_rr = c.hs->orr;
+            kf_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, h->rf, h->minv32, c.sc, dev_status == CR_OK ? 0 : 1);
+            ++c.launches;
             CR_CUDA(cudaGetLastError());
+        }
+    } else if (o->method == CR_METHOD_PCG) {
+        // FP32 PCG (FP32 or BF16 matrix values) inside FP64 iterative
+        // refinement: r = b - G x in FP64, an inner FP32 solve G d = r to the
+        // relative residual inner_tol from d = 0, x += d; repeated until the
+        // FP64 residual meets the tolerance.
+        const bool bf = o->prec == CR_PREC_MIXED_BF16;
+        if ((bf && !h->val16) || (!bf && !h->val32))
+            return fail(CR_ERR_ARG, "cr_solve: the values for this precision were not kept by cr_hybridise");
+        const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+        auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+            if (bf) pcg_iteration<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->x32, h->r32, h->p32, h->q32, e0, e1);
+            else pcg_iteration<D, float, float>(c, h->val32, h->minv32, h->x32, h->r32, h->p32, h->q32, e0, e1);
+        };
+        double last = -1.0;
+        for (;;) {
+            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, h->r32, h->minv64,
+                                                        c.sc, h->red, 0, o->tol, 0.0);
+            ++c.launches;
+            x0 = h->x64;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            const double rel2 = c.hs->obb > 0 ? c.hs->orr / c.hs->obb : 0.0;
+            if (!std::isfinite(rel2)) { status = CR_ERR_BREAKDOWN; break; }
+            if (rel2 <= o->tol * o->tol) break;
+            if (outer >= max_outer || c.hs->it >= gmax) { status = CR_ERR_NOT_CONVERGED; break; }
+            if (last >= 0.0 && rel2 > 100.0 * last) { status = CR_ERR_BREAKDOWN; break; }   // diverging
+            last = rel2;
+            const int it_start = c.hs->it;
+            k_inner_start<float><<<gn, kBlock, 0, c.st>>>(c.n, h->x32, h->r32, h->p32, h->minv32, c.sc, h->red, itol);
+            ++c.launches;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(pcg_loop(c, iter, chunk, graph, bf ? 2 : 1));
+            CR_TRY(read_scal(c));
+            if (c.hs->status == CR_ERR_BREAKDOWN && c.hs->it == it_start) { status = CR_ERR_BREAKDOWN; break; }
+            k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
+            ++c.launches;
+            CR_CUDA(cudaGetLastError());
+            ++outer;
         }
     } else {
         // GMRES in FP32 (or BF16 values) inside FP64 iterative refinement
@@ -671,6 +987,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         for (;;) {
             k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, h->r32, h->minv64,
                                                         c.sc, h->red, 0, o->tol, 0.0);
+            ++c.launches;
             CR_CUDA(cudaGetLastError());
             CR_TRY(read_scal(c));
             const double rel2 = c.hs->obb > 0 ? c.hs->orr / c.hs->obb : 0.0;
@@ -681,6 +998,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             last = rel2;
             const int it_start = c.hs->it;
             k_inner_start<float><<<gn, kBlock, 0, c.st>>>(c.n, h->x32, h->r32, nullptr, h->minv32, c.sc, h->red, itol);
+            ++c.launches;
             CR_CUDA(cudaMemcpyAsync(h->q32, h->r32, sizeof(float) * c.n, cudaMemcpyDeviceToDevice, c.st));
             CR_CUDA(cudaGetLastError());
             if (bf) CR_TRY((gmres_loop<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->q32, h->x32, h->r32, h->V32, h->Z32)));
@@ -688,6 +1006,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             CR_TRY(read_scal(c));
             if (c.hs->status == CR_ERR_BREAKDOWN && c.hs->it == it_start) { status = CR_ERR_BREAKDOWN; break; }
             k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
+            ++c.launches;
             CR_CUDA(cudaGetLastError());
             ++outer;
         }
@@ -698,6 +1017,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     CR_CUDA(cudaMemcpyAsync(W, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
     k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, nullptr, nullptr, h->minv64, c.sc,
                                                 h->red, 0, o->tol, 0.0);
+    ++c.launches;
     CR_CUDA(cudaGetLastError());
     CR_TRY(read_scal(c));
     const double relres = c.hs->obb > 0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
@@ -713,6 +1033,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         st->status = status;
         st->spmv_launches = h->prof_n;
         st->spmv_ms = h->prof_ms;
+        st->kernel_launches = c.launches;
     }
     if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve: iteration limit reached before the tolerance");
     if (status == CR_ERR_BREAKDOWN)

@@ -59,13 +59,14 @@ def make_case(name):
     raise ValueError(name)
 
 
-def gpu_setup(case, keep_bf16=False, k0=0):
+def gpu_setup(case, keep_bf16=False, k0=0, keep_ff=True, keep_ff_bf16=True):
     coords, elems, nu, mu, conv, fbar, w = case
     mesh = crhyb.cr_mesh_load(coords, elems, k0=k0, need_mis=(mu == 0.0))
     fb = torch.from_numpy(np.ascontiguousarray(fbar)).cuda()
     wt = torch.from_numpy(np.ascontiguousarray(w)).cuda() if w is not None else None
     system = crhyb.cr_assemble_coupled(mesh, nu, mu, fb, conv=conv, w=wt)
-    hyb = crhyb.cr_hybridise(system, keep_fp32=True, keep_bf16=keep_bf16)
+    hyb = crhyb.cr_hybridise(system, keep_fp32=True, keep_bf16=keep_bf16, keep_ff=keep_ff,
+                             keep_ff_bf16=keep_ff_bf16)
     return mesh, system, hyb
 
 
@@ -146,7 +147,13 @@ SOLVE_CASES = [
     ("2d_perturbed_37", dict(method="gmres", prec="fp64"), 1e-9),
     ("3d_kuhn_5", dict(method="pcg", prec="fp64"), 1e-9),
     ("3d_kuhn_5", dict(method="pcg", prec="mixed"), 1e-8),
-    ("3d_kuhn_5", dict(method="pcg", prec="mixed_bf16", inner_tol=1e-2), 1e-8),
+    # float-float PCG with FP64 reliable updates (FP64-class accuracy)
+    ("cfg1", dict(method="pcg", prec="ff"), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="ff"), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="ff", use_graph=True), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="ff_bf16"), 1e-8),
+    ("3d_kuhn_5", dict(method="pcg", prec="ff"), 1e-9),
+    ("3d_kuhn_5", dict(method="pcg", prec="ff_bf16", use_graph=True), 1e-8),
     ("ns_newton_9", dict(method="gmres", prec="fp64"), 1e-9),
     ("ns_newton_9", dict(method="gmres", prec="mixed"), 1e-8),
     ("ns_oseen_9", dict(method="gmres", prec="mixed"), 1e-8),
@@ -174,6 +181,47 @@ def test_solution_matches_coupled_direct_solve(name, opts, tol):
     Ul = np.where((t["elem_face"] >= 0)[:, :, None], U.reshape(-1, coords.shape[1])[np.maximum(t["elem_face"], 0)], 0)
     div = np.einsum("kld,kld->k", Ul, g["a"])
     assert np.abs(div).max() <= 1e-9 * np.abs(g["a"]).max() * np.abs(U).max()
+
+
+@pytest.mark.parametrize("name", ["cfg1", "3d_kuhn_5"])
+def test_bf16_values_converge_or_report(name):
+    """BF16 values of G are kept only where the refinement still converges: the
+    solve either matches the oracle or returns a non-convergence status, never
+    a wrong answer with CR_OK."""
+    case = make_case(name)
+    coords, elems, nu, mu, conv, fbar, w = case
+    _, system, hyb = gpu_setup(case, keep_bf16=True)
+    ref = pipeline.direct(coords, elems, nu, mu, fbar[0], conv, w, dense=elems.shape[0] < 3000)
+    n = hyb.n
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve(hyb, W, tol=1e-12, max_iter=50000, method="pcg", prec="mixed_bf16", inner_tol=1e-2,
+                        raise_on_error=False)
+    if st["status"] == 0:
+        assert st["relres"] <= 1e-12
+        U = torch.zeros(n, dtype=torch.float64, device="cuda")
+        P = torch.zeros(hyb.mesh.ne, dtype=torch.float64, device="cuda")
+        crhyb.cr_recover_up(hyb, W, U, P)
+        assert rel(U.cpu().numpy(), ref["U"].ravel()) <= 1e-8
+    else:
+        assert st["status"] in (-4, -5) and st["status_name"] in ("CR_ERR_NOT_CONVERGED", "CR_ERR_BREAKDOWN")
+        assert not (st["relres"] <= 1e-12)
+
+
+def test_float_float_matches_fp64_iteration_count():
+    """The float-float iteration follows the FP64 one: FF (48-bit values) needs
+    at most a few per cent more iterations than FP64 PCG, the BF16-corrected
+    values (about 32 bits) only slightly more."""
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    it = {}
+    for prec in ("fp64", "ff", "ff_bf16"):
+        W.zero_()
+        st = crhyb.cr_solve(hyb, W, tol=1e-10, method="pcg", prec=prec)
+        assert st["status"] == 0 and st["relres"] <= 1e-10
+        it[prec] = st["iterations"]
+    assert it["ff"] <= 1.05 * it["fp64"] + 2
+    assert it["ff_bf16"] <= 1.25 * it["fp64"] + 2
 
 
 def test_second_rhs_and_host_buffers():
@@ -235,6 +283,12 @@ def test_tiny_mesh_and_error_paths():
     with pytest.raises(crhyb.CrError) as ei:
         crhyb.cr_solve(hyb, W, prec="mixed_bf16")      # BF16 values not kept
     assert ei.value.name == "CR_ERR_ARG"
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, prec="ff")              # float-float values not kept
+    assert ei.value.name == "CR_ERR_ARG"
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, prec="ff", method="gmres")
+    assert ei.value.name == "CR_ERR_ARG"
     # iteration limit
     case = make_case("2d_perturbed_37")
     _, _, hyb = gpu_setup(case)
@@ -246,9 +300,10 @@ def test_tiny_mesh_and_error_paths():
         crhyb.cr_assemble_coupled(mesh, 1.0, 0.0, fbar)
 
 
-def test_determinism():
+@pytest.mark.parametrize("prec", ["mixed", "ff"])
+def test_determinism(prec):
     case = make_case("2d_perturbed_37")
     _, _, hyb = gpu_setup(case)
-    a = solve_and_recover(hyb, 0, tol=1e-12, prec="mixed")
-    b = solve_and_recover(hyb, 0, tol=1e-12, prec="mixed")
+    a = solve_and_recover(hyb, 0, tol=1e-12, prec=prec)
+    b = solve_and_recover(hyb, 0, tol=1e-12, prec=prec)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3]) and a[0] == b[0]
