@@ -225,6 +225,43 @@ int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, 
 
 void cr_destroy_hybrid(cr_hybrid* h);
 
+/* ---- allocation-free residual ------------------------------------------- */
+
+/* The paper has no counterpart to these two entry points.  They serve
+ * callers that cannot allocate device memory: a host application whose own
+ * pool owns every allocation, code that must avoid the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause on its hot path, or a checker
+ * that must leave the device's memory exactly as it found it.
+ *
+ * cr_residual_noalloc computes r = b - G x and the squared norms
+ * norms2[0] = ||r||_2^2, norms2[1] = ||b||_2^2 for G in the block ELL layout
+ * that cr_hybrid_export writes, without allocating anything.  Its only scratch
+ * (per-tile partial sums and two counters, 262,208 bytes) is a fixed device
+ * array inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   dim     2 or 3
+ *   nf      face rows, 0 <= nf <= cr_residual_noalloc_max_rows() (4,194,304);
+ *           larger sizes fail with CR_ERR_ARG before any device work
+ *   nslot   block slots per row, 1..2*dim+1 (the export's 2*dim+1)
+ *   cols    int32 [nslot][nf] block column of each slot (slot 0 may be the row itself),
+ *           device; a column outside [0, nf) is skipped and the call fails with CR_ERR_ARG
+ *   vals    float64 [nslot][dim][dim][nf], device
+ *   b, x    float64 [nf][dim], device
+ *   r       float64 [nf][dim], device, or NULL (norms only)
+ *   norms2  float64 [2], host or device
+ *   stream  cudaStream_t (NULL = the legacy default stream); the call synchronises it
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress, once per device, with that device current); make that
+ * first call before any stream capture.  Every call shares the one scratch
+ * array, whose counters the call clears first: calls that overlap on the same
+ * GPU (from several threads or streams) race and must be serialised by the
+ * caller.  Errors: CR_ERR_ARG, CR_ERR_CUDA. */
+int cr_residual_noalloc(int dim, int64_t nf, int nslot, const int32_t* cols, const double* vals, const double* b,
+                        const double* x, double* r, double* norms2, void* stream);
+
+/* The largest nf that cr_residual_noalloc accepts (its fixed scratch capacity). */
+int64_t cr_residual_noalloc_max_rows(void);
+
 /* ---- errors ------------------------------------------------------------- */
 const char* cr_last_error(void);
 

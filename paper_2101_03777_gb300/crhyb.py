@@ -84,6 +84,8 @@ _SIGS = {
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
     "cr_recover_up": (_i32, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cr_destroy_hybrid": (None, [_vp]),
+    "cr_residual_noalloc": (_i32, [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "cr_residual_noalloc_max_rows": (_i64, []),
     "cr_last_error": (ctypes.c_char_p, []),
 }
 EXPORTED = tuple(_SIGS)
@@ -303,6 +305,29 @@ def cr_recover_up(hyb, W, U, P, rhs=0, normalise_p=True, jump=False):
                                         _ptr(U, np.float64, hyb.n, "U"), _ptr(P, np.float64, hyb.mesh.ne, "P"),
                                         int(bool(normalise_p)), ctypes.byref(j) if jump else None))
     return j.value if jump else None
+
+
+def cr_residual_noalloc_max_rows():
+    return int(load_library().cr_residual_noalloc_max_rows())
+
+
+def cr_residual_noalloc(dim, nf, cols, vals, b, x, r=None, stream=None, check_sizes=True):
+    """r = b - G x and (||r||^2, ||b||^2) without any device allocation.
+
+    For callers that cannot allocate device memory: the library's only scratch
+    is a fixed device array.  cols int32 [nslot, nf] and vals float64
+    [nslot, dim, dim, nf] in the layout of cr_hybrid_export; b, x, r float64
+    [nf*dim]; all on the device.  Returns the two squared norms."""
+    nslot = int(cols.shape[0]) if len(cols.shape) == 2 else 2 * dim + 1
+    ns = (lambda k: k) if check_sizes else (lambda k: None)
+    norms = np.zeros(2, dtype=np.float64)
+    rc = load_library().cr_residual_noalloc(
+        int(dim), int(nf), nslot, _ptr(cols, np.int32, ns(nslot * nf), "cols"),
+        _ptr(vals, np.float64, ns(nslot * dim * dim * nf), "vals"), _ptr(b, np.float64, ns(nf * dim), "b"),
+        _ptr(x, np.float64, ns(nf * dim), "x"), _ptr(r, np.float64, ns(nf * dim), "r"), norms.ctypes.data,
+        _stream_handle(stream))
+    _check(rc)
+    return float(norms[0]), float(norms[1])
 
 
 def ell_to_csr(cols, vals):
