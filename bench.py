@@ -37,6 +37,8 @@ WORKLOADS = {
     "cfg2": "2D transient Stokes, 512x512 squares -> 524,288 triangles perturbed +-0.2h, nu=1, dt=1e-3, "
             "8-mode Fourier source",
     "cfg3": "3D transient Stokes, 64^3 cubes -> 1,572,864 Kuhn tetrahedra, nu=1, dt=1e-3, Fourier source",
+    "cfg4": "batch: 64 2D transient Stokes problems on n x n squares split into perturbed triangles, n log-uniform "
+            "in [8, 256] (seed 2), 4 Fourier right-hand sides each, nu=1, dt=1e-3, one persistent batched PCG launch",
     "cfg5": "2D Navier-Stokes Newton step, 1024x1024 squares -> 2,097,152 triangles, Re=100, dt=1e-3, "
             "linearised about a seeded stream-function field",
 }
@@ -51,12 +53,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--graph", type=int, default=1, help="multi-kernel path: replay iteration chunks as graphs")
+    ap.add_argument("--persistent", type=int, default=1, help="PCG in one cooperative persistent launch")
     ap.add_argument("--precs", default="ff,fp64,ff_bf16",
                     help="comma-separated solve precisions to time (the first is the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=30)
+    ap.add_argument("--check-every", type=int, default=16,
+                    help="iterations per convergence check (persistent: x64 iterations per launch)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="profiling runs only: stop every solve after this many iterations (no convergence check)")
     return ap.parse_args()
@@ -92,9 +97,9 @@ DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-fl
          "mixed": "f32 (f64 refinement)"}
 
 
-def solve_opts(prec, tol, graph, profile):
+def solve_opts(prec, tol, graph, profile, persistent):
     o = dict(PRECS[prec][0])
-    o.update(method="pcg", tol=tol, use_graph=graph, profile=profile)
+    o.update(method="pcg", tol=tol, use_graph=graph, profile=profile, persistent=persistent)
     return o
 
 
@@ -237,11 +242,13 @@ def run_ours(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(prec, fb, Wt, Ut, Pt, profile=False):
+    def step(prec, fb, Wt, Ut, Pt, profile=False, persistent=None):
+        persistent = args.persistent if persistent is None else persistent
         system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=w_dev)
         hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_bf16=False, keep_ff=(prec == "ff"),
                                  keep_ff_bf16=(prec == "ff_bf16"))
-        o = solve_opts(prec, args.tol, args.graph, profile)
+        o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
+        o["check_every"] = args.check_every
         if args.max_iter:
             o["max_iter"] = args.max_iter
         st = crhyb.cr_solve(hyb, Wt, raise_on_error=not args.max_iter, **o)
@@ -275,8 +282,19 @@ def run_ours(args, rank, world):
     head = precs[0]
     clocks = ClockSampler(dev)
     clocks.start()
-    runs = {prec: timed(prec, True) for prec in precs}
+    runs = {prec: timed(prec, False) for prec in precs}
     clk = clocks.stop()
+    # kernel timing (outside the timed steps): one step with CUDA events around every launch of the
+    # dominant kernel, and one step of the multi-kernel path for the stand-alone SpMV
+    prof = {}
+    for prec in precs:
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        st_main = step(prec, fbar_dev, W, U, P, profile=True)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        st_spmv = step(prec, fbar_dev, W, U, P, profile=True, persistent=0)
+        prof[prec] = (st_main, st_spmv)
 
     # end-to-end through the C-ABI with host buffers: pinned fbar in, U and P out to pinned host memory
     Uh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -299,20 +317,41 @@ def run_ours(args, rank, world):
             torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
         return float(x.item())
 
+    N = n
+
     def summary(prec):
         times, stats = runs[prec]
         tts = agg(statistics.mean(times))
-        nbytes, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, PRECS[prec][1], PRECS[prec][2])
-        nl = max(sum(s["spmv_launches"] for s in stats), 1)
-        ms = sum(s["spmv_ms"] for s in stats) / nl
-        ach = nbytes / (ms * 1e-3) / 1e9
+        vb, xb = PRECS[prec][1], PRECS[prec][2]
+        spmv_bytes, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, vb, xb)
+        st_main, st_spmv = prof[prec]
+        # stand-alone SpMV launches of the multi-kernel path
+        nl = max(st_spmv["spmv_launches"], 1)
+        ms = st_spmv["spmv_ms"] / nl
+        spmv = {"kernel": SPMV_KERNEL[prec], "bound": "hbm", "achieved": spmv_bytes / (ms * 1e-3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "frac": spmv_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                "bytes_per_launch": spmv_bytes, "avg_launch_ms": ms, "launches_timed": nl, "peak_note": peak_note}
+        if args.persistent:
+            # the persistent PCG kernel: per iteration the SpMV plus the vector phases
+            # (x, r, p, q read and x, r, p, q written as the algorithm states: 11 vector passes,
+            # and the preconditioner read twice)
+            mb = 4 if prec != "fp64" else 8
+            it_bytes = spmv_bytes + 9 * N * xb + 2 * N * mb
+            piters = max(st_main["spmv_launches"], 1)
+            kms = st_main["spmv_ms"]
+            ach = it_bytes * piters / (kms * 1e-3) / 1e9
+            roof = {"kernel": f"k_pcg_persist<{PRECS[prec][0]['prec']}> (SpMV + update + direction phases)",
+                    "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None, "bytes_per_iteration": it_bytes, "iterations_timed": piters,
+                    "bytes_per_launch": it_bytes * piters / max(st_main["kernel_launches"] - 1, 1),
+                    "avg_launch_ms": kms / max(st_main["kernel_launches"] - 1, 1), "peak_note": peak_note}
+        else:
+            roof = dict(spmv, traffic=None)
         return tts, {
             "value": tts, "unit": "s", "solver": PRECS[prec][3], "iterations": stats[-1]["iterations"],
             "outer": stats[-1]["outer"], "relres": stats[-1]["relres"],
             "kernel_launches_per_step": int(statistics.mean(s["kernel_launches"] for s in stats)) + 4,
-            "roofline": {"kernel": SPMV_KERNEL[prec], "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None, "bytes_per_launch": nbytes,
-                         "avg_launch_ms": ms, "peak_note": peak_note, "launches_timed": nl}}
+            "roofline": roof, "spmv": spmv}
 
     sums = {prec: summary(prec) for prec in precs}
     tts, hs = sums[head]
@@ -325,7 +364,8 @@ def run_ours(args, rank, world):
                    "elements": ne, "solver": hs["solver"], "tol": args.tol, "iterations": hs["iterations"],
                    "outer": hs["outer"], "relres": hs["relres"], "mesh_load_s": mesh_load_s,
                    "l2": "512 MB flush between steps",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "graph": bool(args.graph)},
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "graph": bool(args.graph),
+                   "persistent": bool(args.persistent)},
         "roofline": hs["roofline"],
         "e2e": {"value": tts_e2e, "unit": "s", "h2d_bytes_per_step": int(p["fbar"].nbytes),
                 "d2h_bytes_per_step": int(8 * (n + ne))},
@@ -336,6 +376,111 @@ def run_ours(args, rank, world):
     if "fp64" in sums and head != "fp64":
         out["speedup_vs_fp64"] = sums["fp64"][0] / tts
     return out
+
+
+def run_batch(args, rank, world):
+    """cfg4: every step hybridises the 64 problems, solves their 256 (problem, rhs)
+    pairs in one batched persistent PCG and recovers U and P of every pair."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2101_03777_gb300 import build, crhyb
+
+    build.build_library()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    prec = [x for x in args.precs.split(",") if x][0]
+    probs = synth.batch_problems(count=64, nrhs=4, lo=8, hi=256, seed=2)
+    meshes = [crhyb.cr_mesh_load(q["coords"], q["elems"]) for q in probs]
+    fb_host = [torch.from_numpy(q["fbar"]).pin_memory() for q in probs]
+    fb_dev = [f.cuda() for f in fb_host]
+    ns = [m.nf * m.dim for m in meshes]
+    Ws = [torch.zeros(4 * n, dtype=torch.float64, device="cuda") for n in ns]
+    Us = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in ns]
+    Ps = [torch.zeros(m.ne, dtype=torch.float64, device="cuda") for m in meshes]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    keep = dict(keep_fp32=False, keep_ff=(prec == "ff"), keep_ff_bf16=(prec == "ff_bf16"))
+    tuned = {"bps": 0, "tune": None}
+
+    def step(fbs, profile=False):
+        hybs = [crhyb.cr_hybridise(crhyb.cr_assemble_coupled(m, q["nu"], q["mu"], f), **keep)
+                for m, q, f in zip(meshes, probs, fbs)]
+        batch = crhyb.cr_batch_create(hybs, prec=prec, autotune=tuned["bps"] == 0, blocks_per_sm=tuned["bps"])
+        st = crhyb.cr_solve_batched(batch, Ws, tol=args.tol, max_iter=200000, profile=profile)
+        if tuned["bps"] == 0:
+            tuned["bps"] = batch.info()["blocks_per_sm"]
+        for h, W, U, P in zip(hybs, Ws, Us, Ps):
+            for r in range(4):
+                crhyb.cr_recover_up(h, W[r * h.n:(r + 1) * h.n], U, P, rhs=r)
+        return st, batch.info()
+
+    for _ in range(args.warmup):
+        step(fb_dev)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = step(fb_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        stats.append(st)
+    clk = clocks.stop()
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    stp, info = step(fb_dev, profile=True)
+    tts = statistics.mean(times)
+    st = stats[-1]
+    # algorithmic bytes of one batched iteration (all pairs active): per problem the SpMM over
+    # G (values once for its 4 right-hand sides) plus the vector passes of 4 right-hand sides
+    vb = {"ff": 8, "ff_bf16": 6, "fp64": 8}[prec]
+    mb = 8 if prec == "fp64" else 4
+    bytes_all = 0
+    for m in meshes:
+        fe, _ = crhyb.cr_mesh_face_elements(m)
+        sp, blocks, nnz = algorithmic_spmv_bytes(fe, m.nf, m.dim, vb, 8)
+        N = m.nf * m.dim
+        bytes_all += nnz * vb + blocks * 4 + 4 * (11 * N * 8 + 2 * N * mb)
+    iters = [s["iterations"] for s in st]
+    # the kernel runs every pair until its own convergence: weight each problem's bytes by its
+    # mean iteration count over the timed persistent launches
+    kms = stp[0]["spmv_ms"]
+    work = 0.0
+    j = 0
+    for m in meshes:
+        fe, _ = crhyb.cr_mesh_face_elements(m)
+        sp, blocks, nnz = algorithmic_spmv_bytes(fe, m.nf, m.dim, vb, 8)
+        N = m.nf * m.dim
+        its = [stp[j + r]["iterations"] for r in range(4)]
+        j += 4
+        work += max(its) * (nnz * vb + blocks * 4) + sum(its) * (11 * N * 8 + 2 * N * mb)
+    ach = work / (kms * 1e-3) / 1e9
+    return {
+        "metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prec], "data": "synthetic (seeded generators in synth/)",
+        "config": {"workload": f"cfg4: {WORKLOADS['cfg4']}", "problems": len(probs), "pairs": len(st),
+                   "unknowns_total": int(sum(ns)), "n_range": [min(q["n"] for q in probs), max(q["n"] for q in probs)],
+                   "solver": PRECS[prec][3] + ", batched persistent launch", "tol": args.tol,
+                   "iterations_min_max": [min(iters), max(iters)], "relres_max": max(s["relres"] for s in st),
+                   "tiles": info["ntiles"], "grid": info["grid"], "blocks_per_sm_autotuned": info["blocks_per_sm"],
+                   "l2": "512 MB flush between steps", "parallelism": "1 GPU"},
+        "roofline": {"kernel": f"k_pcg_persist<{prec}, 4 rhs> (batched SpMM + update + direction phases)",
+                     "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "traffic": None, "bytes_timed": work, "kernel_ms": kms, "peak_note": peak_note},
+        "gpu_launches": int(st[0]["kernel_launches"]) + 64 * 2 + 256 * 2,
+        "clocks": clk,
+    }
 
 
 def run_reference(args, rank, world):
@@ -374,7 +519,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    out = run_ours(args, rank, world)
+    out = run_batch(args, rank, world) if args.workload == "cfg4" else run_ours(args, rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             try:

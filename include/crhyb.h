@@ -117,6 +117,10 @@ typedef struct cr_solve_opts {
     int32_t check_every;/* iterations between host convergence checks (0 selects 16) */
     int32_t use_graph;  /* 1: replay the iteration chunk as a captured CUDA graph */
     int32_t profile;    /* 1: time every SpMV launch of the iteration with CUDA events (no graph) */
+    int32_t persistent; /* PCG in FP64, FF or FF_BF16 only: 1 runs the iteration in one cooperative
+                           persistent launch (grid barriers with bounded waits between its phases;
+                           up to check_every*64 iterations per launch) instead of three launches
+                           per iteration; profile and use_graph are ignored then */
 } cr_solve_opts;
 
 #define CR_MAX_RESTART 64
@@ -126,8 +130,9 @@ typedef struct cr_solve_stats {
     int32_t outer;       /* refinement steps (0 for plain FP64) */
     double relres;       /* final ||S - G W||_2 / ||S||_2 computed in FP64 from the returned W */
     int32_t status;      /* CR_OK or the error code the solve returned */
-    int32_t spmv_launches; /* profile = 1: SpMV launches timed */
-    double spmv_ms;      /* profile = 1: their summed device time (ms) */
+    int32_t spmv_launches; /* profile = 1: SpMV launches timed (persistent: PCG iterations run by
+                              the timed persistent launches) */
+    double spmv_ms;      /* profile = 1: their summed device time in ms (persistent: of those launches) */
     int64_t kernel_launches; /* kernels this solve launched (iterations after convergence return at once
                                 but still count) */
 } cr_solve_stats;
@@ -224,6 +229,46 @@ int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, 
                   double* jump);
 
 void cr_destroy_hybrid(cr_hybrid* h);
+
+/* ---- batched solves ------------------------------------------------------ */
+
+/* Many transient Stokes systems (mu > 0, b_h = 0, so G is SPD: Section 3.2,
+ * item 6) of uneven size, each with up to 4 right-hand sides (the nrhs of its
+ * cr_assemble_coupled), solved by Jacobi-PCG in one persistent cooperative
+ * launch: the face rows of all problems are cut into tiles of 256 rows that
+ * the resident blocks sweep in every phase of an iteration, and the
+ * right-hand sides of a problem share each pass over its G.  Every
+ * (problem, right-hand side) pair has its own scalars and stops on its own
+ * FP64 true residual. */
+typedef struct cr_batch cr_batch;
+
+typedef struct cr_batch_opts {
+    int32_t prec;          /* CR_PREC_FP64, CR_PREC_FF or CR_PREC_FF_BF16 (values kept by cr_hybridise) */
+    int32_t autotune;      /* 1: the first solve times 1..7 resident blocks per SM (64 iterations each,
+                              from the start state) and keeps the fastest for every later solve */
+    int32_t blocks_per_sm; /* > 0: cap on the resident blocks per SM (default: the occupancy limit) */
+} cr_batch_opts;
+
+/* Plan a batch over nprob hybridised systems of one dimension.  The handles
+ * stay owned by the caller and must outlive the batch; all work is ordered on
+ * the stream of the first problem's mesh.  The plan holds the iteration
+ * vectors of every problem.  Errors: CR_ERR_ARG (mu = 0 or a convection term,
+ * more than 4 right-hand sides, values not kept, dimensions differ), CR_ERR_OOM. */
+int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batch_opts* o, cr_batch** out);
+
+/* Launch shape of a plan (any output may be NULL). */
+int cr_batch_info(const cr_batch* b, int32_t* nsys, int32_t* ntiles, int32_t* grid, int32_t* blocks_per_sm);
+
+/* Solve every (problem, right-hand side) pair.
+ *   opts  method PCG; tol, max_iter, inner_tol, use_x0 and check_every (x64 iterations
+ *         per launch) as for cr_solve; profile = 1 reports the persistent launches' time
+ *   W     nprob device pointers, W[k] float64 [nrhs_k][nf_k][dim] (initial guess on entry
+ *         if use_x0, solution on exit)
+ *   st    NULL or host [sum_k nrhs_k], pair order problem-major
+ * Returns CR_OK, or the first failing pair's status (its W holds the last iterate). */
+int cr_solve_batched(cr_batch* b, const cr_solve_opts* opts, double* const* W, cr_solve_stats* st);
+
+void cr_destroy_batch(cr_batch* b);
 
 /* ---- allocation-free residual ------------------------------------------- */
 

@@ -56,7 +56,11 @@ class cr_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+
+
+class cr_batch_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("autotune", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 class cr_solve_stats(ctypes.Structure):
@@ -84,6 +88,10 @@ _SIGS = {
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
     "cr_recover_up": (_i32, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cr_destroy_hybrid": (None, [_vp]),
+    "cr_batch_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(cr_batch_opts), ctypes.POINTER(_vp)]),
+    "cr_batch_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "cr_solve_batched": (_i32, [_vp, ctypes.POINTER(cr_solve_opts), ctypes.POINTER(_vp), ctypes.POINTER(cr_solve_stats)]),
+    "cr_destroy_batch": (None, [_vp]),
     "cr_residual_noalloc": (_i32, [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cr_residual_noalloc_max_rows": (_i64, []),
     "cr_last_error": (ctypes.c_char_p, []),
@@ -272,10 +280,10 @@ def cr_hybrid_export(hyb):
 
 
 def make_solve_opts(method="pcg", prec="fp64", tol=1e-10, max_iter=100000, restart=30, inner_tol=0.0,
-                    max_outer=60, use_x0=False, check_every=16, use_graph=False, profile=False):
+                    max_outer=60, use_x0=False, check_every=16, use_graph=False, profile=False, persistent=False):
     return cr_solve_opts(METHOD[method], PREC[prec], float(tol), int(max_iter), int(restart), float(inner_tol),
                          int(max_outer), int(bool(use_x0)), int(check_every), int(bool(use_graph)),
-                         int(bool(profile)))
+                         int(bool(profile)), int(bool(persistent)))
 
 
 def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):
@@ -305,6 +313,48 @@ def cr_recover_up(hyb, W, U, P, rhs=0, normalise_p=True, jump=False):
                                         _ptr(U, np.float64, hyb.n, "U"), _ptr(P, np.float64, hyb.mesh.ne, "P"),
                                         int(bool(normalise_p)), ctypes.byref(j) if jump else None))
     return j.value if jump else None
+
+
+class Batch:
+    """Owner of a cr_batch handle (keeps its problems alive)."""
+
+    def __init__(self, handle, probs):
+        self.handle, self.probs = handle, list(probs)
+
+    def info(self):
+        v = [_i32() for _ in range(4)]
+        _check(load_library().cr_batch_info(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("nsys", "ntiles", "grid", "blocks_per_sm"), (x.value for x in v)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _alive():
+            _lib.cr_destroy_batch(self.handle)
+            self.handle = None
+
+
+def cr_batch_create(probs, prec="ff", autotune=False, blocks_per_sm=0):
+    """Plan one persistent batched PCG over the hybridised problems `probs`."""
+    arr = (_vp * len(probs))(*[h.handle for h in probs])
+    o = cr_batch_opts(PREC[prec], int(bool(autotune)), int(blocks_per_sm))
+    h = _vp()
+    _check(load_library().cr_batch_create(arr, len(probs), ctypes.byref(o), ctypes.byref(h)))
+    return Batch(h, probs)
+
+
+def cr_solve_batched(batch, Ws, raise_on_error=True, **opts):
+    """Solve all (problem, rhs) pairs; Ws: one device tensor [nrhs*nf*d] per problem.
+    Returns a list of per-pair statistics (problem-major)."""
+    o = make_solve_opts(**opts)
+    npairs = sum(h.system.nrhs for h in batch.probs)
+    st = (cr_solve_stats * npairs)()
+    ptrs = (_vp * len(Ws))(*[_ptr(W, np.float64, h.system.nrhs * h.n, "W") for W, h in zip(Ws, batch.probs)])
+    rc = load_library().cr_solve_batched(batch.handle, ctypes.byref(o), ptrs, st)
+    out = [{"iterations": s.iterations, "outer": s.outer, "relres": s.relres, "status": s.status,
+            "spmv_launches": s.spmv_launches, "spmv_ms": s.spmv_ms, "kernel_launches": s.kernel_launches}
+           for s in st]
+    if rc != CR_OK and raise_on_error:
+        _check(rc)
+    return out
 
 
 def cr_residual_noalloc_max_rows():

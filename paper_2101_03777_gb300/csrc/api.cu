@@ -68,20 +68,6 @@ int ensure_stage(cr_hybrid* h, size_t bytes) {
 
 namespace {
 
-// Orders the library stream after the caller's stream on entry and the
-// caller's stream after the library stream on exit.
-struct StreamScope {
-    cr_mesh* m;
-    explicit StreamScope(cr_mesh* mm) : m(mm) {
-        cudaEventRecord(m->ev_in, m->user_stream);
-        cudaStreamWaitEvent(m->stream, m->ev_in, 0);
-    }
-    ~StreamScope() {
-        cudaEventRecord(m->ev_out, m->stream);
-        cudaStreamWaitEvent(m->user_stream, m->ev_out, 0);
-    }
-};
-
 // Copy n doubles from a host or device source into a device buffer.
 int copy_in(double* dst, const double* src, size_t n, cudaStream_t st) {
     CR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, st));
@@ -361,6 +347,7 @@ extern "C" void cr_destroy_hybrid(cr_hybrid* h) {
     // so handles may be destroyed in any order.
     for (auto& g : h->graph_exec)
         if (g) cudaGraphExecDestroy(g);
+    destroy_persistent_plans(h);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->arena.release();
     if (h->V32) cudaFree(h->V32);

@@ -140,6 +140,7 @@ struct cr_hybrid {
     int prof_n = 0;
     int graph_key[kGraphs] = {-1, -1, -1, -1, -1, -1, -1, -1};
     int64_t graph_launches[kGraphs] = {};   // kernels in each captured chunk
+    void* pplan[3] = {nullptr, nullptr, nullptr};   // persistent PCG plans (FP64, FF, FF_BF16), solve.cu
 };
 
 namespace crhyb {
@@ -151,9 +152,24 @@ int launch_recover(cr_hybrid* h, int rhs, const double* W, double* U, double* P,
                    double* jump_dev, cudaStream_t st);
 int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st);
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st);
+void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 
 // staging buffer for host arguments (api.cu)
 int ensure_stage(cr_hybrid* h, size_t bytes);
+
+// Orders the library stream after the caller's stream on entry and the
+// caller's stream after the library stream on exit.
+struct StreamScope {
+    cr_mesh* m;
+    explicit StreamScope(cr_mesh* mm) : m(mm) {
+        cudaEventRecord(m->ev_in, m->user_stream);
+        cudaStreamWaitEvent(m->stream, m->ev_in, 0);
+    }
+    ~StreamScope() {
+        cudaEventRecord(m->ev_out, m->stream);
+        cudaStreamWaitEvent(m->user_stream, m->ev_out, 0);
+    }
+};
 
 }  // namespace crhyb

@@ -1,0 +1,909 @@
+// Persistent Jacobi-PCG over a batch of hybridised systems (hybrid method,
+// step 2; Section 3.2, item 6: G is symmetric positive definite for mu > 0
+// and b_h = 0).
+//
+// One cooperative launch runs many PCG iterations for a list of systems.  A
+// system is one matrix G with up to kPMaxRhs right-hand sides, which share
+// every load of G (the SpMV is a block SpMM).  Face rows are cut into tiles of
+// one thread block each; the persistent blocks sweep the tile list in every
+// phase, and the phases of an iteration are separated by a grid barrier:
+//   P1  q = G p and p.q per right-hand side; the block that completes a
+//       system's last tile sums the tile partials in tile order and sets alpha;
+//   P2  x += alpha p, r -= alpha q, r.M^{-1}r and r.r; the same block sets beta
+//       and decides convergence (or that a reliable update is due);
+//   P3  p = M^{-1} r + beta p.
+// Reliable updates (float-float arithmetic) take three more phases:
+//   U1  x64 += x / sigma, x = 0;
+//   U2  r64 = b - G x64 in FP64 with the FP64 values; r.r, b.b, r.M^{-1}r;
+//       new scale sigma = 1/||r64||, beta continues the search direction;
+//   U3  r = sigma r64 (float-float), p = M^{-1} r + beta p.
+// The same update phases start every solve (from x64 = x0, beta = 0) and end
+// it: convergence is always decided on the FP64 true residual of the iterate.
+// In plain FP64 arithmetic U1 has nothing to do and U2 writes r itself.
+//
+// Every barrier wait is bounded: a wait that runs out sets an error flag,
+// after which every block returns; the host reports CR_ERR_TIMEOUT.  Loop
+// decisions are taken from a snapshot of the control counters that the block
+// releasing a barrier writes, so that every block takes the same branch.
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+#include "ff.cuh"
+#include "persist.h"
+
+namespace crhyb {
+namespace {
+
+constexpr int kPBlock = 256;   // rows per tile = threads per block
+constexpr long long kSpinLimit = 1ll << 22;   // bounded barrier wait (about 0.3-1 s with the sleeps)
+
+enum PMode { kModeFP64 = 0, kModeFF32 = 1, kModeFFBF16 = 2 };
+
+__device__ __forceinline__ int ld_vol(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Per-pair scalars are written during the kernel by the block that completes
+// a system's last tile: read them from L2 (the L1 of another SM may be stale).
+__device__ __forceinline__ int sc_i(const int& v) { return __ldcg(&v); }
+__device__ __forceinline__ double sc_d(const double& v) { return __ldcg(&v); }
+__device__ __forceinline__ float2 sc_f2(const float2& v) { return __ldcg(&v); }
+
+// Grid barrier with a bounded wait.  The releasing block snapshots the loop
+// control counters before it opens the barrier.  Returns false in every
+// block once any wait has run out.
+__device__ __forceinline__ bool pbar(PCtl* ctl) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* genp = &ctl->bar_gen;
+        const unsigned g = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            ctl->bar_count = 0u;
+            ctl->snap_active = ld_vol(&ctl->active);
+            ctl->snap_upd = ld_vol(&ctl->upd);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            long long n = 0;
+            while (*genp == g) {
+                if (++n > kSpinLimit) {
+                    atomicExch(&ctl->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_vol(&ctl->err)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of NV doubles over the block (thread 0 gets the totals).
+template <int NV>
+__device__ __forceinline__ void bsum(double (&v)[NV], double (&out)[NV]) {
+    __shared__ double sh[NV * 32];
+    block_sum<NV>(v, sh, out);
+}
+
+// Float-float block sum, converted to FP64 by thread 0.
+template <int NV>
+__device__ __forceinline__ void bsum_ff(float2 (&v)[NV], double (&out)[NV]) {
+    __shared__ float2 sh[NV * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto wred = [&](float2 a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 b;
+            b.x = __shfl_down_sync(0xffffffffu, a.x, o);
+            b.y = __shfl_down_sync(0xffffffffu, a.y, o);
+            a = ff_add(a, b);
+        }
+        return a;
+    };
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float2 a = wred(v[k]);
+        if (lane == 0) sh[k * 32 + warp] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float2 a = wred(lane < nw ? sh[k * 32 + lane] : make_float2(0.f, 0.f));
+            if (lane == 0) out[k] = ff_to_double(a);
+        }
+    }
+    __syncthreads();
+}
+
+// Block partials -> per-system totals.  Each block sums its rows of system s
+// (all of them, over its contiguous tile range) into mine[][]; the block that
+// delivers the system's last partial returns true, with tot[k][q] (thread 0)
+// the sum of the partials in block order: deterministic, and one atomic per
+// block and system.
+template <int R, int NQ>
+__device__ __forceinline__ bool system_flush(const PArgs& a, const PSys& S, int s, const double (&mine)[R][NQ],
+                                             double (&tot)[R][NQ]) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        double* tp = a.tpart + size_t(S.slot0 + int(blockIdx.x) - S.blk0) * kPMaxRhs * 4;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) tp[k * 4 + q] = mine[k][q];
+        __threadfence();
+        last = atomicAdd(a.syscnt + s, 1u) == unsigned(S.nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[R * NQ];
+#pragma unroll
+    for (int k = 0; k < R * NQ; ++k) acc[k] = 0.0;
+    for (int u = threadIdx.x; u < S.nblk; u += blockDim.x) {
+        const double* src = a.tpart + size_t(S.slot0 + u) * kPMaxRhs * 4;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[k * NQ + q] += __ldcg(src + k * 4 + q);
+    }
+    double out[R * NQ];
+    bsum<R * NQ>(acc, out);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) tot[k][q] = out[k * NQ + q];
+        a.syscnt[s] = 0u;
+    }
+    return true;
+}
+
+// Block sum of per-thread partials (float-float or FP64) into a [R][NQ] FP64 array.
+template <int R, int NQ, bool FF>
+__device__ __forceinline__ void block_partials(FFAcc (&af)[R][NQ], double (&ad)[R][NQ], double (&out)[R][NQ]) {
+    double flat[R * NQ];
+    if (FF) {
+        float2 v[R * NQ];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[k * NQ + q] = af[k][q].result();
+        bsum_ff<R * NQ>(v, flat);
+    } else {
+        double v[R * NQ];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[k * NQ + q] = ad[k][q];
+        bsum<R * NQ>(v, flat);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[k][q] = flat[k * NQ + q];
+}
+
+// ---- row kernels ---------------------------------------------------------
+
+// y_k = G p_k for the right-hand sides in amask, float-float (one face row).
+template <int D, int R, typename LT>
+__device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask, const float2* __restrict__ p,
+                                       float2 (&y)[R][D]) {
+    constexpr int NS = 2 * D + 1;
+    const int64_t nf = S.nf, N = nf * D;
+    const float* vh = S.vh;
+    const LT* vl = static_cast<const LT*>(S.vl);
+    FFAcc acc[R][D];
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc[k][i].zero();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + size_t(s - 1) * nf + f));
+        float h[D][D], l[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const size_t idx = ((size_t(s) * D + i) * D + j) * nf + f;
+                h[i][j] = __ldcs(vh + idx);
+                l[i][j] = lo_val(vl + idx);
+            }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!((amask >> k) & 1u)) continue;
+            float2 xv[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) xv[j] = __ldcg(p + k * N + c * D + j);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) acc[k][i].mad(h[i][j], l[i][j], xv[j].x, xv[j].y);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[k][i] = acc[k][i].result();
+}
+
+// y_k = G x_k in FP64 with the FP64 values (one face row).
+template <int D, int R>
+__device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, const double* __restrict__ x,
+                                      double (&y)[R][D]) {
+    constexpr int NS = 2 * D + 1;
+    const int64_t nf = S.nf, N = nf * D;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[k][i] = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + size_t(s - 1) * nf + f));
+        double v[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) v[i][j] = __ldcs(S.v64 + ((size_t(s) * D + i) * D + j) * nf + f);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!((amask >> k) & 1u)) continue;
+            double xv[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) xv[j] = __ldcg(x + k * N + c * D + j);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) y[k][i] = fma(v[i][j], xv[j], y[k][i]);
+        }
+    }
+}
+
+// ---- the persistent kernel -------------------------------------------------
+
+// active-pair mask of system s: pairs that are neither done nor waiting for an update
+__device__ __forceinline__ unsigned active_mask(const PArgs& a, const PSys& S, int s) {
+    unsigned m = 0;
+    for (int k = 0; k < S.R; ++k) {
+        const PScal& P = a.scal[s * kPMaxRhs + k];
+        if (!sc_i(P.done) && !sc_i(P.upd)) m |= 1u << k;
+    }
+    return m;
+}
+
+__device__ __forceinline__ unsigned update_mask(const PArgs& a, const PSys& S, int s) {
+    unsigned m = 0;
+    for (int k = 0; k < S.R; ++k)
+        if (sc_i(a.scal[s * kPMaxRhs + k].upd)) m |= 1u << k;
+    return m;
+}
+
+template <int D, int R, int MODE>
+__global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a) {
+    constexpr bool FF = MODE != kModeFP64;
+    using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float>::type;
+    PCtl* ctl = a.ctl;
+    const int t0 = int(blockIdx.x) * a.tpb, t1 = min(t0 + a.tpb, a.ntiles);
+    int piters = 0, epoch = a.epoch0;
+    bool after_update = false;
+    for (;;) {
+        const int active = ld_vol(&ctl->snap_active), upd = ld_vol(&ctl->snap_upd);
+        if (active == 0) break;
+        if (upd == 0 && piters >= a.iters) break;
+        if (upd != 0) {
+            // One update pass clears every flag it finds; a flag that survives
+            // it means a system whose tiles never ran: stop instead of looping.
+            if (after_update) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctl->err, 2);
+                break;
+            }
+            after_update = true;
+            ++epoch;
+            // ---------------- U1: x64 += x / sigma, x = 0 ----------------
+            if (FF) {
+                for (int t = t0; t < t1; ++t) {
+                    const int2 td = a.tiles[t];
+                    const PSys& S = a.sys[td.x];
+                    const int64_t N = S.nf * D;
+                    const int64_t f = td.y + threadIdx.x;
+                    if (f >= S.nf) continue;
+                    for (int k = 0; k < S.R; ++k) {
+                        const PScal& P = a.scal[td.x * kPMaxRhs + k];
+                        if (!sc_i(P.upd)) continue;
+                        const double inv = 1.0 / sc_d(P.sigma);
+                        float2* xv = static_cast<float2*>(S.x);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            const int64_t q = k * N + f * D + i;
+                            S.x64[q] += ff_to_double(xv[q]) * inv;
+                            xv[q] = make_float2(0.f, 0.f);
+                        }
+                    }
+                }
+                if (!pbar(ctl)) return;
+            }
+            // ---------------- U2: r64 = b - G x64 (FP64); r.r, b.b, r.M^{-1}r ----------------
+            {
+                int cur = -1;
+                unsigned umask = 0;
+                FFAcc af[R][3];
+                double ad[R][3];
+                auto flush = [&]() {
+                    const PSys& S = a.sys[cur];
+                    double bs[R][3], tot[R][3];
+                    block_partials<R, 3, false>(af, ad, bs);
+                    if (system_flush<R, 3>(a, S, cur, bs, tot) && threadIdx.x == 0) {
+                        for (int k = 0; k < S.R; ++k) {
+                            if (!((umask >> k) & 1u)) continue;
+                            PScal& P = a.scal[cur * kPMaxRhs + k];
+                            const double rr = tot[k][0], bb = tot[k][1], rz = tot[k][2];
+                            const double target = a.tol * a.tol * bb;
+                            P.orr = rr;
+                            P.bb = bb;
+                            P.upd = 0;
+                            const int first = sc_i(P.first);
+                            P.outer = sc_i(P.outer) + (FF && !first ? 1 : 0);
+                            atomicSub(&ctl->upd, 1);
+                            if (!isfinite(rr)) {
+                                P.status = CR_ERR_BREAKDOWN;
+                                P.done = 1;
+                                atomicSub(&ctl->active, 1);
+                                continue;
+                            }
+                            if (rr <= target) {
+                                P.conv = 1;
+                                P.done = 1;
+                                atomicSub(&ctl->active, 1);
+                                continue;
+                            }
+                            if (sc_i(P.it) >= a.max_it) {
+                                P.status = CR_ERR_NOT_CONVERGED;
+                                P.done = 1;
+                                atomicSub(&ctl->active, 1);
+                                continue;
+                            }
+                            if (FF) {
+                                const double s_old = sc_d(P.sigma), s_new = 1.0 / sqrt(rr);
+                                const double rz_prev = sc_d(P.rz_prev) / (s_old * s_old);
+                                P.beta = (first || !(rz_prev > 0.0)) ? 0.0 : rz / rz_prev * (s_new / s_old);
+                                P.rz = rz * s_new * s_new;
+                                P.rr = rr * s_new * s_new;
+                                P.tol2 = fmax(a.delta * a.delta * rr, 0.25 * target) * s_new * s_new;
+                                P.sigma = s_new;
+                            } else {   // FP64: the true residual replaces the recursive one
+                                const double rz_prev = sc_d(P.rz_prev);
+                                P.beta = (first || !(rz_prev > 0.0)) ? 0.0 : rz / rz_prev;
+                                P.rz = rz;
+                                P.rr = rr;
+                                P.tol2 = target;
+                            }
+                            P.beta_ff = ff_from_double(P.beta);
+                            P.first = 0;
+                            P.epoch = epoch;
+                        }
+                    }
+                };
+                for (int t = t0; t < t1; ++t) {
+                    const int2 td = a.tiles[t];
+                    if (td.x != cur) {
+                        if (cur >= 0 && umask) flush();
+                        cur = td.x;
+                        umask = update_mask(a, a.sys[cur], cur);
+#pragma unroll
+                        for (int k = 0; k < R; ++k)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) ad[k][q] = 0.0;
+                    }
+                    if (!umask) continue;
+                    const PSys& S = a.sys[cur];
+                    const int64_t N = S.nf * D;
+                    const int64_t f = td.y + threadIdx.x;
+                    if (f >= S.nf) continue;
+                    double y[R][D];
+                    d_row<D, R>(S, f, umask, FF ? S.x64 : static_cast<const double*>(S.x), y);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (!((umask >> k) & 1u)) continue;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            const int64_t q = k * N + f * D + i;
+                            const double bi = S.b[q];
+                            const double ri = bi - y[k][i];
+                            if (FF) S.r64[q] = ri;
+                            else static_cast<double*>(S.r)[q] = ri;
+                            const double mi = FF ? double(S.minv32[f * D + i]) : S.minv64[f * D + i];
+                            ad[k][0] += ri * ri;
+                            ad[k][1] += bi * bi;
+                            ad[k][2] += ri * mi * ri;
+                        }
+                    }
+                }
+                if (cur >= 0 && umask) flush();
+            }
+            if (!pbar(ctl)) return;
+            // ---------------- U3: r = sigma r64 (float-float); p = M^{-1} r + beta p ----------------
+            for (int t = t0; t < t1; ++t) {
+                const int2 td = a.tiles[t];
+                const PSys& S = a.sys[td.x];
+                const int64_t N = S.nf * D;
+                const int64_t f = td.y + threadIdx.x;
+                if (f >= S.nf) continue;
+                for (int k = 0; k < S.R; ++k) {
+                    const PScal& P = a.scal[td.x * kPMaxRhs + k];
+                    if (sc_i(P.epoch) != epoch || sc_i(P.done)) continue;
+                    const double beta = sc_d(P.beta), sigma = sc_d(P.sigma);
+                    const float2 beta_ff = sc_f2(P.beta_ff);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        const int64_t q = k * N + f * D + i;
+                        if (FF) {
+                            const float2 rv = ff_from_double(S.r64[q] * sigma);
+                            static_cast<float2*>(S.r)[q] = rv;
+                            const float2 z = ff_mul1(S.minv32[f * D + i], rv);
+                            float2* pv = static_cast<float2*>(S.p);
+                            pv[q] = ff_add(z, ff_mul(beta_ff, pv[q]));
+                        } else {
+                            const double z = S.minv64[f * D + i] * static_cast<double*>(S.r)[q];
+                            double* pv = static_cast<double*>(S.p);
+                            pv[q] = fma(beta, pv[q], z);
+                        }
+                    }
+                }
+            }
+            if (!pbar(ctl)) return;
+            continue;
+        }
+        // ---------------- P1: q = G p, p.q ----------------
+        {
+            int cur = -1;
+            unsigned amask = 0;
+            FFAcc af[R][1];
+            double ad[R][1];
+            auto flush = [&]() {
+                const PSys& S = a.sys[cur];
+                double bs[R][1], tot[R][1];
+                block_partials<R, 1, FF>(af, ad, bs);
+                if (system_flush<R, 1>(a, S, cur, bs, tot) && threadIdx.x == 0) {
+                    for (int k = 0; k < S.R; ++k) {
+                        if (!((amask >> k) & 1u)) continue;
+                        PScal& P = a.scal[cur * kPMaxRhs + k];
+                        const double pq = tot[k][0];
+                        if (!(pq > 0.0) || !isfinite(pq)) {
+                            P.status = CR_ERR_BREAKDOWN;
+                            P.done = 1;
+                            atomicSub(&ctl->active, 1);
+                        } else {
+                            P.alpha = sc_d(P.rz) / pq;
+                            P.alpha_ff = ff_from_double(P.alpha);
+                        }
+                    }
+                }
+            };
+            for (int t = t0; t < t1; ++t) {
+                const int2 td = a.tiles[t];
+                if (td.x != cur) {
+                    if (cur >= 0 && amask) flush();
+                    cur = td.x;
+                    amask = active_mask(a, a.sys[cur], cur);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        af[k][0].zero();
+                        ad[k][0] = 0.0;
+                    }
+                }
+                if (!amask) continue;
+                const PSys& S = a.sys[cur];
+                const int64_t N = S.nf * D;
+                const int64_t f = td.y + threadIdx.x;
+                if (f >= S.nf) continue;
+                if (FF) {
+                    float2 y[R][D];
+                    const float2* p = static_cast<const float2*>(S.p);
+                    ff_row<D, R, LT>(S, f, amask, p, y);
+                    float2* q = static_cast<float2*>(S.q);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            q[k * N + f * D + i] = y[k][i];
+                            const float2 pi = p[k * N + f * D + i];
+                            af[k][0].mad(pi.x, pi.y, y[k][i].x, y[k][i].y);
+                        }
+                    }
+                } else {
+                    double y[R][D];
+                    const double* p = static_cast<const double*>(S.p);
+                    d_row<D, R>(S, f, amask, p, y);
+                    double* q = static_cast<double*>(S.q);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            q[k * N + f * D + i] = y[k][i];
+                            ad[k][0] += p[k * N + f * D + i] * y[k][i];
+                        }
+                    }
+                }
+            }
+            if (cur >= 0 && amask) flush();
+        }
+        if (!pbar(ctl)) return;
+        // ---------------- P2: x += alpha p, r -= alpha q; r.z, r.r ----------------
+        {
+            int cur = -1;
+            unsigned amask = 0;
+            FFAcc af[R][2];
+            double ad[R][2];
+            float2 al_ff[R];
+            double al[R];
+            auto flush = [&]() {
+                const PSys& S = a.sys[cur];
+                double bs[R][2], tot[R][2];
+                block_partials<R, 2, FF>(af, ad, bs);
+                if (system_flush<R, 2>(a, S, cur, bs, tot) && threadIdx.x == 0) {
+                    for (int k = 0; k < S.R; ++k) {
+                        if (!((amask >> k) & 1u)) continue;
+                        PScal& P = a.scal[cur * kPMaxRhs + k];
+                        const double rz = tot[k][0], rr = tot[k][1];
+                        const double rz_old = sc_d(P.rz);
+                        P.rz_prev = rz_old;
+                        P.beta = rz / rz_old;
+                        P.beta_ff = ff_from_double(P.beta);
+                        P.rz = rz;
+                        P.rr = rr;
+                        const int it = sc_i(P.it) + 1;
+                        P.it = it;
+                        if (!isfinite(rr)) {
+                            P.status = CR_ERR_BREAKDOWN;
+                            P.done = 1;
+                            atomicSub(&ctl->active, 1);
+                        } else if (rr <= sc_d(P.tol2) || it >= a.max_it) {
+                            // the iterated residual reached this update's target (float-float),
+                            // or the tolerance (FP64), or the limit: the true residual of the
+                            // iterate decides in the update phases
+                            P.upd = 1;
+                            atomicAdd(&ctl->upd, 1);
+                        }
+                    }
+                }
+            };
+            for (int t = t0; t < t1; ++t) {
+                const int2 td = a.tiles[t];
+                if (td.x != cur) {
+                    if (cur >= 0 && amask) flush();
+                    cur = td.x;
+                    const PSys& S0 = a.sys[cur];
+                    amask = active_mask(a, S0, cur);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        af[k][0].zero();
+                        af[k][1].zero();
+                        ad[k][0] = ad[k][1] = 0.0;
+                        if (k < S0.R) {
+                            al_ff[k] = sc_f2(a.scal[cur * kPMaxRhs + k].alpha_ff);
+                            al[k] = sc_d(a.scal[cur * kPMaxRhs + k].alpha);
+                        }
+                    }
+                }
+                if (!amask) continue;
+                const PSys& S = a.sys[cur];
+                const int64_t N = S.nf * D;
+                const int64_t f = td.y + threadIdx.x;
+                if (f >= S.nf) continue;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        const int64_t o = k * N + f * D + i;
+                        if (FF) {
+                            float2* x = static_cast<float2*>(S.x);
+                            float2* r = static_cast<float2*>(S.r);
+                            const float2* p = static_cast<const float2*>(S.p);
+                            const float2* q = static_cast<const float2*>(S.q);
+                            x[o] = ff_add(x[o], ff_mul(al_ff[k], p[o]));
+                            const float2 rn = ff_add(r[o], ff_neg(ff_mul(al_ff[k], q[o])));
+                            r[o] = rn;
+                            const float2 z = ff_mul1(S.minv32[f * D + i], rn);
+                            af[k][0].mad(rn.x, rn.y, z.x, z.y);
+                            af[k][1].mad(rn.x, rn.y, rn.x, rn.y);
+                        } else {
+                            double* x = static_cast<double*>(S.x);
+                            double* r = static_cast<double*>(S.r);
+                            const double* p = static_cast<const double*>(S.p);
+                            const double* q = static_cast<const double*>(S.q);
+                            x[o] = fma(al[k], p[o], x[o]);
+                            const double rn = fma(-al[k], q[o], r[o]);
+                            r[o] = rn;
+                            ad[k][0] += rn * S.minv64[f * D + i] * rn;
+                            ad[k][1] += rn * rn;
+                        }
+                    }
+                }
+            }
+            if (cur >= 0 && amask) flush();
+        }
+        if (!pbar(ctl)) return;
+        // ---------------- P3: p = M^{-1} r + beta p ----------------
+        {
+            int cur = -1;
+            unsigned amask = 0;
+            float2 be_ff[R];
+            double be[R];
+            for (int t = t0; t < t1; ++t) {
+                const int2 td = a.tiles[t];
+                if (td.x != cur) {
+                    cur = td.x;
+                    const PSys& S0 = a.sys[cur];
+                    amask = active_mask(a, S0, cur);
+#pragma unroll
+                    for (int k = 0; k < R; ++k)
+                        if (k < S0.R) {
+                            be_ff[k] = sc_f2(a.scal[cur * kPMaxRhs + k].beta_ff);
+                            be[k] = sc_d(a.scal[cur * kPMaxRhs + k].beta);
+                        }
+                }
+                if (!amask) continue;
+                const PSys& S = a.sys[cur];
+                const int64_t N = S.nf * D;
+                const int64_t f = td.y + threadIdx.x;
+                if (f >= S.nf) continue;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        const int64_t o = k * N + f * D + i;
+                        if (FF) {
+                            float2* pv = static_cast<float2*>(S.p);
+                            const float2 z = ff_mul1(S.minv32[f * D + i], static_cast<const float2*>(S.r)[o]);
+                            pv[o] = ff_add(z, ff_mul(be_ff[k], pv[o]));
+                        } else {
+                            double* pv = static_cast<double*>(S.p);
+                            const double z = S.minv64[f * D + i] * static_cast<const double*>(S.r)[o];
+                            pv[o] = fma(be[k], pv[o], z);
+                        }
+                    }
+                }
+            }
+        }
+        if (!pbar(ctl)) return;
+        ++piters;
+        after_update = false;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->epoch = epoch;
+        a.ctl->piters = piters;
+    }
+}
+
+template <int D, int R, int MODE>
+int launch_one(const PArgs& a, int grid, cudaStream_t st) {
+    void* args[] = {const_cast<PArgs*>(&a)};
+    CR_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_pcg_persist<D, R, MODE>), dim3(grid),
+                                        dim3(kPBlock), args, 0, st));
+    return CR_OK;
+}
+
+template <int D, int R, int MODE>
+int occupancy(int* blocks_per_sm) {
+    CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, &k_pcg_persist<D, R, MODE>, kPBlock, 0));
+    return CR_OK;
+}
+
+using LaunchFn = int (*)(const PArgs&, int, cudaStream_t);
+using OccFn = int (*)(int*);
+
+template <int D, int R>
+void pick(int mode, LaunchFn* l, OccFn* o) {
+    if (mode == kModeFP64) { *l = launch_one<D, R, kModeFP64>; *o = occupancy<D, R, kModeFP64>; }
+    else if (mode == kModeFF32) { *l = launch_one<D, R, kModeFF32>; *o = occupancy<D, R, kModeFF32>; }
+    else { *l = launch_one<D, R, kModeFFBF16>; *o = occupancy<D, R, kModeFFBF16>; }
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+
+int PersistPlan::build(const std::vector<PSys>& systems, int d_, int mode_, int blocks_per_sm_cap) {
+    release();
+    d = d_;
+    mode = mode_;
+    nsys = int(systems.size());
+    rmax = 1;
+    for (const PSys& s : systems) rmax = std::max(rmax, s.R);
+    // tiles
+    std::vector<int2> tl;
+    std::vector<PSys> sy = systems;
+    for (int s = 0; s < nsys; ++s) {
+        if (sy[s].nf <= 0 || sy[s].R < 1 || sy[s].R > kPMaxRhs)
+            return fail(CR_ERR_ARG, "persistent PCG: a system without face rows or with a bad number of right-hand sides");
+        sy[s].tile0 = int(tl.size());
+        const int64_t nt = (sy[s].nf + kPBlock - 1) / kPBlock;
+        sy[s].ntiles = int(nt);
+        for (int64_t t = 0; t < nt; ++t) tl.push_back(make_int2(s, int(t * kPBlock)));
+    }
+    ntiles = int(tl.size());
+    const int R = rmax <= 1 ? 1 : kPMaxRhs;
+    LaunchFn l = nullptr;
+    OccFn o = nullptr;
+    if (d == 2) { if (R == 1) pick<2, 1>(mode, &l, &o); else pick<2, kPMaxRhs>(mode, &l, &o); }
+    else { if (R == 1) pick<3, 1>(mode, &l, &o); else pick<3, kPMaxRhs>(mode, &l, &o); }
+    launch = reinterpret_cast<void*>(l);
+    int bps = 0;
+    CR_TRY(o(&bps));
+    if (g_sms == 0) {
+        int dev = 0;
+        CR_CUDA(cudaGetDevice(&dev));
+        CR_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (bps <= 0) return fail(CR_ERR_CUDA, "persistent PCG: the kernel does not fit on an SM");
+    if (blocks_per_sm_cap > 0) bps = std::min(bps, blocks_per_sm_cap);
+    grid = std::min(g_sms * bps, std::max(ntiles, 1));
+    blocks_per_sm = bps;
+    // contiguous tile ranges: block b sweeps tiles [b tpb, (b+1) tpb); per system the
+    // blocks that cover it and their partial-sum slots
+    tpb = (ntiles + grid - 1) / grid;
+    nslots = 0;
+    for (int s = 0; s < nsys; ++s) {
+        sy[s].blk0 = sy[s].tile0 / tpb;
+        sy[s].nblk = (sy[s].tile0 + sy[s].ntiles - 1) / tpb - sy[s].blk0 + 1;
+        sy[s].slot0 = nslots;
+        nslots += sy[s].nblk;
+    }
+    CR_TRY(arena.alloc_n(&d_sys, size_t(nsys)));
+    CR_TRY(arena.alloc_n(&d_tiles, size_t(std::max(ntiles, 1))));
+    CR_TRY(arena.alloc_n(&d_scal, size_t(nsys) * kPMaxRhs));
+    CR_TRY(arena.alloc_n(&d_tpart, size_t(std::max(nslots, 1)) * kPMaxRhs * 4));
+    CR_TRY(arena.alloc_n(&d_syscnt, size_t(nsys)));
+    CR_TRY(arena.alloc_n(&d_ctl, 1));
+    CR_CUDA(cudaMallocHost(&h_scal, sizeof(PScal) * nsys * kPMaxRhs));
+    CR_CUDA(cudaMallocHost(&h_ctl, sizeof(PCtl)));
+    CR_CUDA(cudaMallocHost(&h_sys, sizeof(PSys) * nsys));
+    CR_CUDA(cudaMemcpy(d_sys, sy.data(), sizeof(PSys) * nsys, cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMemcpy(d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMemset(d_syscnt, 0, sizeof(unsigned) * nsys));
+    sys_host = sy;
+    return CR_OK;
+}
+
+int PersistPlan::update_systems(const std::vector<PSys>& systems, cudaStream_t st) {
+    if (int(systems.size()) != nsys) return fail(CR_ERR_ARG, "persistent PCG: system count changed");
+    CR_CUDA(cudaStreamSynchronize(st));   // the staging buffer may still feed an earlier copy
+    for (int s = 0; s < nsys; ++s) {
+        PSys y = systems[s];
+        y.tile0 = sys_host[s].tile0;
+        y.ntiles = sys_host[s].ntiles;
+        y.blk0 = sys_host[s].blk0;
+        y.nblk = sys_host[s].nblk;
+        y.slot0 = sys_host[s].slot0;
+        if (y.nf != sys_host[s].nf || y.R != sys_host[s].R)
+            return fail(CR_ERR_ARG, "persistent PCG: system sizes changed");
+        sys_host[s] = y;
+        h_sys[s] = y;
+    }
+    CR_CUDA(cudaMemcpyAsync(d_sys, h_sys, sizeof(PSys) * nsys, cudaMemcpyHostToDevice, st));
+    return CR_OK;
+}
+
+void PersistPlan::release() {
+    arena.release();
+    for (cudaEvent_t& e : ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (h_scal) cudaFreeHost(h_scal);
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_sys) cudaFreeHost(h_sys);
+    h_scal = nullptr;
+    h_ctl = nullptr;
+    h_sys = nullptr;
+    d_sys = nullptr;
+    d_tiles = nullptr;
+    d_scal = nullptr;
+    d_tpart = nullptr;
+    d_syscnt = nullptr;
+    d_ctl = nullptr;
+}
+
+// Run the solve to completion: every (system, rhs) pair starts from x64
+// (FF) or x (FP64) as set by the caller.  `iters` bounds the iterations of
+// one launch; the host reads the control block between launches.
+int PersistPlan::run(double tol, double delta, int max_it, int iters, cudaStream_t st, int64_t* launches,
+                     bool profile, double* ms, int64_t* piters) {
+    if (profile && !ev[0]) {
+        CR_CUDA(cudaEventCreate(&ev[0]));
+        CR_CUDA(cudaEventCreate(&ev[1]));
+    }
+    if (ms) *ms = 0.0;
+    if (piters) *piters = 0;
+    // start: every pair has a (start) update due
+    std::vector<PScal> sc(size_t(nsys) * kPMaxRhs);
+    int npairs = 0;
+    for (int s = 0; s < nsys; ++s)
+        for (int k = 0; k < kPMaxRhs; ++k) {
+            PScal& P = sc[size_t(s) * kPMaxRhs + k];
+            std::memset(&P, 0, sizeof(PScal));
+            P.sigma = 1.0;
+            P.first = 1;
+            if (k < sys_host[s].R) {
+                P.upd = 1;
+                ++npairs;
+            } else {
+                P.done = 1;
+            }
+        }
+    PCtl c{};
+    c.active = c.snap_active = npairs;
+    c.upd = c.snap_upd = npairs;
+    std::memcpy(h_scal, sc.data(), sizeof(PScal) * sc.size());
+    std::memcpy(h_ctl, &c, sizeof(PCtl));
+    CR_CUDA(cudaMemcpyAsync(d_scal, h_scal, sizeof(PScal) * sc.size(), cudaMemcpyHostToDevice, st));
+    CR_CUDA(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(PCtl), cudaMemcpyHostToDevice, st));
+    CR_CUDA(cudaMemsetAsync(d_syscnt, 0, sizeof(unsigned) * nsys, st));
+    PArgs a{};
+    a.sys = d_sys;
+    a.tiles = d_tiles;
+    a.scal = d_scal;
+    a.tpart = d_tpart;
+    a.syscnt = d_syscnt;
+    a.ctl = d_ctl;
+    a.ntiles = ntiles;
+    a.tpb = tpb;
+    a.tol = tol;
+    a.delta = delta;
+    a.max_it = max_it;
+    a.iters = iters > 0 ? iters : 1 << 30;
+    a.epoch0 = 0;
+    LaunchFn l = reinterpret_cast<LaunchFn>(launch);
+    int idle = 0;
+    for (;;) {
+        if (profile) CR_CUDA(cudaEventRecord(ev[0], st));
+        CR_TRY(l(a, grid, st));
+        if (profile) CR_CUDA(cudaEventRecord(ev[1], st));
+        if (launches) ++*launches;
+        CR_CUDA(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(PCtl), cudaMemcpyDeviceToHost, st));
+        CR_CUDA(cudaStreamSynchronize(st));
+        if (h_ctl->err == 2) return fail(CR_ERR_ARG, "persistent PCG: a reliable update found no tiles to run on");
+        if (h_ctl->err) return fail(CR_ERR_TIMEOUT, "persistent PCG: a bounded grid-barrier wait ran out");
+        if (profile) {
+            float t = 0.f;
+            CR_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+            if (ms) *ms += t;
+            if (piters) *piters += h_ctl->piters;
+        }
+        if (h_ctl->snap_active == 0 || h_ctl->active == 0) break;
+        if (h_ctl->piters == 0 && ++idle > 2)
+            return fail(CR_ERR_BREAKDOWN, "persistent PCG: launches make no progress");
+        if (h_ctl->piters > 0) idle = 0;
+        a.epoch0 = h_ctl->epoch;
+    }
+    CR_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(PScal) * sc.size(), cudaMemcpyDeviceToHost, st));
+    CR_CUDA(cudaStreamSynchronize(st));
+    return CR_OK;
+}
+
+}  // namespace crhyb

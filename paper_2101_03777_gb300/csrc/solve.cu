@@ -22,6 +22,7 @@
 
 #include "device_common.cuh"
 #include "ff.cuh"
+#include "persist.h"
 
 namespace crhyb {
 
@@ -835,6 +836,72 @@ int gmres_loop(Ctx& c, const VT* vals, const XT* minv, const XT* b, XT* x, XT* r
     return CR_OK;
 }
 
+// PCG in one cooperative persistent launch per chunk of iterations
+// (persist.cu): FP64, or float-float with FP64 reliable updates.
+template <int D>
+int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    cr_mesh* m = h->m;
+    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D, false};
+    const int mode = o->prec == CR_PREC_FP64 ? 0 : (o->prec == CR_PREC_FF ? 1 : 2);
+    const bool ff = mode != 0;
+    if (ff && (!h->val32 || (mode == 2 && !h->vlo16) || (mode == 1 && !h->vlo32)))
+        return fail(CR_ERR_ARG, "cr_solve: the float-float values were not kept by cr_hybridise");
+    PSys sy{};
+    sy.nf = m->nf;
+    sy.R = 1;
+    sy.cols = m->cols;
+    sy.vh = h->val32;
+    sy.vl = mode == 2 ? static_cast<const void*>(h->vlo16) : static_cast<const void*>(h->vlo32);
+    sy.v64 = h->val64;
+    sy.minv32 = h->minv32;
+    sy.minv64 = h->minv64;
+    sy.b = h->S + size_t(rhs) * c.n;
+    sy.x64 = h->x64;
+    sy.r64 = h->r64;
+    if (ff) { sy.x = h->xf; sy.r = h->rf; sy.p = h->pf; sy.q = h->qf; }
+    else { sy.x = h->x64; sy.r = h->r64; sy.p = h->p64; sy.q = h->q64; }
+    PersistPlan*& plan = reinterpret_cast<PersistPlan*&>(h->pplan[mode]);
+    if (!plan) plan = new PersistPlan();
+    if (!plan->built()) CR_TRY(plan->build({sy}, D, mode, 0));
+    else CR_TRY(plan->update_systems({sy}, c.st));
+    // start: x64 = x0 (or 0), iteration vectors zero
+    if (o->use_x0) CR_CUDA(cudaMemcpyAsync(h->x64, W, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    else CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
+    if (ff) {
+        CR_CUDA(cudaMemsetAsync(h->xf, 0, sizeof(float2) * c.n, c.st));
+        CR_CUDA(cudaMemsetAsync(h->pf, 0, sizeof(float2) * c.n, c.st));
+    } else {
+        CR_CUDA(cudaMemsetAsync(h->p64, 0, sizeof(double) * c.n, c.st));
+    }
+    const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (mode == 2 ? 0.1 : 0.01);
+    const int gmax = o->max_iter > 0 ? o->max_iter : 100000;
+    const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
+    double kms = 0.0;
+    int64_t kit = 0;
+    CR_TRY(plan->run(o->tol, delta, gmax, per_launch, c.st, &c.launches, o->profile != 0, &kms, &kit));
+    const PScal& P = plan->h_scal[0];
+    int status = P.status;
+    if (status == CR_OK && !P.conv) status = CR_ERR_NOT_CONVERGED;
+    // W = x64, whose FP64 residual the last update phase computed
+    CR_CUDA(cudaMemcpyAsync(W, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    CR_CUDA(cudaStreamSynchronize(c.st));
+    const double relres = P.bb > 0 ? std::sqrt(P.orr / P.bb) : 0.0;
+    if (status == CR_OK && !(relres <= o->tol) && !(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
+    if (st) {
+        st->iterations = P.it;
+        st->outer = P.outer;
+        st->relres = relres;
+        st->status = status;
+        // profile: the persistent launches' time and the PCG iterations they ran
+        st->spmv_launches = int32_t(kit);
+        st->spmv_ms = kms;
+        st->kernel_launches = c.launches;
+    }
+    if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve: iteration limit reached before the tolerance");
+    if (status == CR_ERR_BREAKDOWN) return fail(status, "cr_solve: Krylov breakdown (p.Gp <= 0 or NaN)");
+    return status;
+}
+
 template <int D>
 int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
     cr_mesh* m = h->m;
@@ -1055,7 +1122,17 @@ int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st) {
 }
 
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {
+    if (o->persistent && o->method == CR_METHOD_PCG &&
+        (o->prec == CR_PREC_FP64 || o->prec == CR_PREC_FF || o->prec == CR_PREC_FF_BF16))
+        return h->m->d == 2 ? solve_persistent<2>(h, rhs, o, Wdev, st) : solve_persistent<3>(h, rhs, o, Wdev, st);
     return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);
+}
+
+void destroy_persistent_plans(cr_hybrid* h) {
+    for (void*& p : h->pplan) {
+        delete static_cast<PersistPlan*>(p);
+        p = nullptr;
+    }
 }
 
 }  // namespace crhyb

@@ -154,6 +154,14 @@ SOLVE_CASES = [
     ("2d_perturbed_37", dict(method="pcg", prec="ff_bf16"), 1e-8),
     ("3d_kuhn_5", dict(method="pcg", prec="ff"), 1e-9),
     ("3d_kuhn_5", dict(method="pcg", prec="ff_bf16", use_graph=True), 1e-8),
+    # the same iterations in one cooperative persistent launch
+    ("cfg1", dict(method="pcg", prec="fp64", persistent=True), 1e-9),
+    ("cfg1", dict(method="pcg", prec="ff", persistent=True), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="fp64", persistent=True), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="ff", persistent=True), 1e-9),
+    ("2d_perturbed_37", dict(method="pcg", prec="ff_bf16", persistent=True), 1e-8),
+    ("3d_kuhn_5", dict(method="pcg", prec="fp64", persistent=True), 1e-9),
+    ("3d_kuhn_5", dict(method="pcg", prec="ff", persistent=True), 1e-9),
     ("ns_newton_9", dict(method="gmres", prec="fp64"), 1e-9),
     ("ns_newton_9", dict(method="gmres", prec="mixed"), 1e-8),
     ("ns_oseen_9", dict(method="gmres", prec="mixed"), 1e-8),
@@ -222,6 +230,41 @@ def test_float_float_matches_fp64_iteration_count():
         it[prec] = st["iterations"]
     assert it["ff"] <= 1.05 * it["fp64"] + 2
     assert it["ff_bf16"] <= 1.25 * it["fp64"] + 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_persistent_matches_multi_kernel_iteration(prec):
+    """One persistent launch runs the same PCG as three launches per iteration:
+    iteration counts agree to rounding (the dot products are summed in another
+    order) and so do the solutions; a small chunk forces many relaunches."""
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    W0 = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    W1 = torch.zeros_like(W0)
+    a = crhyb.cr_solve(hyb, W0, tol=1e-11, method="pcg", prec=prec)
+    b = crhyb.cr_solve(hyb, W1, tol=1e-11, method="pcg", prec=prec, persistent=True, check_every=1)
+    assert a["status"] == 0 and b["status"] == 0 and b["relres"] <= 1e-11
+    assert abs(a["iterations"] - b["iterations"]) <= 0.02 * a["iterations"] + 2
+    assert rel(W1.cpu().numpy(), W0.cpu().numpy()) <= 1e-9
+    assert b["kernel_launches"] >= b["iterations"] // 64   # 64 iterations per launch with check_every=1
+
+
+def test_persistent_tiny_mesh_limits_and_warm_start():
+    coords, elems = synth.mesh2d_square(1)          # 2 triangles, 1 interior face, one tile
+    mesh = crhyb.cr_mesh_load(coords, elems)
+    hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 1.0, 10.0, np.ones((1, 2, 2))), keep_ff=True)
+    for prec in ("fp64", "ff"):
+        W = np.zeros(2)
+        st = crhyb.cr_solve(hyb, W, tol=1e-14, prec=prec, persistent=True)
+        assert st["status"] == 0 and st["relres"] <= 1e-13
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve(hyb, W, tol=1e-13, max_iter=7, prec="fp64", persistent=True, raise_on_error=False)
+    assert st["status"] == -4 and st["iterations"] == 7
+    st = crhyb.cr_solve(hyb, W, tol=1e-11, prec="ff", persistent=True)
+    st2 = crhyb.cr_solve(hyb, W, tol=1e-10, prec="ff", persistent=True, use_x0=True)
+    assert st2["status"] == 0 and st2["iterations"] <= 1
 
 
 def test_second_rhs_and_host_buffers():
@@ -300,10 +343,10 @@ def test_tiny_mesh_and_error_paths():
         crhyb.cr_assemble_coupled(mesh, 1.0, 0.0, fbar)
 
 
-@pytest.mark.parametrize("prec", ["mixed", "ff"])
-def test_determinism(prec):
+@pytest.mark.parametrize("prec,persistent", [("mixed", False), ("ff", False), ("ff", True), ("fp64", True)])
+def test_determinism(prec, persistent):
     case = make_case("2d_perturbed_37")
     _, _, hyb = gpu_setup(case)
-    a = solve_and_recover(hyb, 0, tol=1e-12, prec=prec)
-    b = solve_and_recover(hyb, 0, tol=1e-12, prec=prec)
+    a = solve_and_recover(hyb, 0, tol=1e-12, prec=prec, persistent=persistent)
+    b = solve_and_recover(hyb, 0, tol=1e-12, prec=prec, persistent=persistent)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3]) and a[0] == b[0]
