@@ -260,8 +260,10 @@ int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batch_opts* o, 
 int cr_batch_info(const cr_batch* b, int32_t* nsys, int32_t* ntiles, int32_t* grid, int32_t* blocks_per_sm);
 
 /* Solve every (problem, right-hand side) pair.
- *   opts  method PCG; tol, max_iter, inner_tol, use_x0 and check_every (x64 iterations
- *         per launch) as for cr_solve; profile = 1 reports the persistent launches' time
+ *   opts  method PCG; tol, max_iter, inner_tol and use_x0 as for cr_solve; check_every x 8
+ *         iterations per launch (between launches the plan drops the converged problems
+ *         and spreads the others over the resident blocks); profile = 1 reports the
+ *         persistent launches' time
  *   W     nprob device pointers, W[k] float64 [nrhs_k][nf_k][dim] (initial guess on entry
  *         if use_x0, solution on exit)
  *   st    NULL or host [sum_k nrhs_k], pair order problem-major

@@ -44,7 +44,13 @@ def _stale():
 
 
 def build_library(force=False, verbose=False):
-    """Compile and link libcrhyb.so; returns its path."""
+    """Compile and link libcrhyb.so; returns its path.
+
+    CRHYB_NVCC_FLAGS (environment, optional) adds compiler flags, e.g. the -D
+    build knobs of the persistent kernel, and forces a rebuild."""
+    extra = os.environ.get("CRHYB_NVCC_FLAGS", "").split()
+    if extra:
+        force = True
     if not force and not _stale():
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
@@ -54,7 +60,7 @@ def build_library(force=False, verbose=False):
     for src in sources():
         obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))

@@ -201,7 +201,7 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
     h->s = s;
     h->m = m;
     h->nslot = 2 * d + 1;
-    const size_t nv = size_t(h->nslot) * d * d * m->nf;
+    const size_t nv = size_t(h->nslot) * d * d * m->nfp;   // sliced ELL: whole slices of 256 rows
     const size_t n = size_t(m->nf) * d;
     StreamScope scope(m);
     DevArena tmp;
@@ -231,6 +231,18 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
     if ((e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), m->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->red.count, 0, sizeof(unsigned), m->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
+    // zero the last slice of every value array: its rows beyond nf are staged, never used
+    if (m->nfp > m->nf) {
+        const size_t npl = size_t(h->nslot) * d * d, off = size_t(m->nfp - kSlice) * npl;
+        auto zero_last = [&](void* base, size_t es) {
+            if (!base) return cudaSuccess;
+            return cudaMemsetAsync(static_cast<char*>(base) + off * es, 0, npl * kSlice * es, m->stream);
+        };
+        if ((e = zero_last(h->val64, 8)) != cudaSuccess || (e = zero_last(h->val32, 4)) != cudaSuccess ||
+            (e = zero_last(h->val16, 2)) != cudaSuccess || (e = zero_last(h->vlo32, 4)) != cudaSuccess ||
+            (e = zero_last(h->vlo16, 2)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMemsetAsync"));
+    }
     if ((rc = launch_hybridise(h, m->stream))) return bail(rc);
     int32_t status = 0;
     if ((e = cudaMemcpyAsync(&status, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream)) != cudaSuccess ||
@@ -250,18 +262,27 @@ extern "C" int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals,
     const size_t nf = size_t(m->nf);
     cudaError_t e;
     if ((e = cudaStreamSynchronize(m->stream)) != cudaSuccess) return cuda_fail(e, "cr_hybrid_export");
+    // the library keeps G sliced (see internal.h); the export is plane-major with stride nf
+    const int npl = h->nslot * m->d * m->d, ncol = 2 * m->d;
     if (cols) {
-        // slot 0 is the diagonal: its column is the row itself
-        std::vector<int32_t> c0(nf);
-        for (size_t f = 0; f < nf; ++f) c0[f] = int32_t(f);
-        if ((e = cudaMemcpy(cols, c0.data(), nf * sizeof(int32_t), cudaMemcpyDefault)) != cudaSuccess ||
-            (e = cudaMemcpy(cols + nf, m->cols, size_t(2 * m->d) * nf * sizeof(int32_t), cudaMemcpyDefault)) !=
-                cudaSuccess)
+        std::vector<int32_t> sl(size_t(ncol) * m->nfp), out(size_t(h->nslot) * nf);
+        if ((e = cudaMemcpy(sl.data(), m->cols, sl.size() * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cr_hybrid_export (cols)");
+        for (size_t f = 0; f < nf; ++f) out[f] = int32_t(f);   // slot 0 is the diagonal
+        for (int q = 0; q < ncol; ++q)
+            for (size_t f = 0; f < nf; ++f) out[(q + 1) * nf + f] = sl[sell(int64_t(f), q, ncol)];
+        if ((e = cudaMemcpy(cols, out.data(), out.size() * sizeof(int32_t), cudaMemcpyDefault)) != cudaSuccess)
             return cuda_fail(e, "cr_hybrid_export (cols)");
     }
-    if (vals && (e = cudaMemcpy(vals, h->val64, size_t(h->nslot) * m->d * m->d * nf * sizeof(double),
-                                cudaMemcpyDefault)) != cudaSuccess)
-        return cuda_fail(e, "cr_hybrid_export (vals)");
+    if (vals) {
+        std::vector<double> sl(size_t(npl) * m->nfp), out(size_t(npl) * nf);
+        if ((e = cudaMemcpy(sl.data(), h->val64, sl.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cr_hybrid_export (vals)");
+        for (int q = 0; q < npl; ++q)
+            for (size_t f = 0; f < nf; ++f) out[q * nf + f] = sl[sell(int64_t(f), q, npl)];
+        if ((e = cudaMemcpy(vals, out.data(), out.size() * sizeof(double), cudaMemcpyDefault)) != cudaSuccess)
+            return cuda_fail(e, "cr_hybrid_export (vals)");
+    }
     if (S && (e = cudaMemcpy(S, h->S, size_t(h->s->nrhs) * nf * m->d * sizeof(double), cudaMemcpyDefault)) !=
                  cudaSuccess)
         return cuda_fail(e, "cr_hybrid_export (S)");

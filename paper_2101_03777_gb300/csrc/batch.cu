@@ -148,7 +148,9 @@ extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* con
     StreamScope scope(b->probs[0]->m);
     const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (b->mode == 2 ? 0.1 : 0.01);
     const int gmax = o->max_iter > 0 ? o->max_iter : 100000;
-    const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
+    // shorter launches than a single solve: between launches the plan drops the
+    // problems that have converged and spreads the rest over the resident blocks
+    const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 8;
     auto start = [&]() -> int {
         for (int k = 0; k < np; ++k) {
             const size_t len = size_t(b->nrhs[k]) * b->n[k];

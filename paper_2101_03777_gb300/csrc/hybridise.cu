@@ -40,6 +40,7 @@ struct Outputs {
     __nv_bfloat16* val16;
     float* vlo32;
     __nv_bfloat16* vlo16;
+    int npl;             // value planes of the sliced ELL: (2d+1) d^2
     double* dpart;
     double* spart;
     int32_t* status;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kElemBlock) k_condense_stokes(MeshView mv, dou
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
                         const double gv = cc * ((i == j ? L.Ti[l][m] : 0.0) - L.v[l][i] * L.v[m][j] * L.invB);
-                        store_val(o, ((size_t(slot) * D + i) * D + j) * nf + f, gv);
+                        store_val(o, sell(f, (slot * D + i) * D + j, o.npl), gv);
                     }
             }
         }
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(kElemBlock) k_condense_conv2(MeshView mv, doub
                     const int p = l * 2 + i, q = m * 2 + j;
                     const double gv = cc * (L.Ai[p][q] - L.u[p] * L.wt[q] * L.invB);
                     if (m == l) o.dpart[((size_t(s) * 2 + i) * 2 + j) * nf + f] = gv;
-                    else store_val(o, ((size_t(slot) * 2 + i) * 2 + j) * nf + f, gv);
+                    else store_val(o, sell(f, (slot * 2 + i) * 2 + j, o.npl), gv);
                 }
         }
     }
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(256) k_merge(int64_t nf, int nrhs, const doubl
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const double gv = dpart[((size_t(0) * D + i) * D + j) * nf + f] + dpart[((size_t(1) * D + i) * D + j) * nf + f];
-            store_val(o, (size_t(i) * D + j) * nf + f, gv);
+            store_val(o, sell(f, i * D + j, o.npl), gv);
             if (i == j) {
                 minv64[f * D + i] = 1.0 / gv;
                 if (minv32) minv32[f * D + i] = __double2float_rn(1.0 / gv);
@@ -782,7 +783,8 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st) {
         CR_CUDA(cudaGetLastError());
         lam = h->lam;
     }
-    Outputs o{h->val64, h->val32, h->val16, h->vlo32, h->vlo16, h->dpart, h->spart, h->status};
+    Outputs o{h->val64, h->val32, h->val16, h->vlo32, h->vlo16, h->nslot * m->d * m->d, h->dpart, h->spart,
+              h->status};
     if (s->conv != CR_CONV_NONE)
         k_condense_conv2<<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, lam, s->fbar, s->nrhs, o);
     else if (m->d == 2)

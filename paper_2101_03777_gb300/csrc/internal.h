@@ -4,15 +4,18 @@
 //   mesh    coords f64 [nv][d], elems i32 [ne][d+1], elem_face i32 [ne][d+1]
 //           (-1: exterior face), elem_side u8 [ne][d+1] (0: the simplex owns
 //           the face, C = +1; 1: C = -1), face_elems / face_local i32 [nf][2],
-//           cols i32 [2d][nf] (ELL columns of slots 1..2d).
+//           cols i32 sliced like G below, 2d planes (ELL columns of slots 1..2d).
 //   G       block ELL with NSLOT = 2d+1 slots per face row.  Slot 0 is the
 //           diagonal block; slots 1..d are the other local faces of the
 //           owner simplex of the row face, in increasing local index; slots
 //           d+1..2d those of the second simplex.  A slot whose face is
-//           exterior keeps col = row and zero values.  Values are stored
-//           structure-of-arrays, vals[((slot*d + i)*d + j)*nf + f], so that
-//           consecutive face rows are consecutive in memory for every (slot,
-//           i, j): the SpMV's loads are fully coalesced.
+//           exterior keeps col = row and zero values.  Sliced ELL: the face
+//           rows are cut into slices of 256; a slice stores its planes q =
+//           (slot*d + i)*d + j one after the other, 256 rows each, so element
+//           (f, q) is at ((f/256)*nplanes + q)*256 + f%256.  Consecutive rows
+//           are consecutive in memory in every plane (coalesced loads), and a
+//           slice is one contiguous run that one bulk copy stages.  The rows
+//           of the last slice beyond nf hold zero values and column 0.
 //   vectors [nf][d], face major, component fastest.
 #pragma once
 
@@ -26,6 +29,13 @@
 #include "../../include/crhyb.h"
 
 namespace crhyb {
+
+constexpr int kSlice = 256;   // face rows per slice of the sliced ELL
+
+// Index of row f in plane q of a sliced-ELL array with nplanes planes.
+__host__ __device__ __forceinline__ size_t sell(int64_t f, int q, int nplanes) {
+    return (size_t(f >> 8) * size_t(nplanes) + size_t(q)) * kSlice + size_t(f & (kSlice - 1));
+}
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
@@ -69,6 +79,7 @@ struct RedBuf {
 struct cr_mesh {
     int d = 0;
     int64_t ne = 0, nv = 0, nf = 0, nf_ext = 0;
+    int64_t nfp = 0;   // face rows rounded up to whole slices of the sliced ELL (a multiple of 256)
     int k0 = 0;
     bool has_mis = false;
     cudaStream_t user_stream = nullptr;  // the caller's stream

@@ -150,8 +150,10 @@ extern "C" int cr_mesh_load(int dim, const double* coords, int64_t nv, const int
         return fail(CR_ERR_MESH, "cr_mesh_load: the mesh has no interior face");
     }
 
-    // ---- ELL columns (slots 1..2d) ----
-    std::vector<int32_t> cols(size_t(2 * d) * nf);
+    // ---- ELL columns (slots 1..2d), sliced ----
+    const int64_t nfp = (nf + kSlice - 1) / kSlice * kSlice;
+    m->nfp = nfp;
+    std::vector<int32_t> cols(size_t(2 * d) * nfp, 0);
     for (int64_t f = 0; f < nf; ++f) {
         for (int s = 0; s < 2; ++s) {
             const int64_t E = m->h_face_elems[2 * f + s];
@@ -159,7 +161,7 @@ extern "C" int cr_mesh_load(int dim, const double* coords, int64_t nv, const int
             for (int r = 0; r < d; ++r) {
                 const int mm = r < l ? r : r + 1;
                 const int32_t c = elem_face[E * dp1 + mm];
-                cols[size_t(s * d + r) * nf + f] = c < 0 ? int32_t(f) : c;
+                cols[sell(f, s * d + r, 2 * d)] = c < 0 ? int32_t(f) : c;
             }
         }
     }
@@ -195,7 +197,7 @@ extern "C" int cr_mesh_load(int dim, const double* coords, int64_t nv, const int
         (rc = m->arena.alloc_n(&m->elem_side, size_t(ninc))) ||
         (rc = m->arena.alloc_n(&m->face_elems, size_t(2 * nf))) ||
         (rc = m->arena.alloc_n(&m->face_local, size_t(2 * nf))) ||
-        (rc = m->arena.alloc_n(&m->cols, size_t(2 * d) * nf)))
+        (rc = m->arena.alloc_n(&m->cols, size_t(2 * d) * nfp)))
         return cleanup(rc);
     if (m->has_mis && (rc = m->arena.alloc_n(&m->mis, size_t(ne)))) return cleanup(rc);
     struct Cp { void* dst; const void* src; size_t bytes; };

@@ -42,6 +42,20 @@
 namespace crhyb {
 namespace {
 
+// Build knobs (defaults are the measured best on cfg2): blocks per SM the
+// register allocation aims at for single-right-hand-side d = 2 kernels, and
+// whether d = 2 tiles are staged through shared memory.  Staging (two 45 KB
+// stages per block) limits a block of 256 threads to 2 per SM; measured per
+// iteration on cfg2 (float-float): 95.6 us staged at 2 blocks/SM against
+// 75.4 us with per-thread coalesced loads at 3 blocks/SM, the update and
+// direction phases losing more to the lower occupancy than the SpMV phase gains.
+#ifndef CRHYB_PERSIST_MINB
+#define CRHYB_PERSIST_MINB 3
+#endif
+#ifndef CRHYB_STAGE_D2
+#define CRHYB_STAGE_D2 0
+#endif
+
 constexpr int kPBlock = 256;   // rows per tile = threads per block
 constexpr long long kSpinLimit = 1ll << 22;   // bounded barrier wait (about 0.3-1 s with the sleeps)
 
@@ -90,6 +104,17 @@ __device__ __forceinline__ bool pbar(PCtl* ctl) {
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Phase timing (profile runs only): block 0 adds the time since the previous
+// barrier to the phase's total, read from the global nanosecond timer.
+__device__ __forceinline__ void phase_mark(const PArgs& a, int phase, unsigned long long& t_last) {
+    if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.phase_ns[phase] += t - t_last;
+        t_last = t;
+    }
 }
 
 // Sum of NV doubles over the block (thread 0 gets the totals).
@@ -205,7 +230,8 @@ template <int D, int R, typename LT>
 __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask, const float2* __restrict__ p,
                                        float2 (&y)[R][D]) {
     constexpr int NS = 2 * D + 1;
-    const int64_t nf = S.nf, N = nf * D;
+    constexpr int NPV = NS * D * D;
+    const int64_t N = S.nf * D;
     const float* vh = S.vh;
     const LT* vl = static_cast<const LT*>(S.vl);
     FFAcc acc[R][D];
@@ -215,13 +241,13 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
         for (int i = 0; i < D; ++i) acc[k][i].zero();
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + size_t(s - 1) * nf + f));
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + sell(f, s - 1, 2 * D)));
         float h[D][D], l[D][D];
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const size_t idx = ((size_t(s) * D + i) * D + j) * nf + f;
+                const size_t idx = sell(f, (s * D + i) * D + j, NPV);
                 h[i][j] = __ldcs(vh + idx);
                 l[i][j] = lo_val(vl + idx);
             }
@@ -248,19 +274,20 @@ template <int D, int R>
 __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, const double* __restrict__ x,
                                       double (&y)[R][D]) {
     constexpr int NS = 2 * D + 1;
-    const int64_t nf = S.nf, N = nf * D;
+    constexpr int NPV = NS * D * D;
+    const int64_t N = S.nf * D;
 #pragma unroll
     for (int k = 0; k < R; ++k)
 #pragma unroll
         for (int i = 0; i < D; ++i) y[k][i] = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + size_t(s - 1) * nf + f));
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + sell(f, s - 1, 2 * D)));
         double v[D][D];
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
-            for (int j = 0; j < D; ++j) v[i][j] = __ldcs(S.v64 + ((size_t(s) * D + i) * D + j) * nf + f);
+            for (int j = 0; j < D; ++j) v[i][j] = __ldcs(S.v64 + sell(f, (s * D + i) * D + j, NPV));
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             if (!((amask >> k) & 1u)) continue;
@@ -272,6 +299,162 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
 #pragma unroll
                 for (int j = 0; j < D; ++j) y[k][i] = fma(v[i][j], xv[j], y[k][i]);
         }
+    }
+}
+
+// ---- tile staging (TMA bulk copies) ------------------------------------------
+//
+// For d = 2 the SpMV phase stages each tile (one slice of the sliced ELL: its
+// high values, low values and columns are three contiguous runs) into shared
+// memory with cp.async.bulk (the TMA engine's 1D mode) while the block
+// computes the previous tile: two stages, one mbarrier each, completion counted
+// in bytes.  A slice starts at a multiple of 256 rows times 2-8 bytes per
+// value, so every copy is 16-byte aligned and a multiple of 16 bytes long; the
+// last slice is copied whole (its rows beyond nf are zero).
+
+template <int D, int MODE>
+struct Stage {
+    static constexpr bool kOn = D == 2 && CRHYB_STAGE_D2 != 0;  // d = 3 tiles would not fit twice
+    static constexpr int NS = 2 * D + 1, NPV = NS * D * D, NC = 2 * D;
+    static constexpr int VB = MODE == kModeFP64 ? 8 : 4;      // bytes of a (high) value
+    static constexpr int LB = MODE == kModeFF32 ? 4 : (MODE == kModeFFBF16 ? 2 : 0);
+    static constexpr int HI = 0;                              // offsets inside a stage
+    static constexpr int LO = NPV * kPBlock * VB;
+    static constexpr int CO = LO + NPV * kPBlock * LB;
+    static constexpr int BYTES = CO + NC * kPBlock * 4;
+    static constexpr int SMEM = kOn ? 2 * BYTES + 16 : 0;     // two stages and two mbarriers
+};
+
+constexpr long long kWaitLimit = 1ll << 22;   // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Warp 0 stages the slice that starts at row r0 of system S into buf.
+template <int D, int MODE>
+__device__ __forceinline__ void stage_issue(const PSys& S, int64_t r0, unsigned char* buf, uint64_t* bar) {
+    using G = Stage<D, MODE>;
+    const int lane = threadIdx.x & 31;
+    constexpr uint32_t HB = uint32_t(G::NPV) * kPBlock * G::VB, LBY = uint32_t(G::NPV) * kPBlock * G::LB,
+                       CB = uint32_t(G::NC) * kPBlock * 4;
+    const size_t slice = size_t(r0 / kPBlock);
+    if (lane == 0) {
+        mbar_expect_tx(bar, HB + LBY + CB);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of buf before the new writes
+        const char* vh = MODE == kModeFP64 ? reinterpret_cast<const char*>(S.v64) : reinterpret_cast<const char*>(S.vh);
+        bulk_g2s(buf + G::HI, vh + slice * HB, HB, bar);
+        if (G::LB) bulk_g2s(buf + G::LO, static_cast<const char*>(S.vl) + slice * LBY, LBY, bar);
+        bulk_g2s(buf + G::CO, reinterpret_cast<const char*>(S.cols) + slice * CB, CB, bar);
+    }
+}
+
+// Every thread waits for the stage; a wait that runs out sets the error flag.
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, PCtl* ctl) {
+    for (long long n = 0; n < kWaitLimit; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(&ctl->err, 3);
+    return false;
+}
+
+// q = G p for one row from a staged tile (row r of the stage), float-float.
+// Right-hand sides outermost: only one right-hand side's gathers of p are live
+// at a time; the values of G are re-read from shared memory for each.
+template <int D, int R, int MODE>
+__device__ __forceinline__ void ff_row_staged(const unsigned char* buf, int r, int64_t f, unsigned amask,
+                                              const float2* __restrict__ p, int64_t N, float2 (&y)[R][D]) {
+    using G = Stage<D, MODE>;
+    constexpr int NS = 2 * D + 1;
+    const float* hi = reinterpret_cast<const float*>(buf + G::HI);
+    const int32_t* co = reinterpret_cast<const int32_t*>(buf + G::CO);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        FFAcc acc[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc[i].zero();
+        if ((amask >> k) & 1u) {
+            float2 xv[NS][D];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int64_t c = s == 0 ? f : int64_t(co[(s - 1) * kPBlock + r]);
+#pragma unroll
+                for (int j = 0; j < D; ++j) xv[s][j] = __ldcg(p + k * N + c * D + j);
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const int q = (s * D + i) * D + j;
+                        float l;
+                        if (MODE == kModeFFBF16)
+                            l = __uint_as_float(
+                                unsigned(reinterpret_cast<const unsigned short*>(buf + G::LO)[q * kPBlock + r]) << 16);
+                        else
+                            l = reinterpret_cast<const float*>(buf + G::LO)[q * kPBlock + r];
+                        acc[i].mad(hi[q * kPBlock + r], l, xv[s][j].x, xv[s][j].y);
+                    }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[k][i] = acc[i].result();
+    }
+}
+
+// q = G x for one row from a staged tile, FP64 (right-hand sides outermost).
+template <int D, int R, int MODE>
+__device__ __forceinline__ void d_row_staged(const unsigned char* buf, int r, int64_t f, unsigned amask,
+                                             const double* __restrict__ x, int64_t N, double (&y)[R][D]) {
+    using G = Stage<D, MODE>;
+    constexpr int NS = 2 * D + 1;
+    const double* v = reinterpret_cast<const double*>(buf + G::HI);
+    const int32_t* co = reinterpret_cast<const int32_t*>(buf + G::CO);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[k][i] = 0.0;
+        if (!((amask >> k) & 1u)) continue;
+        double xv[NS][D];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int64_t c = s == 0 ? f : int64_t(co[(s - 1) * kPBlock + r]);
+#pragma unroll
+            for (int j = 0; j < D; ++j) xv[s][j] = __ldcg(x + k * N + c * D + j);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) y[k][i] = fma(v[((s * D + i) * D + j) * kPBlock + r], xv[s][j], y[k][i]);
     }
 }
 
@@ -295,12 +478,25 @@ __device__ __forceinline__ unsigned update_mask(const PArgs& a, const PSys& S, i
 }
 
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a) {
+__global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : 2)) k_pcg_persist(PArgs a) {
     constexpr bool FF = MODE != kModeFP64;
     using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float>::type;
     PCtl* ctl = a.ctl;
     const int t0 = int(blockIdx.x) * a.tpb, t1 = min(t0 + a.tpb, a.ntiles);
     int piters = 0, epoch = a.epoch0;
+    int ph[2] = {0, 0};   // phase parity of the two staging mbarriers
+    unsigned long long t_last = 0;
+    if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_last));
+    if constexpr (Stage<D, MODE>::kOn) {
+        extern __shared__ __align__(128) unsigned char dsm[];
+        uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + 2 * Stage<D, MODE>::BYTES);
+        if (threadIdx.x == 0) {
+            mbar_init(bars);
+            mbar_init(bars + 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     bool after_update = false;
     for (;;) {
         const int active = ld_vol(&ctl->snap_active), upd = ld_vol(&ctl->snap_upd);
@@ -337,6 +533,7 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                     }
                 }
                 if (!pbar(ctl)) return;
+                phase_mark(a, 0, t_last);
             }
             // ---------------- U2: r64 = b - G x64 (FP64); r.r, b.b, r.M^{-1}r ----------------
             {
@@ -437,6 +634,7 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                 if (cur >= 0 && umask) flush();
             }
             if (!pbar(ctl)) return;
+            phase_mark(a, 1, t_last);
             // ---------------- U3: r = sigma r64 (float-float); p = M^{-1} r + beta p ----------------
             for (int t = t0; t < t1; ++t) {
                 const int2 td = a.tiles[t];
@@ -467,6 +665,7 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                 }
             }
             if (!pbar(ctl)) return;
+            phase_mark(a, 2, t_last);
             continue;
         }
         // ---------------- P1: q = G p, p.q ----------------
@@ -495,27 +694,12 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                     }
                 }
             };
-            for (int t = t0; t < t1; ++t) {
-                const int2 td = a.tiles[t];
-                if (td.x != cur) {
-                    if (cur >= 0 && amask) flush();
-                    cur = td.x;
-                    amask = active_mask(a, a.sys[cur], cur);
-#pragma unroll
-                    for (int k = 0; k < R; ++k) {
-                        af[k][0].zero();
-                        ad[k][0] = 0.0;
-                    }
-                }
-                if (!amask) continue;
-                const PSys& S = a.sys[cur];
+            // accumulate one row's q = G p and p.q (y computed by the caller)
+            auto row_out = [&](const PSys& S, int64_t f, const void* yv) {
                 const int64_t N = S.nf * D;
-                const int64_t f = td.y + threadIdx.x;
-                if (f >= S.nf) continue;
                 if (FF) {
-                    float2 y[R][D];
+                    const float2(&y)[R][D] = *static_cast<const float2(*)[R][D]>(yv);
                     const float2* p = static_cast<const float2*>(S.p);
-                    ff_row<D, R, LT>(S, f, amask, p, y);
                     float2* q = static_cast<float2*>(S.q);
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
@@ -528,9 +712,8 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                         }
                     }
                 } else {
-                    double y[R][D];
+                    const double(&y)[R][D] = *static_cast<const double(*)[R][D]>(yv);
                     const double* p = static_cast<const double*>(S.p);
-                    d_row<D, R>(S, f, amask, p, y);
                     double* q = static_cast<double*>(S.q);
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
@@ -542,10 +725,99 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
                         }
                     }
                 }
+            };
+            auto new_system = [&](int s) {
+                cur = s;
+                amask = active_mask(a, a.sys[cur], cur);
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    af[k][0].zero();
+                    ad[k][0] = 0.0;
+                }
+            };
+            if constexpr (Stage<D, MODE>::kOn) {
+                // staged: tile t + 1 is copied in while tile t is computed
+                extern __shared__ __align__(128) unsigned char dsm[];   // the same dynamic buffer
+                using G = Stage<D, MODE>;
+                uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + 2 * G::BYTES);
+                auto work = [&](int t) {   // is tile t one with rows to compute?
+                    const int sidx = a.tiles[t].x;
+                    return active_mask(a, a.sys[sidx], sidx) != 0u;
+                };
+                auto issue = [&](int t, int stage) {
+                    const int2 td = a.tiles[t];
+                    stage_issue<D, MODE>(a.sys[td.x], td.y, dsm + stage * G::BYTES, bars + stage);
+                };
+                int u = 0;         // work tiles seen in this phase
+                int issued = -1;   // the last tile whose copies were issued
+                for (int t = t0; t < t1; ++t) {
+                    const int2 td = a.tiles[t];
+                    if (td.x != cur) {
+                        if (cur >= 0 && amask) flush();
+                        new_system(td.x);
+                    }
+                    if (!amask) continue;
+                    const int stage = u & 1;
+                    if (issued < t) {   // not prefetched (the previous tile was not a work tile)
+                        if (threadIdx.x < 32) issue(t, stage);
+                        issued = t;
+                    }
+                    // prefetch the next work tile into the other stage (read last by tile t - 1)
+                    if (t + 1 < t1 && work(t + 1)) {
+                        if (threadIdx.x < 32) issue(t + 1, stage ^ 1);
+                        issued = t + 1;
+                    }
+                    if (!stage_wait(bars + stage, uint32_t(ph[stage]), ctl)) {
+                        stage_wait(bars + stage, uint32_t(ph[stage]), ctl);   // bounded, then give up
+                        return;
+                    }
+                    ph[stage] ^= 1;
+                    const PSys& S = a.sys[cur];
+                    const int64_t f = td.y + threadIdx.x;
+                    if (f < S.nf) {
+                        const int64_t N = S.nf * D;
+                        if (FF) {
+                            float2 y[R][D];
+                            ff_row_staged<D, R, MODE>(dsm + stage * G::BYTES, threadIdx.x, f, amask,
+                                                      static_cast<const float2*>(S.p), N, y);
+                            row_out(S, f, &y);
+                        } else {
+                            double y[R][D];
+                            d_row_staged<D, R, MODE>(dsm + stage * G::BYTES, threadIdx.x, f, amask,
+                                                     static_cast<const double*>(S.p), N, y);
+                            row_out(S, f, &y);
+                        }
+                    }
+                    __syncthreads();   // the stage may be refilled
+                    ++u;
+                }
+            } else {
+                for (int t = t0; t < t1; ++t) {
+                    const int2 td = a.tiles[t];
+                    if (td.x != cur) {
+                        if (cur >= 0 && amask) flush();
+                        new_system(td.x);
+                    }
+                    if (!amask) continue;
+                    const PSys& S = a.sys[cur];
+                    const int64_t N = S.nf * D;
+                    const int64_t f = td.y + threadIdx.x;
+                    if (f >= S.nf) continue;
+                    if (FF) {
+                        float2 y[R][D];
+                        ff_row<D, R, LT>(S, f, amask, static_cast<const float2*>(S.p), y);
+                        row_out(S, f, &y);
+                    } else {
+                        double y[R][D];
+                        d_row<D, R>(S, f, amask, static_cast<const double*>(S.p), y);
+                        row_out(S, f, &y);
+                    }
+                }
             }
             if (cur >= 0 && amask) flush();
         }
         if (!pbar(ctl)) return;
+        phase_mark(a, 3, t_last);
         // ---------------- P2: x += alpha p, r -= alpha q; r.z, r.r ----------------
         {
             int cur = -1;
@@ -642,6 +914,7 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
             if (cur >= 0 && amask) flush();
         }
         if (!pbar(ctl)) return;
+        phase_mark(a, 4, t_last);
         // ---------------- P3: p = M^{-1} r + beta p ----------------
         {
             int cur = -1;
@@ -686,6 +959,7 @@ __global__ void __launch_bounds__(kPBlock, R == 1 ? 3 : 1) k_pcg_persist(PArgs a
             }
         }
         if (!pbar(ctl)) return;
+        phase_mark(a, 5, t_last);
         ++piters;
         after_update = false;
     }
@@ -699,13 +973,16 @@ template <int D, int R, int MODE>
 int launch_one(const PArgs& a, int grid, cudaStream_t st) {
     void* args[] = {const_cast<PArgs*>(&a)};
     CR_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_pcg_persist<D, R, MODE>), dim3(grid),
-                                        dim3(kPBlock), args, 0, st));
+                                        dim3(kPBlock), args, size_t(Stage<D, MODE>::SMEM), st));
     return CR_OK;
 }
 
 template <int D, int R, int MODE>
 int occupancy(int* blocks_per_sm) {
-    CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, &k_pcg_persist<D, R, MODE>, kPBlock, 0));
+    constexpr int smem = Stage<D, MODE>::SMEM;
+    if (smem > 48 * 1024)
+        CR_CUDA(cudaFuncSetAttribute(&k_pcg_persist<D, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, &k_pcg_persist<D, R, MODE>, kPBlock, smem));
     return CR_OK;
 }
 
@@ -763,29 +1040,56 @@ int PersistPlan::build(const std::vector<PSys>& systems, int d_, int mode_, int 
     if (blocks_per_sm_cap > 0) bps = std::min(bps, blocks_per_sm_cap);
     grid = std::min(g_sms * bps, std::max(ntiles, 1));
     blocks_per_sm = bps;
-    // contiguous tile ranges: block b sweeps tiles [b tpb, (b+1) tpb); per system the
-    // blocks that cover it and their partial-sum slots
-    tpb = (ntiles + grid - 1) / grid;
-    nslots = 0;
-    for (int s = 0; s < nsys; ++s) {
-        sy[s].blk0 = sy[s].tile0 / tpb;
-        sy[s].nblk = (sy[s].tile0 + sy[s].ntiles - 1) / tpb - sy[s].blk0 + 1;
-        sy[s].slot0 = nslots;
-        nslots += sy[s].nblk;
-    }
     CR_TRY(arena.alloc_n(&d_sys, size_t(nsys)));
     CR_TRY(arena.alloc_n(&d_tiles, size_t(std::max(ntiles, 1))));
     CR_TRY(arena.alloc_n(&d_scal, size_t(nsys) * kPMaxRhs));
-    CR_TRY(arena.alloc_n(&d_tpart, size_t(std::max(nslots, 1)) * kPMaxRhs * 4));
+    CR_TRY(arena.alloc_n(&d_tpart, size_t(nsys + grid) * kPMaxRhs * 4));   // slots never exceed nsys + grid
     CR_TRY(arena.alloc_n(&d_syscnt, size_t(nsys)));
     CR_TRY(arena.alloc_n(&d_ctl, 1));
+    CR_TRY(arena.alloc_n(&d_phase, 8));
     CR_CUDA(cudaMallocHost(&h_scal, sizeof(PScal) * nsys * kPMaxRhs));
     CR_CUDA(cudaMallocHost(&h_ctl, sizeof(PCtl)));
     CR_CUDA(cudaMallocHost(&h_sys, sizeof(PSys) * nsys));
-    CR_CUDA(cudaMemcpy(d_sys, sy.data(), sizeof(PSys) * nsys, cudaMemcpyHostToDevice));
-    CR_CUDA(cudaMemcpy(d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMallocHost(&h_tiles, sizeof(int2) * std::max(ntiles, 1)));
     CR_CUDA(cudaMemset(d_syscnt, 0, sizeof(unsigned) * nsys));
     sys_host = sy;
+    live.assign(size_t(nsys), 1);
+    CR_TRY(layout(nullptr));
+    CR_CUDA(cudaDeviceSynchronize());
+    return CR_OK;
+}
+
+// Lay the tiles of the live systems out over the blocks: block b sweeps the
+// contiguous range [b tpb, (b+1) tpb); per system the blocks that cover it and
+// their partial-sum slots.  Systems whose pairs are all done get no tiles, so
+// the resident blocks spread over the work that is left.
+int PersistPlan::layout(cudaStream_t st) {
+    int nt = 0;
+    for (int s = 0; s < nsys; ++s) {
+        PSys& y = sys_host[s];
+        y.tile0 = nt;
+        y.ntiles = live[s] ? int((y.nf + kPBlock - 1) / kPBlock) : 0;
+        for (int t = 0; t < y.ntiles; ++t) h_tiles[nt + t] = make_int2(s, t * kPBlock);
+        nt += y.ntiles;
+    }
+    ntiles_live = nt;
+    tpb = std::max((nt + grid - 1) / grid, 1);
+    nslots = 0;
+    for (int s = 0; s < nsys; ++s) {
+        PSys& y = sys_host[s];
+        if (y.ntiles == 0) {
+            y.blk0 = y.nblk = 0;
+            y.slot0 = nslots;
+        } else {
+            y.blk0 = y.tile0 / tpb;
+            y.nblk = (y.tile0 + y.ntiles - 1) / tpb - y.blk0 + 1;
+            y.slot0 = nslots;
+            nslots += y.nblk;
+        }
+        h_sys[s] = y;
+    }
+    CR_CUDA(cudaMemcpyAsync(d_tiles, h_tiles, sizeof(int2) * std::max(nt, 1), cudaMemcpyHostToDevice, st));
+    CR_CUDA(cudaMemcpyAsync(d_sys, h_sys, sizeof(PSys) * nsys, cudaMemcpyHostToDevice, st));
     return CR_OK;
 }
 
@@ -818,6 +1122,8 @@ void PersistPlan::release() {
     if (h_scal) cudaFreeHost(h_scal);
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_sys) cudaFreeHost(h_sys);
+    if (h_tiles) cudaFreeHost(h_tiles);
+    h_tiles = nullptr;
     h_scal = nullptr;
     h_ctl = nullptr;
     h_sys = nullptr;
@@ -827,6 +1133,7 @@ void PersistPlan::release() {
     d_tpart = nullptr;
     d_syscnt = nullptr;
     d_ctl = nullptr;
+    d_phase = nullptr;
 }
 
 // Run the solve to completion: every (system, rhs) pair starts from x64
@@ -864,6 +1171,11 @@ int PersistPlan::run(double tol, double delta, int max_it, int iters, cudaStream
     CR_CUDA(cudaMemcpyAsync(d_scal, h_scal, sizeof(PScal) * sc.size(), cudaMemcpyHostToDevice, st));
     CR_CUDA(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(PCtl), cudaMemcpyHostToDevice, st));
     CR_CUDA(cudaMemsetAsync(d_syscnt, 0, sizeof(unsigned) * nsys, st));
+    if (std::find(live.begin(), live.end(), 0) != live.end()) {
+        std::fill(live.begin(), live.end(), 1);
+        CR_CUDA(cudaStreamSynchronize(st));   // the pinned staging buffers may feed an earlier copy
+        CR_TRY(layout(st));
+    }
     PArgs a{};
     a.sys = d_sys;
     a.tiles = d_tiles;
@@ -871,13 +1183,15 @@ int PersistPlan::run(double tol, double delta, int max_it, int iters, cudaStream
     a.tpart = d_tpart;
     a.syscnt = d_syscnt;
     a.ctl = d_ctl;
-    a.ntiles = ntiles;
+    a.ntiles = ntiles_live;
     a.tpb = tpb;
     a.tol = tol;
     a.delta = delta;
     a.max_it = max_it;
     a.iters = iters > 0 ? iters : 1 << 30;
     a.epoch0 = 0;
+    a.phase_ns = profile ? d_phase : nullptr;
+    if (profile) CR_CUDA(cudaMemsetAsync(d_phase, 0, sizeof(unsigned long long) * 8, st));
     LaunchFn l = reinterpret_cast<LaunchFn>(launch);
     int idle = 0;
     for (;;) {
@@ -896,13 +1210,39 @@ int PersistPlan::run(double tol, double delta, int max_it, int iters, cudaStream
             if (piters) *piters += h_ctl->piters;
         }
         if (h_ctl->snap_active == 0 || h_ctl->active == 0) break;
+        if (nsys > 1) {
+            // drop the systems whose pairs are all done and spread the rest over the blocks
+            CR_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(PScal) * sc.size(), cudaMemcpyDeviceToHost, st));
+            CR_CUDA(cudaStreamSynchronize(st));
+            bool changed = false;
+            for (int s2 = 0; s2 < nsys; ++s2) {
+                if (!live[s2]) continue;
+                bool any = false;
+                for (int k = 0; k < sys_host[s2].R; ++k) any |= !h_scal[size_t(s2) * kPMaxRhs + k].done;
+                if (!any) {
+                    live[s2] = 0;
+                    changed = true;
+                }
+            }
+            if (changed) {
+                CR_TRY(layout(st));
+                a.ntiles = ntiles_live;
+                a.tpb = tpb;
+            }
+        }
         if (h_ctl->piters == 0 && ++idle > 2)
             return fail(CR_ERR_BREAKDOWN, "persistent PCG: launches make no progress");
         if (h_ctl->piters > 0) idle = 0;
         a.epoch0 = h_ctl->epoch;
     }
     CR_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(PScal) * sc.size(), cudaMemcpyDeviceToHost, st));
+    if (profile) CR_CUDA(cudaMemcpyAsync(h_phase, d_phase, sizeof(h_phase), cudaMemcpyDeviceToHost, st));
     CR_CUDA(cudaStreamSynchronize(st));
+    if (profile && std::getenv("CRHYB_TRACE")) {
+        static const char* names[6] = {"U1", "U2", "U3", "P1", "P2", "P3"};
+        for (int k = 0; k < 6; ++k)
+            std::fprintf(stderr, "[crhyb] persistent phase %s: %.3f ms\n", names[k], h_phase[k] * 1e-6);
+    }
     return CR_OK;
 }
 

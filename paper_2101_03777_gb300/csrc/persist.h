@@ -20,8 +20,8 @@ struct PSys {
     int R;
     int tile0, ntiles;          // its tiles in the tile list (set by PersistPlan::build)
     int blk0, nblk, slot0;      // the blocks whose tile ranges cover it, and its partial-sum slots
-    const int32_t* cols;        // [2d][nf], block ELL slots 1..2d
-    const float* vh;            // float-float high plane [2d+1][d][d][nf]
+    const int32_t* cols;        // sliced ELL columns of slots 1..2d
+    const float* vh;            // float-float high values, sliced ELL
     const void* vl;             // low plane (float or bf16)
     const double* v64;          // FP64 values
     const float* minv32;        // 1 / diag(G)
@@ -59,11 +59,14 @@ struct PArgs {
     int ntiles, tpb;            // tiles, tiles per block (contiguous ranges)
     double tol, delta;
     int max_it, iters, epoch0;
+    unsigned long long* phase_ns;   // profile runs: time per phase (U1 U2 U3 P1 P2 P3), else NULL
 };
 
 // A launch plan for one list of systems (all with the same d and arithmetic).
 struct PersistPlan {
     int d = 2, mode = 0, nsys = 0, rmax = 1, ntiles = 0, grid = 0, blocks_per_sm = 0, tpb = 1, nslots = 0;
+    int ntiles_live = 0;        // tiles of the systems that still have pairs to solve
+    std::vector<char> live;     // per system: some pair not done
     void* launch = nullptr;
     DevArena arena;
     PSys* d_sys = nullptr;
@@ -75,14 +78,18 @@ struct PersistPlan {
     PScal* h_scal = nullptr;    // pinned
     PCtl* h_ctl = nullptr;      // pinned
     PSys* h_sys = nullptr;      // pinned staging of the system table
+    int2* h_tiles = nullptr;    // pinned staging of the tile list
     std::vector<PSys> sys_host;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    unsigned long long* d_phase = nullptr;   // [8] phase times of the profile runs
+    unsigned long long h_phase[8] = {};
 
     // mode: 0 FP64, 1 float-float (FP32 low plane), 2 float-float (BF16 low plane)
     int build(const std::vector<PSys>& systems, int d, int mode, int blocks_per_sm_cap);
     // replace the systems' pointers (same sizes and tiles as at build), stream ordered
     int update_systems(const std::vector<PSys>& systems, cudaStream_t st);
     bool built() const { return d_sys != nullptr; }
+    int layout(cudaStream_t st);
     // profile: time every launch with CUDA events; *ms and *piters receive the summed
     // kernel time and the PCG iterations those launches ran
     int run(double tol, double delta, int max_it, int iters, cudaStream_t st, int64_t* launches,

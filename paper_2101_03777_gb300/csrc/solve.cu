@@ -73,14 +73,14 @@ __device__ __forceinline__ float ld_val(const __nv_bfloat16* p) {
 
 // y_f = sum over the 2d+1 slots of block(slot) * x[col(slot)]  (one face row)
 template <int D, typename VT, typename XT, typename AT>
-__device__ __forceinline__ void ell_row(int64_t f, int64_t nf, const int32_t* __restrict__ cols,
+__device__ __forceinline__ void ell_row(int64_t f, const int32_t* __restrict__ cols,
                                         const VT* __restrict__ vals, const XT* __restrict__ x, AT (&y)[D]) {
     constexpr int NS = 2 * D + 1;
 #pragma unroll
     for (int i = 0; i < D; ++i) y[i] = AT(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + size_t(s - 1) * nf + f));
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + sell(f, s - 1, 2 * D)));
         AT xv[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) xv[j] = AT(__ldg(x + c * D + j));
@@ -88,7 +88,7 @@ __device__ __forceinline__ void ell_row(int64_t f, int64_t nf, const int32_t* __
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j)
-                y[i] = fma(AT(ld_val(vals + ((size_t(s) * D + i) * D + j) * nf + f)), xv[j], y[i]);
+                y[i] = fma(AT(ld_val(vals + sell(f, (s * D + i) * D + j, NS * D * D))), xv[j], y[i]);
     }
 }
 
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv(int64_t nf, const int32_t* 
     double part[1] = {0.0};
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         XT y[D];
-        ell_row<D, VT, XT, XT>(f, nf, cols, vals, p, y);
+        ell_row<D, VT, XT, XT>(f, cols, vals, p, y);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             q[f * D + i] = y[i];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t
     double part[3] = {0.0, 0.0, 0.0};
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         double y[D];
-        if (x) ell_row<D, double, double, double>(f, nf, cols, vals, x, y);
+        if (x) ell_row<D, double, double, double>(f, cols, vals, x, y);
         else {
 #pragma unroll
             for (int i = 0; i < D; ++i) y[i] = 0.0;
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv64(int64_t nf, const int32_t* __
                                                    double* __restrict__ y) {
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         double v[D];
-        ell_row<D, double, double, double>(f, nf, cols, vals, x, v);
+        ell_row<D, double, double, double>(f, cols, vals, x, v);
 #pragma unroll
         for (int i = 0; i < D; ++i) y[f * D + i] = v[i];
     }
@@ -373,7 +373,7 @@ __device__ __forceinline__ bool ff_grid_sum(float2 (&v)[NV], RedBuf red, double 
 
 // y_f = sum over the 2d+1 slots of block(slot) * x[col(slot)], float-float
 template <int D, typename LT>
-__device__ __forceinline__ void ff_ell_row(int64_t f, int64_t nf, const int32_t* __restrict__ cols,
+__device__ __forceinline__ void ff_ell_row(int64_t f, const int32_t* __restrict__ cols,
                                            const float* __restrict__ vh, const LT* __restrict__ vl,
                                            const float2* __restrict__ x, float2 (&y)[D]) {
     constexpr int NS = 2 * D + 1;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void ff_ell_row(int64_t f, int64_t nf, const int32_t*
     for (int i = 0; i < D; ++i) acc[i].zero();
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + size_t(s - 1) * nf + f));
+        const int64_t c = s == 0 ? f : int64_t(__ldcs(cols + sell(f, s - 1, 2 * D)));
         float2 xv[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) xv[j] = __ldg(x + c * D + j);
@@ -390,7 +390,7 @@ __device__ __forceinline__ void ff_ell_row(int64_t f, int64_t nf, const int32_t*
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const size_t idx = ((size_t(s) * D + i) * D + j) * nf + f;
+                const size_t idx = sell(f, (s * D + i) * D + j, NS * D * D);
                 acc[i].mad(__ldcs(vh + idx), lo_val(vl + idx), xv[j].x, xv[j].y);
             }
     }
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) kf_spmv(int64_t nf, const int32_t* __r
     dot.zero();
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         float2 y[D];
-        ff_ell_row<D, LT>(f, nf, cols, vh, vl, p, y);
+        ff_ell_row<D, LT>(f, cols, vh, vl, p, y);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             q[f * D + i] = y[i];
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kBlock) k_gm_spmv(int64_t nf, const int32_t* _
     XT* w = V + size_t(sc->j + 1) * nf * D;
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         XT y[D];
-        ell_row<D, VT, XT, XT>(f, nf, cols, vals, z, y);
+        ell_row<D, VT, XT, XT>(f, cols, vals, z, y);
 #pragma unroll
         for (int i = 0; i < D; ++i) w[f * D + i] = y[i];
     }
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_w(int64_t nf, const int32_t
     if (sc->done) return;
     for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
         XT y[D];
-        ell_row<D, VT, XT, XT>(f, nf, cols, vals, x, y);
+        ell_row<D, VT, XT, XT>(f, cols, vals, x, y);
 #pragma unroll
         for (int i = 0; i < D; ++i) r[f * D + i] = b[f * D + i] - y[i];
     }
