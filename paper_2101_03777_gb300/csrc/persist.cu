@@ -44,7 +44,9 @@ namespace {
 
 // Build knobs (defaults are the measured best on cfg2): blocks per SM the
 // register allocation aims at for single-right-hand-side d = 2 kernels, and
-// whether d = 2 tiles are staged through shared memory.  Staging (two 45 KB
+// how d = 2 tiles reach the SpMV phase: 0 per-thread loads, 1 one shared-memory
+// stage per block filled by TMA bulk copies, 2 two stages (the next tile is
+// copied in while the current one is computed).  Staging (two 45 KB
 // stages per block) limits a block of 256 threads to 2 per SM; measured per
 // iteration on cfg2 (float-float): 95.6 us staged at 2 blocks/SM against
 // 75.4 us with per-thread coalesced loads at 3 blocks/SM, the update and
@@ -68,6 +70,61 @@ __device__ __forceinline__ int ld_vol(const int* p) { return *reinterpret_cast<c
 __device__ __forceinline__ int sc_i(const int& v) { return __ldcg(&v); }
 __device__ __forceinline__ double sc_d(const double& v) { return __ldcg(&v); }
 __device__ __forceinline__ float2 sc_f2(const float2& v) { return __ldcg(&v); }
+
+// The d components of a face are adjacent: in 2D one 16-byte access moves both
+// (float-float pairs or FP64 values; the arrays are 16-byte aligned).
+__device__ __forceinline__ void ld2(const float2* p, float2 (&v)[2]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void ld2(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+}
+__device__ __forceinline__ void ld2(const float* p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+}
+__device__ __forceinline__ void ld2cg(const float2* p, float2 (&v)[2]) {
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void ld2cg(const double* p, double (&v)[2]) {
+    const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+}
+__device__ __forceinline__ void st2(float2* p, const float2 (&v)[2]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+}
+__device__ __forceinline__ void st2(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+template <int D, typename V>
+__device__ __forceinline__ void ldrow(const V* p, V (&v)[D]) {
+    if constexpr (D == 2) ld2(p, v);
+    else
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = p[j];
+}
+template <int D, typename V>
+__device__ __forceinline__ void ldrow_cg(const V* p, V (&v)[D]) {
+    if constexpr (D == 2) ld2cg(p, v);
+    else
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = __ldcg(p + j);
+}
+template <int D, typename V>
+__device__ __forceinline__ void strow(V* p, const V (&v)[D]) {
+    if constexpr (D == 2) st2(p, v);
+    else
+#pragma unroll
+        for (int j = 0; j < D; ++j) p[j] = v[j];
+}
 
 // Grid barrier with a bounded wait.  The releasing block snapshots the loop
 // control counters before it opens the barrier.  Returns false in every
@@ -256,7 +313,7 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
             if (!((amask >> k) & 1u)) continue;
             float2 xv[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) xv[j] = __ldcg(p + k * N + c * D + j);
+            ldrow_cg<D>(p + k * N + c * D, xv);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -293,7 +350,7 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
             if (!((amask >> k) & 1u)) continue;
             double xv[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) xv[j] = __ldcg(x + k * N + c * D + j);
+            ldrow_cg<D>(x + k * N + c * D, xv);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -315,6 +372,7 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
 template <int D, int MODE>
 struct Stage {
     static constexpr bool kOn = D == 2 && CRHYB_STAGE_D2 != 0;  // d = 3 tiles would not fit twice
+    static constexpr int NST = CRHYB_STAGE_D2 >= 2 ? 2 : 1;    // stages per block (2: prefetch the next tile)
     static constexpr int NS = 2 * D + 1, NPV = NS * D * D, NC = 2 * D;
     static constexpr int VB = MODE == kModeFP64 ? 8 : 4;      // bytes of a (high) value
     static constexpr int LB = MODE == kModeFF32 ? 4 : (MODE == kModeFFBF16 ? 2 : 0);
@@ -322,7 +380,7 @@ struct Stage {
     static constexpr int LO = NPV * kPBlock * VB;
     static constexpr int CO = LO + NPV * kPBlock * LB;
     static constexpr int BYTES = CO + NC * kPBlock * 4;
-    static constexpr int SMEM = kOn ? 2 * BYTES + 16 : 0;     // two stages and two mbarriers
+    static constexpr int SMEM = kOn ? NST * BYTES + 16 : 0;   // the stages and two mbarriers
 };
 
 constexpr long long kWaitLimit = 1ll << 22;   // bounded mbarrier waits
@@ -489,7 +547,7 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
     if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_last));
     if constexpr (Stage<D, MODE>::kOn) {
         extern __shared__ __align__(128) unsigned char dsm[];
-        uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + 2 * Stage<D, MODE>::BYTES);
+        uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + Stage<D, MODE>::NST * Stage<D, MODE>::BYTES);
         if (threadIdx.x == 0) {
             mbar_init(bars);
             mbar_init(bars + 1);
@@ -704,12 +762,11 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
                         if (!((amask >> k) & 1u)) continue;
+                        float2 pv[D];
+                        ldrow<D>(p + k * N + f * D, pv);
+                        strow<D>(q + k * N + f * D, y[k]);
 #pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            q[k * N + f * D + i] = y[k][i];
-                            const float2 pi = p[k * N + f * D + i];
-                            af[k][0].mad(pi.x, pi.y, y[k][i].x, y[k][i].y);
-                        }
+                        for (int i = 0; i < D; ++i) af[k][0].mad(pv[i].x, pv[i].y, y[k][i].x, y[k][i].y);
                     }
                 } else {
                     const double(&y)[R][D] = *static_cast<const double(*)[R][D]>(yv);
@@ -718,11 +775,11 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
                         if (!((amask >> k) & 1u)) continue;
+                        double pv[D];
+                        ldrow<D>(p + k * N + f * D, pv);
+                        strow<D>(q + k * N + f * D, y[k]);
 #pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            q[k * N + f * D + i] = y[k][i];
-                            ad[k][0] += p[k * N + f * D + i] * y[k][i];
-                        }
+                        for (int i = 0; i < D; ++i) ad[k][0] += pv[i] * y[k][i];
                     }
                 }
             };
@@ -739,7 +796,7 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                 // staged: tile t + 1 is copied in while tile t is computed
                 extern __shared__ __align__(128) unsigned char dsm[];   // the same dynamic buffer
                 using G = Stage<D, MODE>;
-                uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + 2 * G::BYTES);
+                uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + G::NST * G::BYTES);
                 auto work = [&](int t) {   // is tile t one with rows to compute?
                     const int sidx = a.tiles[t].x;
                     return active_mask(a, a.sys[sidx], sidx) != 0u;
@@ -757,13 +814,13 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                         new_system(td.x);
                     }
                     if (!amask) continue;
-                    const int stage = u & 1;
-                    if (issued < t) {   // not prefetched (the previous tile was not a work tile)
+                    const int stage = G::NST == 2 ? (u & 1) : 0;
+                    if (issued < t) {   // not prefetched (single stage, or the previous tile was not a work tile)
                         if (threadIdx.x < 32) issue(t, stage);
                         issued = t;
                     }
                     // prefetch the next work tile into the other stage (read last by tile t - 1)
-                    if (t + 1 < t1 && work(t + 1)) {
+                    if (G::NST == 2 && t + 1 < t1 && work(t + 1)) {
                         if (threadIdx.x < 32) issue(t + 1, stage ^ 1);
                         issued = t + 1;
                     }
@@ -883,31 +940,45 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     if (!((amask >> k) & 1u)) continue;
+                    const int64_t o = k * N + f * D;
+                    if (FF) {
+                        float2* x = static_cast<float2*>(S.x);
+                        float2* r = static_cast<float2*>(S.r);
+                        float2 xv[D], rv[D], pv[D], qv[D];
+                        float mv[D];
+                        ldrow<D>(x + o, xv);
+                        ldrow<D>(r + o, rv);
+                        ldrow<D>(static_cast<const float2*>(S.p) + o, pv);
+                        ldrow<D>(static_cast<const float2*>(S.q) + o, qv);
+                        ldrow<D>(S.minv32 + f * D, mv);
 #pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        const int64_t o = k * N + f * D + i;
-                        if (FF) {
-                            float2* x = static_cast<float2*>(S.x);
-                            float2* r = static_cast<float2*>(S.r);
-                            const float2* p = static_cast<const float2*>(S.p);
-                            const float2* q = static_cast<const float2*>(S.q);
-                            x[o] = ff_add(x[o], ff_mul(al_ff[k], p[o]));
-                            const float2 rn = ff_add(r[o], ff_neg(ff_mul(al_ff[k], q[o])));
-                            r[o] = rn;
-                            const float2 z = ff_mul1(S.minv32[f * D + i], rn);
-                            af[k][0].mad(rn.x, rn.y, z.x, z.y);
-                            af[k][1].mad(rn.x, rn.y, rn.x, rn.y);
-                        } else {
-                            double* x = static_cast<double*>(S.x);
-                            double* r = static_cast<double*>(S.r);
-                            const double* p = static_cast<const double*>(S.p);
-                            const double* q = static_cast<const double*>(S.q);
-                            x[o] = fma(al[k], p[o], x[o]);
-                            const double rn = fma(-al[k], q[o], r[o]);
-                            r[o] = rn;
-                            ad[k][0] += rn * S.minv64[f * D + i] * rn;
-                            ad[k][1] += rn * rn;
+                        for (int i = 0; i < D; ++i) {
+                            xv[i] = ff_add(xv[i], ff_mul(al_ff[k], pv[i]));
+                            rv[i] = ff_add(rv[i], ff_neg(ff_mul(al_ff[k], qv[i])));
+                            const float2 z = ff_mul1(mv[i], rv[i]);
+                            af[k][0].mad(rv[i].x, rv[i].y, z.x, z.y);
+                            af[k][1].mad(rv[i].x, rv[i].y, rv[i].x, rv[i].y);
                         }
+                        strow<D>(x + o, xv);
+                        strow<D>(r + o, rv);
+                    } else {
+                        double* x = static_cast<double*>(S.x);
+                        double* r = static_cast<double*>(S.r);
+                        double xv[D], rv[D], pv[D], qv[D], mv[D];
+                        ldrow<D>(x + o, xv);
+                        ldrow<D>(r + o, rv);
+                        ldrow<D>(static_cast<const double*>(S.p) + o, pv);
+                        ldrow<D>(static_cast<const double*>(S.q) + o, qv);
+                        ldrow<D>(S.minv64 + f * D, mv);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            xv[i] = fma(al[k], pv[i], xv[i]);
+                            rv[i] = fma(-al[k], qv[i], rv[i]);
+                            ad[k][0] += rv[i] * mv[i] * rv[i];
+                            ad[k][1] += rv[i] * rv[i];
+                        }
+                        strow<D>(x + o, xv);
+                        strow<D>(r + o, rv);
                     }
                 }
             }
@@ -942,18 +1013,26 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     if (!((amask >> k) & 1u)) continue;
+                    const int64_t o = k * N + f * D;
+                    if (FF) {
+                        float2* p = static_cast<float2*>(S.p);
+                        float2 pv[D], rv[D];
+                        float mv[D];
+                        ldrow<D>(p + o, pv);
+                        ldrow<D>(static_cast<const float2*>(S.r) + o, rv);
+                        ldrow<D>(S.minv32 + f * D, mv);
 #pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        const int64_t o = k * N + f * D + i;
-                        if (FF) {
-                            float2* pv = static_cast<float2*>(S.p);
-                            const float2 z = ff_mul1(S.minv32[f * D + i], static_cast<const float2*>(S.r)[o]);
-                            pv[o] = ff_add(z, ff_mul(be_ff[k], pv[o]));
-                        } else {
-                            double* pv = static_cast<double*>(S.p);
-                            const double z = S.minv64[f * D + i] * static_cast<const double*>(S.r)[o];
-                            pv[o] = fma(be[k], pv[o], z);
-                        }
+                        for (int i = 0; i < D; ++i) pv[i] = ff_add(ff_mul1(mv[i], rv[i]), ff_mul(be_ff[k], pv[i]));
+                        strow<D>(p + o, pv);
+                    } else {
+                        double* p = static_cast<double*>(S.p);
+                        double pv[D], rv[D], mv[D];
+                        ldrow<D>(p + o, pv);
+                        ldrow<D>(static_cast<const double*>(S.r) + o, rv);
+                        ldrow<D>(S.minv64 + f * D, mv);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) pv[i] = fma(be[k], pv[i], mv[i] * rv[i]);
+                        strow<D>(p + o, pv);
                     }
                 }
             }
