@@ -244,9 +244,14 @@ typedef struct cr_batch cr_batch;
 
 typedef struct cr_batch_opts {
     int32_t prec;          /* CR_PREC_FP64, CR_PREC_FF or CR_PREC_FF_BF16 (values kept by cr_hybridise) */
-    int32_t autotune;      /* 1: the first solve times 1..7 resident blocks per SM (64 iterations each,
-                              from the start state) and keeps the fastest for every later solve */
+    int32_t autotune;      /* 1: the first solve times both right-hand-side groupings and 1..7 resident
+                              blocks per SM (64 iterations each, from the start state) and keeps the
+                              fastest for every later solve */
     int32_t blocks_per_sm; /* > 0: cap on the resident blocks per SM (default: the occupancy limit) */
+    int32_t rhs_grouping;  /* 0 or 1: the right-hand sides of a problem share each pass over its G (one
+                              system per problem); 2: one system per (problem, right-hand side) pair,
+                              G read once per right-hand side by the single-right-hand-side kernel.
+                              With autotune = 1 both groupings are timed and the faster is kept */
 } cr_batch_opts;
 
 /* Plan a batch over nprob hybridised systems of one dimension.  The handles
@@ -256,7 +261,8 @@ typedef struct cr_batch_opts {
  * more than 4 right-hand sides, values not kept, dimensions differ), CR_ERR_OOM. */
 int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batch_opts* o, cr_batch** out);
 
-/* Launch shape of a plan (any output may be NULL). */
+/* Launch shape of a plan (any output may be NULL): systems of the grouping in use (problems, or
+ * (problem, rhs) pairs), tiles, grid and resident blocks per SM. */
 int cr_batch_info(const cr_batch* b, int32_t* nsys, int32_t* ntiles, int32_t* grid, int32_t* blocks_per_sm);
 
 /* Solve every (problem, right-hand side) pair.

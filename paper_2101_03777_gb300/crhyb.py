@@ -60,7 +60,8 @@ class cr_solve_opts(ctypes.Structure):
 
 
 class cr_batch_opts(ctypes.Structure):
-    _fields_ = [("prec", ctypes.c_int32), ("autotune", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("prec", ctypes.c_int32), ("autotune", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("rhs_grouping", ctypes.c_int32)]
 
 
 class cr_solve_stats(ctypes.Structure):
@@ -332,10 +333,11 @@ class Batch:
             self.handle = None
 
 
-def cr_batch_create(probs, prec="ff", autotune=False, blocks_per_sm=0):
-    """Plan one persistent batched PCG over the hybridised problems `probs`."""
+def cr_batch_create(probs, prec="ff", autotune=False, blocks_per_sm=0, rhs_grouping=0):
+    """Plan one persistent batched PCG over the hybridised problems `probs`
+    (rhs_grouping 1: right-hand sides of a problem share G; 2: one system per pair)."""
     arr = (_vp * len(probs))(*[h.handle for h in probs])
-    o = cr_batch_opts(PREC[prec], int(bool(autotune)), int(blocks_per_sm))
+    o = cr_batch_opts(PREC[prec], int(bool(autotune)), int(blocks_per_sm), int(rhs_grouping))
     h = _vp()
     _check(load_library().cr_batch_create(arr, len(probs), ctypes.byref(o), ctypes.byref(h)))
     return Batch(h, probs)

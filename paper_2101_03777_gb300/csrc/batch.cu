@@ -4,9 +4,12 @@
 // cooperative launch (persist.cu).  The right-hand sides of a mesh share
 // every pass over its G.
 //
-// The plan lays the problems' tiles end to end; an autotuner times a few
-// launch shapes (resident blocks per SM) on the first solve and keeps the
-// fastest.
+// The plan lays the problems' tiles end to end.  Two groupings of the
+// right-hand sides: one system per problem (its right-hand sides share each
+// pass over G, a block SpMM) or one system per (problem, right-hand side)
+// pair (G read once per right-hand side by the leaner single-right-hand-side
+// kernel).  An autotuner times the groupings and the resident blocks per SM
+// on the first solve and keeps the fastest.
 
 #include <algorithm>
 #include <cmath>
@@ -24,11 +27,13 @@ struct cr_batch {
     std::vector<int64_t> n;         // unknowns per problem
     std::vector<double*> x64, r64;  // per problem [nrhs][n]
     std::vector<void*> x, r, p, q;
-    std::vector<crhyb::PSys> sys;
+    std::vector<crhyb::PSys> sys[2];  // [0]: one system per problem; [1]: one per right-hand side
+    std::vector<int2> pair[2];        // per (problem, rhs) pair: (system, right-hand side within it)
+    int group = 0;                    // the grouping in use
     cudaStream_t stream = nullptr;
     bool tuned = false;
-    int bps = 0;                    // chosen resident blocks per SM
-    double tune_ms[8] = {};         // autotuner: time per PCG iteration of each candidate (index = blocks per SM)
+    int bps = 0;                      // chosen resident blocks per SM
+    double tune_ms[2][8] = {};        // autotuner: time per PCG iteration of each candidate
 };
 
 namespace crhyb {
@@ -66,6 +71,7 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
     const bool ff = b->mode != 0;
     b->tuned = !(o && o->autotune);
     b->bps = o && o->blocks_per_sm > 0 ? o->blocks_per_sm : 0;
+    b->group = (o && o->rhs_grouping == 2) ? 1 : 0;
     for (int k = 0; k < nprob; ++k) {
         cr_hybrid* h = probs[k];
         if (!h) return bail(fail(CR_ERR_ARG, "cr_batch_create: NULL problem"));
@@ -120,9 +126,26 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
         sy.r = r;
         sy.p = p;
         sy.q = q;
-        b->sys.push_back(sy);
+        for (int r = 0; r < R; ++r) b->pair[0].push_back(make_int2(int(b->sys[0].size()), r));
+        b->sys[0].push_back(sy);
+        // the same problem as R single-right-hand-side systems
+        const size_t vb1 = ff ? sizeof(float2) : sizeof(double);
+        for (int k2 = 0; k2 < R; ++k2) {
+            PSys y = sy;
+            const size_t off = size_t(k2) * n;
+            y.R = 1;
+            y.b = h->S + off;
+            y.x64 = x64 + off;
+            y.r64 = r64 + off;
+            y.x = static_cast<char*>(x) + off * vb1;
+            y.r = static_cast<char*>(r) + off * vb1;
+            y.p = static_cast<char*>(p) + off * vb1;
+            y.q = static_cast<char*>(q) + off * vb1;
+            b->pair[1].push_back(make_int2(int(b->sys[1].size()), 0));
+            b->sys[1].push_back(y);
+        }
     }
-    int rc = b->plan.build(b->sys, b->d, b->mode, b->bps);
+    int rc = b->plan.build(b->sys[b->group], b->d, b->mode, b->bps);
     if (rc) return bail(rc);
     *out = b;
     return CR_OK;
@@ -131,6 +154,7 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
 extern "C" int cr_batch_info(const cr_batch* b, int32_t* nsys, int32_t* ntiles, int32_t* grid,
                              int32_t* blocks_per_sm) {
     if (!b) return fail(CR_ERR_ARG, "cr_batch_info: NULL batch");
+    // nsys: systems of the grouping in use (problems, or (problem, rhs) pairs)
     if (nsys) *nsys = b->plan.nsys;
     if (ntiles) *ntiles = b->plan.ntiles;
     if (grid) *grid = b->plan.grid;
@@ -160,26 +184,32 @@ extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* con
         return zero_vectors(b, s);
     };
     if (!b->tuned) {
-        // autotune the resident blocks per SM: a short run of each candidate from the
-        // start state, timed per PCG iteration; the fastest is kept for every later solve
-        const int maxb = std::min(b->plan.blocks_per_sm, 7);
+        // autotune the grouping of the right-hand sides and the resident blocks per SM:
+        // a short run of each candidate from the start state, timed per PCG iteration;
+        // the fastest is kept for every later solve
         double best = 1e30;
-        int best_b = maxb;
-        for (int cand = 1; cand <= maxb; ++cand) {
-            CR_TRY(b->plan.build(b->sys, b->d, b->mode, cand));
-            CR_TRY(start());
-            double ms = 0.0;
-            int64_t pit = 0;
-            CR_TRY(b->plan.run(o->tol, delta, 64, 64, s, nullptr, true, &ms, &pit));
-            const double per = pit > 0 ? ms / double(pit) : 1e30;
-            b->tune_ms[cand] = per;
-            if (per < best) {
-                best = per;
-                best_b = cand;
+        int best_g = b->group, best_b = 1;
+        for (int g = 0; g < 2; ++g) {
+            CR_TRY(b->plan.build(b->sys[g], b->d, b->mode, 0));
+            const int maxb = std::min(b->plan.blocks_per_sm, 7);
+            for (int cand = 1; cand <= maxb; ++cand) {
+                CR_TRY(b->plan.build(b->sys[g], b->d, b->mode, cand));
+                CR_TRY(start());
+                double ms = 0.0;
+                int64_t pit = 0;
+                CR_TRY(b->plan.run(o->tol, delta, 64, 64, s, nullptr, true, &ms, &pit));
+                const double per = pit > 0 ? ms / double(pit) : 1e30;
+                b->tune_ms[g][cand] = per;
+                if (per < best) {
+                    best = per;
+                    best_g = g;
+                    best_b = cand;
+                }
             }
         }
+        b->group = best_g;
         b->bps = best_b;
-        CR_TRY(b->plan.build(b->sys, b->d, b->mode, best_b));
+        CR_TRY(b->plan.build(b->sys[best_g], b->d, b->mode, best_b));
         b->tuned = true;
     }
     CR_TRY(start());
@@ -196,7 +226,8 @@ extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* con
     int j = 0;
     for (int k = 0; k < np; ++k)
         for (int r = 0; r < b->nrhs[k]; ++r, ++j) {
-            const PScal& P = b->plan.h_scal[size_t(k) * kPMaxRhs + r];
+            const int2 pr = b->pair[b->group][size_t(j)];
+            const PScal& P = b->plan.h_scal[size_t(pr.x) * kPMaxRhs + pr.y];
             int status = P.status;
             if (status == CR_OK && !P.conv) status = CR_ERR_NOT_CONVERGED;
             if (status != CR_OK && worst == CR_OK) worst = status;

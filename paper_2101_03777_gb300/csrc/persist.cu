@@ -73,6 +73,13 @@ __device__ __forceinline__ float2 sc_f2(const float2& v) { return __ldcg(&v); }
 
 // The d components of a face are adjacent: in 2D one 16-byte access moves both
 // (float-float pairs or FP64 values; the arrays are 16-byte aligned).
+//
+// Vectors written by other blocks in an earlier phase (the gathered p, x64)
+// are read with ordinary coherent loads, which may hit in L1: the grid barrier
+// orders them after those writes (release by the writers' fence and atomic,
+// acquire by the waiting thread's fence, then bar.sync for its block), the
+// same ordering a cooperative-groups grid sync gives.  Only the non-coherent
+// read-only path (ld.global.nc) would be unsafe here, and it is not used.
 __device__ __forceinline__ void ld2(const float2* p, float2 (&v)[2]) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     v[0] = make_float2(t.x, t.y);
@@ -284,7 +291,7 @@ __device__ __forceinline__ void block_partials(FFAcc (&af)[R][NQ], double (&ad)[
 
 // y_k = G p_k for the right-hand sides in amask, float-float (one face row).
 template <int D, int R, typename LT>
-__device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask, const float2* __restrict__ p,
+__device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask, const float2* p,
                                        float2 (&y)[R][D]) {
     constexpr int NS = 2 * D + 1;
     constexpr int NPV = NS * D * D;
@@ -296,7 +303,7 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
     for (int k = 0; k < R; ++k)
 #pragma unroll
         for (int i = 0; i < D; ++i) acc[k][i].zero();
-#pragma unroll
+#pragma unroll(R == 1 ? NS : 1)
     for (int s = 0; s < NS; ++s) {
         const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + sell(f, s - 1, 2 * D)));
         float h[D][D], l[D][D];
@@ -312,8 +319,7 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
         for (int k = 0; k < R; ++k) {
             if (!((amask >> k) & 1u)) continue;
             float2 xv[D];
-#pragma unroll
-            ldrow_cg<D>(p + k * N + c * D, xv);
+            ldrow<D>(p + k * N + c * D, xv);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -328,7 +334,7 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
 
 // y_k = G x_k in FP64 with the FP64 values (one face row).
 template <int D, int R>
-__device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, const double* __restrict__ x,
+__device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, const double* x,
                                       double (&y)[R][D]) {
     constexpr int NS = 2 * D + 1;
     constexpr int NPV = NS * D * D;
@@ -337,7 +343,7 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
     for (int k = 0; k < R; ++k)
 #pragma unroll
         for (int i = 0; i < D; ++i) y[k][i] = 0.0;
-#pragma unroll
+#pragma unroll(R == 1 ? NS : 1)
     for (int s = 0; s < NS; ++s) {
         const int64_t c = s == 0 ? f : int64_t(__ldcs(S.cols + sell(f, s - 1, 2 * D)));
         double v[D][D];
@@ -349,8 +355,7 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
         for (int k = 0; k < R; ++k) {
             if (!((amask >> k) & 1u)) continue;
             double xv[D];
-#pragma unroll
-            ldrow_cg<D>(x + k * N + c * D, xv);
+            ldrow<D>(x + k * N + c * D, xv);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -448,7 +453,7 @@ __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, PCtl*
 // at a time; the values of G are re-read from shared memory for each.
 template <int D, int R, int MODE>
 __device__ __forceinline__ void ff_row_staged(const unsigned char* buf, int r, int64_t f, unsigned amask,
-                                              const float2* __restrict__ p, int64_t N, float2 (&y)[R][D]) {
+                                              const float2* p, int64_t N, float2 (&y)[R][D]) {
     using G = Stage<D, MODE>;
     constexpr int NS = 2 * D + 1;
     const float* hi = reinterpret_cast<const float*>(buf + G::HI);
@@ -464,7 +469,7 @@ __device__ __forceinline__ void ff_row_staged(const unsigned char* buf, int r, i
             for (int s = 0; s < NS; ++s) {
                 const int64_t c = s == 0 ? f : int64_t(co[(s - 1) * kPBlock + r]);
 #pragma unroll
-                for (int j = 0; j < D; ++j) xv[s][j] = __ldcg(p + k * N + c * D + j);
+                for (int j = 0; j < D; ++j) xv[s][j] = p[k * N + c * D + j];
             }
 #pragma unroll
             for (int s = 0; s < NS; ++s)
@@ -490,7 +495,7 @@ __device__ __forceinline__ void ff_row_staged(const unsigned char* buf, int r, i
 // q = G x for one row from a staged tile, FP64 (right-hand sides outermost).
 template <int D, int R, int MODE>
 __device__ __forceinline__ void d_row_staged(const unsigned char* buf, int r, int64_t f, unsigned amask,
-                                             const double* __restrict__ x, int64_t N, double (&y)[R][D]) {
+                                             const double* x, int64_t N, double (&y)[R][D]) {
     using G = Stage<D, MODE>;
     constexpr int NS = 2 * D + 1;
     const double* v = reinterpret_cast<const double*>(buf + G::HI);
@@ -505,7 +510,7 @@ __device__ __forceinline__ void d_row_staged(const unsigned char* buf, int r, in
         for (int s = 0; s < NS; ++s) {
             const int64_t c = s == 0 ? f : int64_t(co[(s - 1) * kPBlock + r]);
 #pragma unroll
-            for (int j = 0; j < D; ++j) xv[s][j] = __ldcg(x + k * N + c * D + j);
+            for (int j = 0; j < D; ++j) xv[s][j] = x[k * N + c * D + j];
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s)
@@ -540,6 +545,7 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
     constexpr bool FF = MODE != kModeFP64;
     using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float>::type;
     PCtl* ctl = a.ctl;
+    if (int(blockIdx.x) == a.stall_block) return;   // testing hook (failure detection), see PArgs
     const int t0 = int(blockIdx.x) * a.tpb, t1 = min(t0 + a.tpb, a.ntiles);
     int piters = 0, epoch = a.epoch0;
     int ph[2] = {0, 0};   // phase parity of the two staging mbarriers
@@ -1270,6 +1276,11 @@ int PersistPlan::run(double tol, double delta, int max_it, int iters, cudaStream
     a.iters = iters > 0 ? iters : 1 << 30;
     a.epoch0 = 0;
     a.phase_ns = profile ? d_phase : nullptr;
+    // Failure-detection test hook: CRHYB_TEST_STALL_BLOCK=<block> makes that block skip the
+    // solve; every other block's barrier wait then runs out (bounded) and the call returns
+    // CR_ERR_TIMEOUT with the context intact.  Nothing faults or hangs.
+    a.stall_block = -1;
+    if (const char* sb = std::getenv("CRHYB_TEST_STALL_BLOCK")) a.stall_block = std::atoi(sb);
     if (profile) CR_CUDA(cudaMemsetAsync(d_phase, 0, sizeof(unsigned long long) * 8, st));
     LaunchFn l = reinterpret_cast<LaunchFn>(launch);
     int idle = 0;

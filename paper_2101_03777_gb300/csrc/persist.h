@@ -60,6 +60,8 @@ struct PArgs {
     double tol, delta;
     int max_it, iters, epoch0;
     unsigned long long* phase_ns;   // profile runs: time per phase (U1 U2 U3 P1 P2 P3), else NULL
+    int stall_block;                // testing hook: this block leaves at once (-1: none), so that the
+                                    // others' bounded barrier waits run out
 };
 
 // A launch plan for one list of systems (all with the same d and arithmetic).

@@ -267,6 +267,22 @@ def test_persistent_tiny_mesh_limits_and_warm_start():
     assert st2["status"] == 0 and st2["iterations"] <= 1
 
 
+def test_persistent_barrier_timeout_is_reported(monkeypatch):
+    """Failure detection without a fault: a block that leaves at once makes the
+    other blocks' bounded grid-barrier waits run out; the solve returns
+    CR_ERR_TIMEOUT and the context stays usable for the next solve."""
+    case = make_case("2d_perturbed_37")
+    _, _, hyb = gpu_setup(case)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    monkeypatch.setenv("CRHYB_TEST_STALL_BLOCK", "0")
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, tol=1e-10, prec="ff", persistent=True)
+    assert ei.value.name == "CR_ERR_TIMEOUT"
+    monkeypatch.delenv("CRHYB_TEST_STALL_BLOCK")
+    st = crhyb.cr_solve(hyb, W, tol=1e-10, prec="ff", persistent=True)
+    assert st["status"] == 0 and st["relres"] <= 1e-10
+
+
 def test_second_rhs_and_host_buffers():
     case = make_case("2d_perturbed_37")
     coords, elems, nu, mu, conv, fbar, w = case
