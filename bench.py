@@ -103,6 +103,17 @@ def solve_opts(prec, tol, graph, profile, persistent):
     return o
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest of the ranks' values (each rank times its own replica; the job
+    takes as long as the slowest).  world 1 returns the value unchanged."""
+    if world <= 1:
+        return float(value)
+    import torch
+    x = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+    return float(x.item())
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -312,10 +323,7 @@ def run_ours(args, rank, world):
             e2e.append(time.perf_counter() - t0)
 
     def agg(v):
-        x = torch.tensor([v], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        return float(x.item())
+        return max_over_ranks(v, world)
 
     N = n
 

@@ -92,7 +92,11 @@ typedef struct cr_params {
  *   FF_BF16     the same with the low plane of G stored in BF16 (6 bytes per value). */
 enum cr_prec { CR_PREC_FP64 = 0, CR_PREC_MIXED_FP32 = 1, CR_PREC_MIXED_BF16 = 2, CR_PREC_FF = 3,
                CR_PREC_FF_BF16 = 4 };
-enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1 };
+/* Krylov method: PCG (G symmetric positive definite: mu > 0, b_h = 0, Section 3.2 item 6);
+ * restarted GMRES(m) with right Jacobi preconditioning (Section 4.3); BiCGStab with right
+ * Jacobi preconditioning (van der Vorst), FP64, for nonsymmetric G where restarted GMRES with
+ * a Jacobi preconditioner stalls (the Newton/Oseen steps on fine meshes). */
+enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1, CR_METHOD_BICGSTAB = 2 };
 
 typedef struct cr_hyb_opts {
     int32_t keep_fp32;  /* also keep FP32 values of G (needed by CR_PREC_MIXED_FP32) */
@@ -244,14 +248,15 @@ typedef struct cr_batch cr_batch;
 
 typedef struct cr_batch_opts {
     int32_t prec;          /* CR_PREC_FP64, CR_PREC_FF or CR_PREC_FF_BF16 (values kept by cr_hybridise) */
-    int32_t autotune;      /* 1: the first solve times both right-hand-side groupings and 1..7 resident
+    int32_t autotune;      /* 1: the first solve times the right-hand-side groupings and 1..7 resident
                               blocks per SM (64 iterations each, from the start state) and keeps the
                               fastest for every later solve */
     int32_t blocks_per_sm; /* > 0: cap on the resident blocks per SM (default: the occupancy limit) */
     int32_t rhs_grouping;  /* 0 or 1: the right-hand sides of a problem share each pass over its G (one
                               system per problem); 2: one system per (problem, right-hand side) pair,
-                              G read once per right-hand side by the single-right-hand-side kernel.
-                              With autotune = 1 both groupings are timed and the faster is kept */
+                              G read once per right-hand side by the single-right-hand-side kernel;
+                              3: one system per two right-hand sides.  With autotune = 1 the three
+                              groupings are timed and the fastest is kept */
 } cr_batch_opts;
 
 /* Plan a batch over nprob hybridised systems of one dimension.  The handles

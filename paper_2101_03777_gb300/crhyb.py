@@ -25,7 +25,7 @@ CR_ERR = {
 }
 CONV = {"none": 0, "newton": 1, "oseen": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_bf16": 2, "ff": 3, "ff_bf16": 4}
-METHOD = {"pcg": 0, "gmres": 1}
+METHOD = {"pcg": 0, "gmres": 1, "bicgstab": 2}
 CR_MAX_RESTART = 64
 
 

@@ -105,6 +105,14 @@ int ensure_workspace(cr_hybrid* h, bool gmres, int restart, int prec) {
         CR_CUDA(cudaMalloc(&h->Z64, sizeof(double) * n));
         h->ws_restart = restart;
     }
+    if (prec == -1 && !h->bs_rh) {   // BiCGStab
+        CR_TRY(h->arena.alloc_n(&h->bs_rh, n));
+        CR_TRY(h->arena.alloc_n(&h->bs_v, n));
+        CR_TRY(h->arena.alloc_n(&h->bs_y, n));
+        CR_TRY(h->arena.alloc_n(&h->bs_s, n));
+        CR_TRY(h->arena.alloc_n(&h->bs_z, n));
+        CR_TRY(h->arena.alloc_n(&h->bs_t, n));
+    }
     if ((prec == CR_PREC_FF || prec == CR_PREC_FF_BF16) && !h->xf) {
         CR_TRY(h->arena.alloc_n(&h->xf, n));
         CR_TRY(h->arena.alloc_n(&h->rf, n));
@@ -300,7 +308,10 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     if (st) std::memset(st, 0, sizeof(*st));
     if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
     if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve: rhs out of range");
-    if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve: bad method");
+    if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES && o->method != CR_METHOD_BICGSTAB)
+        return fail(CR_ERR_ARG, "cr_solve: bad method");
+    if (o->method == CR_METHOD_BICGSTAB && o->prec != CR_PREC_FP64)
+        return fail(CR_ERR_ARG, "cr_solve: BiCGStab runs in FP64");
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_MIXED_FP32 && o->prec != CR_PREC_MIXED_BF16 &&
         o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve: bad precision");
@@ -312,6 +323,7 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     const size_t n = size_t(m->nf) * m->d;
     StreamScope scope(m);
     CR_TRY(ensure_workspace(h, o->method == CR_METHOD_GMRES, restart, o->prec));
+    if (o->method == CR_METHOD_BICGSTAB) CR_TRY(ensure_workspace(h, false, restart, -1));
     double* Wd = W;
     const bool host = !is_device_pointer(W);
     if (host) {

@@ -4,12 +4,14 @@
 // cooperative launch (persist.cu).  The right-hand sides of a mesh share
 // every pass over its G.
 //
-// The plan lays the problems' tiles end to end.  Two groupings of the
+// The plan lays the problems' tiles end to end.  Three groupings of the
 // right-hand sides: one system per problem (its right-hand sides share each
-// pass over G, a block SpMM) or one system per (problem, right-hand side)
-// pair (G read once per right-hand side by the leaner single-right-hand-side
-// kernel).  An autotuner times the groupings and the resident blocks per SM
-// on the first solve and keeps the fastest.
+// pass over G, a block SpMM), one system per pair of right-hand sides, or one
+// system per (problem, right-hand side) (G read once per right-hand side by the
+// leanest kernel).  Fewer right-hand sides per system need fewer registers and
+// let more blocks reside on an SM; more share more of G's traffic.  An
+// autotuner times the groupings and the resident blocks per SM on the first
+// solve and keeps the fastest.
 
 #include <algorithm>
 #include <cmath>
@@ -27,13 +29,14 @@ struct cr_batch {
     std::vector<int64_t> n;         // unknowns per problem
     std::vector<double*> x64, r64;  // per problem [nrhs][n]
     std::vector<void*> x, r, p, q;
-    std::vector<crhyb::PSys> sys[2];  // [0]: one system per problem; [1]: one per right-hand side
-    std::vector<int2> pair[2];        // per (problem, rhs) pair: (system, right-hand side within it)
+    std::vector<crhyb::PSys> sys[3];  // [0]: one system per problem; [1]: one per right-hand side;
+                                      // [2]: one per two right-hand sides
+    std::vector<int2> pair[3];        // per (problem, rhs) pair: (system, right-hand side within it)
     int group = 0;                    // the grouping in use
     cudaStream_t stream = nullptr;
     bool tuned = false;
     int bps = 0;                      // chosen resident blocks per SM
-    double tune_ms[2][8] = {};        // autotuner: time per PCG iteration of each candidate
+    double tune_ms[3][8] = {};        // autotuner: time per PCG iteration of each candidate
 };
 
 namespace crhyb {
@@ -71,7 +74,7 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
     const bool ff = b->mode != 0;
     b->tuned = !(o && o->autotune);
     b->bps = o && o->blocks_per_sm > 0 ? o->blocks_per_sm : 0;
-    b->group = (o && o->rhs_grouping == 2) ? 1 : 0;
+    b->group = (o && o->rhs_grouping == 2) ? 1 : ((o && o->rhs_grouping == 3) ? 2 : 0);
     for (int k = 0; k < nprob; ++k) {
         cr_hybrid* h = probs[k];
         if (!h) return bail(fail(CR_ERR_ARG, "cr_batch_create: NULL problem"));
@@ -144,6 +147,21 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
             b->pair[1].push_back(make_int2(int(b->sys[1].size()), 0));
             b->sys[1].push_back(y);
         }
+        // and as systems of two right-hand sides (the last may have one)
+        for (int k2 = 0; k2 < R; k2 += 2) {
+            PSys y = sy;
+            const size_t off = size_t(k2) * n;
+            y.R = std::min(2, R - k2);
+            y.b = h->S + off;
+            y.x64 = x64 + off;
+            y.r64 = r64 + off;
+            y.x = static_cast<char*>(x) + off * vb1;
+            y.r = static_cast<char*>(r) + off * vb1;
+            y.p = static_cast<char*>(p) + off * vb1;
+            y.q = static_cast<char*>(q) + off * vb1;
+            for (int j2 = 0; j2 < y.R; ++j2) b->pair[2].push_back(make_int2(int(b->sys[2].size()), j2));
+            b->sys[2].push_back(y);
+        }
     }
     int rc = b->plan.build(b->sys[b->group], b->d, b->mode, b->bps);
     if (rc) return bail(rc);
@@ -189,7 +207,7 @@ extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* con
         // the fastest is kept for every later solve
         double best = 1e30;
         int best_g = b->group, best_b = 1;
-        for (int g = 0; g < 2; ++g) {
+        for (int g = 0; g < 3; ++g) {
             CR_TRY(b->plan.build(b->sys[g], b->d, b->mode, 0));
             const int maxb = std::min(b->plan.blocks_per_sm, 7);
             for (int cand = 1; cand <= maxb; ++cand) {

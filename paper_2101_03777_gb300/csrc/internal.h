@@ -134,6 +134,8 @@ struct cr_hybrid {
     double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *b64 = nullptr;
     float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     float2 *xf = nullptr, *rf = nullptr, *pf = nullptr, *qf = nullptr;  // float-float PCG vectors
+    double *bs_rh = nullptr, *bs_v = nullptr, *bs_y = nullptr, *bs_s = nullptr, *bs_z = nullptr,
+           *bs_t = nullptr;       // BiCGStab: shadow residual, A y, M p, s, M s, A z
     float* V32 = nullptr;         // GMRES basis [restart+1][N]
     double* V64 = nullptr;        // GMRES basis FP64 [restart+1][N]
     float* Z32 = nullptr;         // GMRES scratch vector

@@ -610,8 +610,9 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                     double bs[R][3], tot[R][3];
                     block_partials<R, 3, false>(af, ad, bs);
                     if (system_flush<R, 3>(a, S, cur, bs, tot) && threadIdx.x == 0) {
-                        for (int k = 0; k < S.R; ++k) {
-                            if (!((umask >> k) & 1u)) continue;
+#pragma unroll
+                        for (int k = 0; k < R; ++k) {
+                            if (k >= S.R || !((umask >> k) & 1u)) continue;
                             PScal& P = a.scal[cur * kPMaxRhs + k];
                             const double rr = tot[k][0], bb = tot[k][1], rz = tot[k][2];
                             const double target = a.tol * a.tol * bb;
@@ -743,8 +744,9 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                 double bs[R][1], tot[R][1];
                 block_partials<R, 1, FF>(af, ad, bs);
                 if (system_flush<R, 1>(a, S, cur, bs, tot) && threadIdx.x == 0) {
-                    for (int k = 0; k < S.R; ++k) {
-                        if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (k >= S.R || !((amask >> k) & 1u)) continue;
                         PScal& P = a.scal[cur * kPMaxRhs + k];
                         const double pq = tot[k][0];
                         if (!(pq > 0.0) || !isfinite(pq)) {
@@ -894,8 +896,9 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                 double bs[R][2], tot[R][2];
                 block_partials<R, 2, FF>(af, ad, bs);
                 if (system_flush<R, 2>(a, S, cur, bs, tot) && threadIdx.x == 0) {
-                    for (int k = 0; k < S.R; ++k) {
-                        if (!((amask >> k) & 1u)) continue;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (k >= S.R || !((amask >> k) & 1u)) continue;
                         PScal& P = a.scal[cur * kPMaxRhs + k];
                         const double rz = tot[k][0], rr = tot[k][1];
                         const double rz_old = sc_d(P.rz);
@@ -1108,11 +1111,19 @@ int PersistPlan::build(const std::vector<PSys>& systems, int d_, int mode_, int 
         for (int64_t t = 0; t < nt; ++t) tl.push_back(make_int2(s, int(t * kPBlock)));
     }
     ntiles = int(tl.size());
-    const int R = rmax <= 1 ? 1 : kPMaxRhs;
+    // kernels for 1, 2 or 4 right-hand sides per system
+    const int R = rmax <= 1 ? 1 : (rmax <= 2 ? 2 : kPMaxRhs);
     LaunchFn l = nullptr;
     OccFn o = nullptr;
-    if (d == 2) { if (R == 1) pick<2, 1>(mode, &l, &o); else pick<2, kPMaxRhs>(mode, &l, &o); }
-    else { if (R == 1) pick<3, 1>(mode, &l, &o); else pick<3, kPMaxRhs>(mode, &l, &o); }
+    if (d == 2) {
+        if (R == 1) pick<2, 1>(mode, &l, &o);
+        else if (R == 2) pick<2, 2>(mode, &l, &o);
+        else pick<2, kPMaxRhs>(mode, &l, &o);
+    } else {
+        if (R == 1) pick<3, 1>(mode, &l, &o);
+        else if (R == 2) pick<3, 2>(mode, &l, &o);
+        else pick<3, kPMaxRhs>(mode, &l, &o);
+    }
     launch = reinterpret_cast<void*>(l);
     int bps = 0;
     CR_TRY(o(&bps));

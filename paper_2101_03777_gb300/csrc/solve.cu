@@ -41,6 +41,7 @@ struct KScal {
     int pad_;
     float2 alpha_ff, beta_ff;                   // alpha and beta in float-float for the FF iteration
     double sigma;                               // FF vectors hold sigma * (the FP64 quantities)
+    double omega, rho_old, rr_min;              // BiCGStab (rr_min: the cycle's smallest r.r)
     double hb[CR_MAX_RESTART + 1];              // Gram-Schmidt coefficients of the current step
     double H[(CR_MAX_RESTART + 1) * CR_MAX_RESTART];
     double cs[CR_MAX_RESTART], sn[CR_MAX_RESTART], g[CR_MAX_RESTART + 1];
@@ -503,6 +504,139 @@ __global__ void __launch_bounds__(kBlock) k_ff_from64(int64_t n, const double* _
 }
 
 // ---------------------------------------------------------------------------
+// BiCGStab (van der Vorst 1992) with right Jacobi preconditioning, FP64:
+//   rho = rh.r, beta = (rho/rho_old)(alpha/omega), p = r + beta (p - omega v),
+//   y = M^{-1} p, v = G y, alpha = rho / rh.v, s = r - alpha v, z = M^{-1} s,
+//   t = G z, omega = t.s / t.t, x += alpha y + omega z, r = s - omega t.
+// ---------------------------------------------------------------------------
+
+// rh = r (the shadow residual), p = v = 0; rho = r.r, rho_old = alpha = omega = 1.
+__global__ void __launch_bounds__(kBlock) k_bs_init(int64_t n, const double* __restrict__ r, double* __restrict__ rh,
+                                                   double* __restrict__ p, double* __restrict__ v, KScal* sc,
+                                                   RedBuf red) {
+    double part[1] = {0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double rk = r[k];
+        rh[k] = rk;
+        p[k] = 0.0;
+        v[k] = 0.0;
+        part[0] += rk * rk;
+    }
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        sc->rz = tot[0];
+        sc->rho_old = 1.0;
+        sc->alpha = 1.0;
+        sc->omega = 1.0;
+        sc->rr_min = tot[0];
+    }
+}
+
+// p = r + beta (p - omega v), y = M^{-1} p
+__global__ void __launch_bounds__(kBlock) k_bs_dir(int64_t n, const double* __restrict__ r, double* __restrict__ p,
+                                                  const double* __restrict__ v, const double* __restrict__ minv,
+                                                  double* __restrict__ y, const KScal* sc) {
+    if (sc->done) return;
+    const double omega = sc->omega, beta = (sc->rz / sc->rho_old) * (sc->alpha / omega);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double pk = fma(beta, p[k] - omega * v[k], r[k]);
+        p[k] = pk;
+        y[k] = minv[k] * pk;
+    }
+}
+
+// out = G in and its dot products.  which = 0: rh.out -> alpha = rho / rh.out;
+// which = 1: out.s and out.out -> omega = out.s / out.out.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_bs_spmv(int64_t nf, const int32_t* __restrict__ cols,
+                                                   const double* __restrict__ vals, const double* __restrict__ in,
+                                                   double* __restrict__ out, const double* __restrict__ w,
+                                                   KScal* sc, RedBuf red, int which) {
+    if (sc->done) return;
+    double part[2] = {0.0, 0.0};
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        double y[D];
+        ell_row<D, double, double, double>(f, cols, vals, in, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            out[f * D + i] = y[i];
+            part[0] += w[f * D + i] * y[i];
+            part[1] += y[i] * y[i];
+        }
+    }
+    double tot[2];
+    if (grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        if (which == 0) {
+            if (!(tot[0] != 0.0) || !isfinite(tot[0])) {
+                sc->status = CR_ERR_BREAKDOWN;
+                sc->done = 1;
+            } else {
+                sc->alpha = sc->rz / tot[0];
+            }
+        } else {
+            sc->omega = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+            if (!isfinite(sc->omega)) {
+                sc->status = CR_ERR_BREAKDOWN;
+                sc->done = 1;
+            }
+        }
+    }
+}
+
+// s = r - alpha v, z = M^{-1} s
+__global__ void __launch_bounds__(kBlock) k_bs_s(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
+                                                const double* __restrict__ minv, double* __restrict__ sv,
+                                                double* __restrict__ z, const KScal* sc) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double s = fma(-alpha, v[k], r[k]);
+        sv[k] = s;
+        z[k] = minv[k] * s;
+    }
+}
+
+// x += alpha y + omega z, r = s - omega t; rho' = rh.r, r.r; last block: the
+// iteration count, convergence, the limit, and breakdown (rho' or omega zero).
+__global__ void __launch_bounds__(kBlock) k_bs_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                     const double* __restrict__ y, const double* __restrict__ z,
+                                                     const double* __restrict__ sv, const double* __restrict__ t,
+                                                     const double* __restrict__ rh, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const double alpha = sc->alpha, omega = sc->omega;
+    double part[2] = {0.0, 0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] = fma(omega, z[k], fma(alpha, y[k], x[k]));
+        const double rk = fma(-omega, t[k], sv[k]);
+        r[k] = rk;
+        part[0] += rh[k] * rk;
+        part[1] += rk * rk;
+    }
+    double tot[2];
+    if (grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        sc->rho_old = sc->rz;
+        sc->rz = tot[0];
+        sc->rr = tot[1];
+        sc->it += 1;
+        if (!isfinite(tot[1])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        } else if (!(tot[0] != 0.0) || !(sc->omega != 0.0)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[1] > 1e8 * sc->rr_min) {
+            sc->done = 1;   // the residual grew 1e4-fold over the cycle's best: restart (status stays CR_OK)
+        }
+        sc->rr_min = fmin(sc->rr_min, tot[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // GMRES(m) kernels: Arnoldi with classical Gram-Schmidt applied twice (CGS2),
 // right Jacobi preconditioning: G M^{-1} z_j, x = x0 + M^{-1} V y.
 // ---------------------------------------------------------------------------
@@ -931,7 +1065,37 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                                                     h->red, 1, o->tol, 0.0);
         ++c.launches;
         CR_CUDA(cudaGetLastError());
-        if (o->method == CR_METHOD_PCG) {
+        if (o->method == CR_METHOD_BICGSTAB) {
+            auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                const int g = grid_for(c.nf);
+                k_bs_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->p64, h->bs_v, h->minv64, h->bs_y, c.sc);
+                if (e0) cudaEventRecord(e0, c.st);
+                k_bs_spmv<D><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->bs_y, h->bs_v, h->bs_rh, c.sc, h->red, 0);
+                if (e1) cudaEventRecord(e1, c.st);
+                k_bs_s<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->bs_v, h->minv64, h->bs_s, h->bs_z, c.sc);
+                k_bs_spmv<D><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->bs_z, h->bs_t, h->bs_s, c.sc, h->red, 1);
+                k_bs_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->bs_y, h->bs_z, h->bs_s, h->bs_t, h->bs_rh,
+                                                     c.sc, h->red);
+                c.launches += 5;
+            };
+            // The recursive residual of BiCGStab drifts from the true one on these
+            // ill-conditioned systems: when it meets the tolerance the FP64 true
+            // residual decides, and a shortfall restarts BiCGStab from the iterate
+            // (shadow residual = the true residual), up to max_outer times.
+            for (int restart = 0;; ++restart) {
+                k_bs_init<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->bs_rh, h->p64, h->bs_v, c.sc, h->red);
+                ++c.launches;
+                CR_TRY(pcg_loop(c, iter, chunk, graph, 5));
+                CR_TRY(read_scal(c));
+                if (c.hs->status != CR_OK) break;
+                k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, nullptr,
+                                                            h->minv64, c.sc, h->red, 1, o->tol, 0.0);
+                ++c.launches;
+                CR_TRY(read_scal(c));
+                if (c.hs->done || restart >= max_outer) break;
+                ++outer;
+            }
+        } else if (o->method == CR_METHOD_PCG) {
             k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
             ++c.launches;
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {

@@ -1,0 +1,112 @@
+"""Parity at the full sizes of the benchmark workloads, through the C-ABI.
+
+The oracle's direct solve does not reach these sizes, so the CUDA results are
+checked on properties that the oracle computes from the paper at any size:
+  * the coupled system of Eq. 10 assembled by the oracle, A U + D^t P = R with
+    P_{K_0} = 0: the relative residual of the GPU's recovered U and P is at
+    most 1e-7 (the hybridised solve stops at a relative residual of 1e-10; the
+    oracle's own solve to 1e-10 leaves 2.3e-9 at 128x128, growing with the
+    norm of A; a wrong U or P leaves a residual of order one);
+  * D U = 0 element by element (Section 3.2, item 2) to rounding (1e-8 of
+    max|D| max|U|), and the face jumps |U_K - U_L| (Eq. 15), which equal the
+    entries of S - G W, below 2e-10 ||S||;
+  * the relative residual of the GPU's W in the oracle's own G and S (2D
+    workloads, whose G the oracle assembles in seconds) at most 1.01e-10 for
+    PCG (1e-9 for GMRES, which accepts a final true residual within 10 x the
+    tolerance);
+  * 2000 seeded rows of the exported G and entries of S against the
+    oracle's, to 1e-11 of the largest entry (the element inverses of T_K on the
+    perturbed 512x512 mesh have condition numbers near 3e3, so the two FP64
+    evaluation orders differ by about 1e-12 of max|G|).
+The solves run as bench.py times them: persistent float-float and FP64
+Jacobi-PCG for transient Stokes; BiCGStab for the Newton step (Jacobi-GMRES(30)
+does not reach 1e-10 on it: 28,538 iterations at 64x64, and no convergence
+within 60,000 at 128x128).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import coupled, hybrid, pipeline, topology
+from paper_2101_03777_gb300 import crhyb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def problem(name):
+    p = synth.config_problem(name)
+    w = None
+    if name == "cfg5":
+        p["mu"] = 1000.0          # a transient Newton step (dt = 1e-3), as the benchmark runs it
+        p["conv"] = "newton"
+        t = topology.build_faces(p["elems"])
+        w = synth.stream_velocity(p["coords"][t["face_vertices"]].mean(axis=1), seed=3)
+    return p, w
+
+
+def oracle(name, with_g):
+    key = (name, with_g)
+    if key not in _ORACLE:
+        p, w = problem(name)
+        topo, geom, A_K, D_K, R_K = pipeline.setup(p["coords"], p["elems"], p["nu"], p["mu"], p["fbar"][0],
+                                                   p["conv"], w)
+        A, D, R = coupled.assemble(topo, A_K, D_K, R_K, 0)
+        out = {"A": A, "D": D, "R": R, "topo": topo, "geom": geom}
+        if with_g:
+            h = hybrid.hybridise(topo, A_K, D_K, R_K, p["mu"])
+            out["G"], out["S"] = h["G"], h["S"]
+        _ORACLE.clear()
+        _ORACLE[key] = out
+    return _ORACLE[key]
+
+
+CASES = [
+    ("cfg2", dict(method="pcg", prec="ff", persistent=True), True),
+    ("cfg2", dict(method="pcg", prec="fp64", persistent=True), True),
+    ("cfg3", dict(method="pcg", prec="fp64", persistent=True), False),
+    ("cfg3", dict(method="pcg", prec="ff", persistent=True), False),
+    ("cfg5", dict(method="bicgstab", prec="fp64"), True),
+]
+
+
+@pytest.mark.parametrize("name,opts,with_g", CASES, ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}" for c in CASES])
+def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
+    p, w = problem(name)
+    o = oracle(name, with_g)
+    mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
+    fb = torch.from_numpy(p["fbar"]).cuda()
+    wt = torch.from_numpy(w).cuda() if w is not None else None
+    hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=wt),
+                             keep_fp32=False, keep_ff=(opts["prec"] == "ff"))
+    n, ne, d = hyb.n, mesh.ne, mesh.dim
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve(hyb, W, tol=1e-10, max_iter=400000, **opts)
+    # PCG stops on the FP64 true residual; GMRES and BiCGStab on their recursive residual, then
+    # accept a true residual within 10 x the tolerance
+    relmax = 1.01e-10 if opts["method"] == "pcg" else 1e-9
+    assert st["status"] == 0 and st["relres"] <= relmax
+    U = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(ne, dtype=torch.float64, device="cuda")
+    jump = crhyb.cr_recover_up(hyb, W, U, P, normalise_p=False, jump=True)
+    Un, Pn, Wn = U.cpu().numpy(), P.cpu().numpy(), W.cpu().numpy()
+    assert Pn[0] == 0.0                                   # P_{K_0} = 0 with K_0 = element 0
+    # Eq. 10 in the oracle's assembly: [A D^t; D 0][U; P'] = [R; 0], P' = P without K_0
+    A, D, R = o["A"], o["D"], o["R"]
+    res = A @ Un + D.T @ Pn[1:] - R
+    assert np.linalg.norm(res) <= 1e-7 * np.linalg.norm(R)
+    assert np.abs(D @ Un).max() <= 1e-8 * abs(D).max() * np.abs(Un).max()
+    if with_g:
+        G, S = o["G"], o["S"]
+        assert np.linalg.norm(S - G @ Wn) <= relmax * np.linalg.norm(S)
+        assert jump <= 2 * relmax * np.linalg.norm(S)
+        # seeded rows of the exported G and entries of S against the oracle's
+        cols, vals, Sx = crhyb.cr_hybrid_export(hyb)
+        Gx = crhyb.ell_to_csr(cols, vals)
+        rows = np.random.default_rng(7).choice(n, size=2000, replace=False)
+        diff = (Gx[rows] - G[rows]).tocsr()
+        assert (abs(diff).max() if diff.nnz else 0.0) <= 1e-11 * abs(G).max()
+        assert np.abs(Sx[0].ravel()[rows] - S[rows]).max() <= 1e-11 * np.abs(S).max()

@@ -163,6 +163,10 @@ SOLVE_CASES = [
     ("3d_kuhn_5", dict(method="pcg", prec="fp64", persistent=True), 1e-9),
     ("3d_kuhn_5", dict(method="pcg", prec="ff", persistent=True), 1e-9),
     ("ns_newton_9", dict(method="gmres", prec="fp64"), 1e-9),
+    # BiCGStab (nonsymmetric Newton/Oseen systems, and the SPD case)
+    ("ns_newton_9", dict(method="bicgstab", prec="fp64"), 1e-9),
+    ("ns_oseen_9", dict(method="bicgstab", prec="fp64"), 1e-9),
+    ("2d_perturbed_37", dict(method="bicgstab", prec="fp64", use_graph=True), 1e-9),
     ("ns_newton_9", dict(method="gmres", prec="mixed"), 1e-8),
     ("ns_oseen_9", dict(method="gmres", prec="mixed"), 1e-8),
     # steady (mu = 0): full GMRES (restart >= N = 42), Jacobi-GMRES(30) stagnates there
@@ -347,6 +351,9 @@ def test_tiny_mesh_and_error_paths():
     assert ei.value.name == "CR_ERR_ARG"
     with pytest.raises(crhyb.CrError) as ei:
         crhyb.cr_solve(hyb, W, prec="ff", method="gmres")
+    assert ei.value.name == "CR_ERR_ARG"
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve(hyb, W, prec="mixed", method="bicgstab")   # BiCGStab runs in FP64
     assert ei.value.name == "CR_ERR_ARG"
     # iteration limit
     case = make_case("2d_perturbed_37")
