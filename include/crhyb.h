@@ -218,6 +218,34 @@ int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S)
  * CR_ERR_CUDA. */
 int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st);
 
+/* Solve G W = S (right-hand side `rhs` of h) by flexible GMRES(m) in FP64
+ * (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.6), right-
+ * preconditioned by an inner Jacobi-PCG solve with the SPD matrix G_pre of
+ * `pre` (the persistent PCG kernel of cr_solve):
+ *   z_j = PCG(G_pre, v_j) to relative residual inner_tol,  v_{j+1} from G z_j,
+ *   W = W_0 + Z y  (y minimises ||S - G W|| over the cycle).
+ * For the nonsymmetric Newton/Oseen systems (Section 4.3) `pre` is the
+ * transient Stokes system with the same mu and nu on the same mesh: G_pre^{-1} G
+ * departs from the identity only by the convection term, so the number of
+ * GMRES steps does not grow as the mesh is refined (Jacobi-preconditioned
+ * GMRES(30) stagnates on these systems beyond about 64x64 squares).
+ *   h     the system to solve (any conv, mu > 0 or mu = 0)
+ *   pre   hybridised on the same mesh handle with conv = NONE and mu > 0;
+ *         FF and FF_BF16 need the float-float values kept (keep_lo_fp32 or
+ *         keep_lo_bf16); its own S and W are untouched
+ *   opts  method GMRES; prec is the precision of the inner PCG (FP64, FF or
+ *         FF_BF16); restart m (default 30); tol on ||S - G W|| / ||S||;
+ *         inner_tol (default 0.1); max_iter caps the GMRES steps (default 1000);
+ *         use_x0 as for cr_solve; check_every x 64 inner iterations per launch
+ *   W     as for cr_solve
+ *   st    iterations = inner PCG iterations in total, outer = GMRES steps,
+ *         relres = FP64 relative residual of the returned W; with opts->profile,
+ *         spmv_ms and spmv_launches receive the inner persistent launches' time
+ *         and the PCG iterations they ran
+ * Returns CR_OK, CR_ERR_NOT_CONVERGED, CR_ERR_BREAKDOWN, CR_ERR_ARG, CR_ERR_CUDA. */
+int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* opts, double* W,
+                            cr_solve_stats* st);
+
 /* y = G x in FP64 (x, y float64 [nf_int][dim], device pointers). */
 int cr_apply_G(cr_hybrid* h, const double* x, double* y);
 

@@ -86,6 +86,8 @@ _SIGS = {
     "cr_hybridise": (_i32, [_vp, ctypes.POINTER(cr_hyb_opts), ctypes.POINTER(_vp)]),
     "cr_hybrid_export": (_i32, [_vp, _vp, _vp, _vp]),
     "cr_solve": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, ctypes.POINTER(cr_solve_stats)]),
+    "cr_solve_preconditioned": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(cr_solve_opts), _vp,
+                                       ctypes.POINTER(cr_solve_stats)]),
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
     "cr_recover_up": (_i32, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cr_destroy_hybrid": (None, [_vp]),
@@ -303,6 +305,24 @@ def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):
     return stats
 
 
+def cr_solve_preconditioned(hyb, pre, W, rhs=0, raise_on_error=True, **opts):
+    """Flexible GMRES on G W = S of `hyb`, preconditioned by inner PCG solves with
+    the SPD G of `pre` (same mesh).  opts as for cr_solve; method defaults to
+    "gmres" and prec (the inner PCG's precision) to "ff".  Returns the statistics
+    (iterations = inner PCG iterations, outer = GMRES steps)."""
+    opts.setdefault("method", "gmres")
+    opts.setdefault("prec", "ff")
+    o = make_solve_opts(**opts)
+    st = cr_solve_stats()
+    rc = load_library().cr_solve_preconditioned(hyb.handle, int(rhs), pre.handle, ctypes.byref(o),
+                                                _ptr(W, np.float64, hyb.n, "W"), ctypes.byref(st))
+    stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
+             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)), "kernel_launches": st.kernel_launches}
+    if rc != CR_OK and raise_on_error:
+        _check(rc)
+    return stats
+
+
 def cr_apply_G(hyb, x, y):
     _check(load_library().cr_apply_G(hyb.handle, _ptr(x, np.float64, hyb.n, "x"), _ptr(y, np.float64, hyb.n, "y")))
 
@@ -335,7 +355,8 @@ class Batch:
 
 def cr_batch_create(probs, prec="ff", autotune=False, blocks_per_sm=0, rhs_grouping=0):
     """Plan one persistent batched PCG over the hybridised problems `probs`
-    (rhs_grouping 1: right-hand sides of a problem share G; 2: one system per pair)."""
+    (rhs_grouping 1: right-hand sides of a problem share G; 2: one system per pair; 3: one system
+    per two right-hand sides)."""
     arr = (_vp * len(probs))(*[h.handle for h in probs])
     o = cr_batch_opts(PREC[prec], int(bool(autotune)), int(blocks_per_sm), int(rhs_grouping))
     h = _vp()

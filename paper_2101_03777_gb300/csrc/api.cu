@@ -340,6 +340,52 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     return rc;
 }
 
+extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* W,
+                                       cr_solve_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    if (!h || !pre || !o || !W) return fail(CR_ERR_ARG, "cr_solve_preconditioned: NULL argument");
+    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve_preconditioned: rhs out of range");
+    if (pre->m != h->m) return fail(CR_ERR_ARG, "cr_solve_preconditioned: pre must be hybridised on the same mesh");
+    if (pre->s->mu <= 0.0 || pre->s->conv != CR_CONV_NONE)
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: pre needs a transient Stokes system (mu > 0, b_h = 0), "
+                                "whose G is SPD");
+    if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_preconditioned: the outer method is GMRES");
+    if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG runs in FP64, FF or FF_BF16");
+    if ((o->prec == CR_PREC_FF && (!pre->val32 || !pre->vlo32)) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: the float-float values of pre were not kept");
+    if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve_preconditioned: tol must be > 0");
+    const int restart = o->restart > 0 ? o->restart : 30;
+    if (restart < 1 || restart > CR_MAX_RESTART)
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: restart must be in [1, CR_MAX_RESTART]");
+    cr_mesh* m = h->m;
+    const size_t n = size_t(m->nf) * m->d;
+    StreamScope scope(m);
+    CR_TRY(ensure_workspace(h, true, restart, CR_PREC_FP64));
+    CR_TRY(ensure_workspace(pre, false, 0, o->prec));
+    if (restart > h->fgz_m) {
+        if (h->fgz) cudaFree(h->fgz);
+        h->fgz = nullptr;
+        h->fgz_m = 0;
+        CR_CUDA(cudaMalloc(&h->fgz, sizeof(double) * n * restart));
+        h->fgz_m = restart;
+    }
+    double* Wd = W;
+    const bool host = !is_device_pointer(W);
+    if (host) {
+        CR_TRY(ensure_stage(h, n * sizeof(double)));
+        Wd = h->stage;
+        if (o->use_x0) CR_CUDA(cudaMemcpyAsync(Wd, W, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    }
+    int rc = solve_fgmres_impl(h, rhs, pre, o, Wd, st);
+    if (host) {
+        cudaError_t e = cudaMemcpyAsync(W, Wd, n * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess && rc == CR_OK) rc = cuda_fail(e, "cr_solve_preconditioned: copy of W");
+    }
+    return rc;
+}
+
 extern "C" int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise_p,
                              double* jump) {
     if (!h || !W || !U || !P) return fail(CR_ERR_ARG, "cr_recover_up: NULL argument");
@@ -387,6 +433,7 @@ extern "C" void cr_destroy_hybrid(cr_hybrid* h) {
     if (h->V64) cudaFree(h->V64);
     if (h->Z32) cudaFree(h->Z32);
     if (h->Z64) cudaFree(h->Z64);
+    if (h->fgz) cudaFree(h->fgz);
     if (h->stage) cudaFree(h->stage);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete h;

@@ -140,6 +140,8 @@ struct cr_hybrid {
     double* V64 = nullptr;        // GMRES basis FP64 [restart+1][N]
     float* Z32 = nullptr;         // GMRES scratch vector
     double* Z64 = nullptr;
+    double* fgz = nullptr;        // flexible GMRES: preconditioned vectors FP64 [restart][N]
+    int fgz_m = 0;
     void* scal = nullptr;         // device Krylov scalars
     void* h_scal = nullptr;       // pinned host mirror
     double* pvol = nullptr;       // recovery scratch
@@ -165,6 +167,8 @@ int launch_recover(cr_hybrid* h, int rhs, const double* W, double* U, double* P,
                    double* jump_dev, cudaStream_t st);
 int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st);
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st);
+int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* Wdev,
+                      cr_solve_stats* st);
 void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 

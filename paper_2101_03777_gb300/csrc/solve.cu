@@ -41,7 +41,7 @@ struct KScal {
     int pad_;
     float2 alpha_ff, beta_ff;                   // alpha and beta in float-float for the FF iteration
     double sigma;                               // FF vectors hold sigma * (the FP64 quantities)
-    double omega, rho_old, rr_min;              // BiCGStab (rr_min: the cycle's smallest r.r)
+    double omega, rho_old;                      // BiCGStab
     double hb[CR_MAX_RESTART + 1];              // Gram-Schmidt coefficients of the current step
     double H[(CR_MAX_RESTART + 1) * CR_MAX_RESTART];
     double cs[CR_MAX_RESTART], sn[CR_MAX_RESTART], g[CR_MAX_RESTART + 1];
@@ -528,7 +528,6 @@ __global__ void __launch_bounds__(kBlock) k_bs_init(int64_t n, const double* __r
         sc->rho_old = 1.0;
         sc->alpha = 1.0;
         sc->omega = 1.0;
-        sc->rr_min = tot[0];
     }
 }
 
@@ -629,10 +628,7 @@ __global__ void __launch_bounds__(kBlock) k_bs_update(int64_t n, double* __restr
         } else if (!(tot[0] != 0.0) || !(sc->omega != 0.0)) {
             sc->status = CR_ERR_BREAKDOWN;
             sc->done = 1;
-        } else if (tot[1] > 1e8 * sc->rr_min) {
-            sc->done = 1;   // the residual grew 1e4-fold over the cycle's best: restart (status stays CR_OK)
         }
-        sc->rr_min = fmin(sc->rr_min, tot[1]);
     }
 }
 
@@ -798,6 +794,17 @@ __global__ void __launch_bounds__(kBlock) k_gm_update(int64_t n, XT* __restrict_
         double s = 0.0;
         for (int i = 0; i < k; ++i) s += sc->y[i] * double(V[size_t(i) * n + q]);
         x[q] = XT(double(x[q]) + double(minv[q]) * s);
+    }
+}
+
+// x += Z y (flexible GMRES: the preconditioned vectors are stored)
+__global__ void __launch_bounds__(kBlock) k_fgm_update(int64_t n, double* __restrict__ x, const double* __restrict__ Z,
+                                                       const KScal* sc) {
+    const int k = sc->j;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += sc->y[i] * Z[size_t(i) * n + q];
+        x[q] += s;
     }
 }
 
@@ -971,12 +978,15 @@ int gmres_loop(Ctx& c, const VT* vals, const XT* minv, const XT* b, XT* x, XT* r
 }
 
 // PCG in one cooperative persistent launch per chunk of iterations
-// (persist.cu): FP64, or float-float with FP64 reliable updates.
+// (persist.cu): FP64 (mode 0), or float-float with FP64 reliable updates
+// (mode 1: FP32 low plane, mode 2: BF16 low plane).  Solves G x = b for one
+// right-hand side b (device, FP64 [nf][d]) from x0 (or 0) and writes the FP64
+// iterate to x; *out receives the pair's final scalars.
 template <int D>
-int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+int persistent_pcg(Ctx& c, const double* b, const double* x0, double* x, int mode, double tol, double delta,
+                   int max_it, int per_launch, bool profile, PScal* out, double* kms, int64_t* kit) {
+    cr_hybrid* h = c.h;
     cr_mesh* m = h->m;
-    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D, false};
-    const int mode = o->prec == CR_PREC_FP64 ? 0 : (o->prec == CR_PREC_FF ? 1 : 2);
     const bool ff = mode != 0;
     if (ff && (!h->val32 || (mode == 2 && !h->vlo16) || (mode == 1 && !h->vlo32)))
         return fail(CR_ERR_ARG, "cr_solve: the float-float values were not kept by cr_hybridise");
@@ -989,7 +999,7 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
     sy.v64 = h->val64;
     sy.minv32 = h->minv32;
     sy.minv64 = h->minv64;
-    sy.b = h->S + size_t(rhs) * c.n;
+    sy.b = b;
     sy.x64 = h->x64;
     sy.r64 = h->r64;
     if (ff) { sy.x = h->xf; sy.r = h->rf; sy.p = h->pf; sy.q = h->qf; }
@@ -999,7 +1009,7 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
     if (!plan->built()) CR_TRY(plan->build({sy}, D, mode, 0));
     else CR_TRY(plan->update_systems({sy}, c.st));
     // start: x64 = x0 (or 0), iteration vectors zero
-    if (o->use_x0) CR_CUDA(cudaMemcpyAsync(h->x64, W, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    if (x0) CR_CUDA(cudaMemcpyAsync(h->x64, x0, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
     else CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
     if (ff) {
         CR_CUDA(cudaMemsetAsync(h->xf, 0, sizeof(float2) * c.n, c.st));
@@ -1007,18 +1017,32 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
     } else {
         CR_CUDA(cudaMemsetAsync(h->p64, 0, sizeof(double) * c.n, c.st));
     }
-    const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (mode == 2 ? 0.1 : 0.01);
+    CR_TRY(plan->run(tol, delta, max_it, per_launch, c.st, &c.launches, profile, kms, kit));
+    *out = plan->h_scal[0];
+    // x = x64, whose FP64 residual the last update phase computed
+    CR_CUDA(cudaMemcpyAsync(x, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    return CR_OK;
+}
+
+double default_delta(int mode) { return mode == 2 ? 0.1 : 0.01; }
+int persistent_mode(int prec) { return prec == CR_PREC_FP64 ? 0 : (prec == CR_PREC_FF ? 1 : 2); }
+
+template <int D>
+int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    cr_mesh* m = h->m;
+    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D, false};
+    const int mode = persistent_mode(o->prec);
+    const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : default_delta(mode);
     const int gmax = o->max_iter > 0 ? o->max_iter : 100000;
     const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
     double kms = 0.0;
     int64_t kit = 0;
-    CR_TRY(plan->run(o->tol, delta, gmax, per_launch, c.st, &c.launches, o->profile != 0, &kms, &kit));
-    const PScal& P = plan->h_scal[0];
+    PScal P{};
+    CR_TRY(persistent_pcg<D>(c, h->S + size_t(rhs) * c.n, o->use_x0 ? W : nullptr, W, mode, o->tol, delta, gmax,
+                             per_launch, o->profile != 0, &P, &kms, &kit));
+    CR_CUDA(cudaStreamSynchronize(c.st));
     int status = P.status;
     if (status == CR_OK && !P.conv) status = CR_ERR_NOT_CONVERGED;
-    // W = x64, whose FP64 residual the last update phase computed
-    CR_CUDA(cudaMemcpyAsync(W, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
-    CR_CUDA(cudaStreamSynchronize(c.st));
     const double relres = P.bb > 0 ? std::sqrt(P.orr / P.bb) : 0.0;
     if (status == CR_OK && !(relres <= o->tol) && !(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
     if (st) {
@@ -1033,6 +1057,114 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
     }
     if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve: iteration limit reached before the tolerance");
     if (status == CR_ERR_BREAKDOWN) return fail(status, "cr_solve: Krylov breakdown (p.Gp <= 0 or NaN)");
+    return status;
+}
+
+// Flexible GMRES(m) in FP64 (Saad, Iterative Methods for Sparse Linear
+// Systems, Algorithm 9.6) on G W = S, right-preconditioned by an inner
+// Jacobi-PCG solve with the SPD matrix of `pre` (persistent kernel, FP64 or
+// float-float), each to the relative residual inner_tol:
+//   z_j = PCG(G_pre, v_j),  v_{j+1} = G z_j orthogonalised (CGS2),  x = x0 + Z y.
+// A preconditioner that changes from step to step is what the flexible form
+// allows; the minimised residual is still that of G.
+template <int D>
+int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    cr_mesh* m = h->m;
+    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D, false};
+    Ctx cp{pre, m->stream, static_cast<KScal*>(pre->scal), static_cast<KScal*>(pre->h_scal), m->nf, m->nf * D, D,
+           false};
+    const double* b = h->S + size_t(rhs) * c.n;
+    const int g = grid_for(c.nf), gn = grid_for(c.n);
+    const int mode = persistent_mode(o->prec);
+    const double itol = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : 0.1;
+    const int gmax = o->max_iter > 0 ? o->max_iter : 1000;
+    const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
+    double* V = h->V64;
+    double* Z = h->fgz;
+    std::memset(c.hs, 0, sizeof(KScal));
+    c.hs->max_it = gmax;
+    c.hs->m = o->restart > 0 ? o->restart : 30;
+    CR_CUDA(cudaMemcpyAsync(c.sc, c.hs, sizeof(KScal), cudaMemcpyHostToDevice, c.st));
+    if (o->use_x0) CR_CUDA(cudaMemcpyAsync(h->x64, W, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    else CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
+    // tol2 = tol^2 ||b||^2 from the FP64 residual of the start
+    k_residual64<D><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, nullptr, h->minv64, c.sc,
+                                            h->red, 1, o->tol, 0.0);
+    ++c.launches;
+    CR_CUDA(cudaGetLastError());
+    int64_t inner_its = 0, prof_it = 0;
+    double prof_ms = 0.0;
+    int status = CR_OK;
+    for (;;) {
+        k_residual_w<D, double, double><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, h->r64, c.sc);
+        k_gm_norm_start<double><<<gn, kBlock, 0, c.st>>>(c.n, h->r64, c.sc, h->red);
+        k_gm_scale_v0<double><<<gn, kBlock, 0, c.st>>>(c.n, h->r64, V, c.sc);
+        c.launches += 3;
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->done) break;
+        const int mr = c.hs->m;
+        for (int j = 0; j < mr; ++j) {
+            PScal P{};
+            double kms = 0.0;
+            int64_t kit = 0;
+            CR_TRY(persistent_pcg<D>(cp, V + size_t(j) * c.n, nullptr, Z + size_t(j) * c.n, mode, itol,
+                                     default_delta(mode), 100000, per_launch, o->profile != 0, &P, &kms, &kit));
+            inner_its += P.it;
+            prof_ms += kms;
+            prof_it += kit;
+            if (P.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+            k_gm_spmv<D, double, double><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, Z + size_t(j) * c.n, V,
+                                                                 c.sc);
+            ++c.launches;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i0 = 0; i0 <= j; i0 += kRedSlots) {
+                    k_gm_dots<double><<<gn, kBlock, 0, c.st>>>(c.n, V, i0, c.sc, h->red);
+                    ++c.launches;
+                }
+                k_gm_orth<double><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc, h->red, pass);
+                ++c.launches;
+            }
+            k_gm_normalise<double><<<gn, kBlock, 0, c.st>>>(c.n, V, c.sc);
+            ++c.launches;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            if (c.hs->done || c.hs->stop) break;
+        }
+        if (status != CR_OK) break;
+        // x += Z y over the steps taken in this cycle
+        k_gm_solve_y<<<1, 32, 0, c.st>>>(c.sc);
+        k_fgm_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, Z, c.sc);
+        c.launches += 2;
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->status != CR_OK) break;
+    }
+    c.launches += cp.launches;
+    CR_TRY(read_scal(c));
+    if (status == CR_OK) status = c.hs->status;
+    const int steps = c.hs->it;
+    // W = x; final FP64 residual of the returned W
+    CR_CUDA(cudaMemcpyAsync(W, h->x64, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
+    k_residual64<D><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, h->x64, nullptr, nullptr, h->minv64, c.sc,
+                                            h->red, 0, o->tol, 0.0);
+    ++c.launches;
+    CR_CUDA(cudaGetLastError());
+    CR_TRY(read_scal(c));
+    const double relres = c.hs->obb > 0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
+    if (status == CR_OK && !(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
+    if (st) {
+        st->iterations = int32_t(inner_its);
+        st->outer = steps;
+        st->relres = relres;
+        st->status = status;
+        // profile: the inner persistent launches' time and the PCG iterations they ran
+        st->spmv_launches = int32_t(prof_it);
+        st->spmv_ms = prof_ms;
+        st->kernel_launches = c.launches;
+    }
+    if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve_preconditioned: step limit reached before the tolerance");
+    if (status == CR_ERR_BREAKDOWN) return fail(status, "cr_solve_preconditioned: breakdown (zero Arnoldi vector, NaN, or p.Gp <= 0 in the inner PCG)");
     return status;
 }
 
@@ -1283,6 +1415,11 @@ int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st) {
     else k_spmv64<3><<<g, kBlock, 0, st>>>(h->m->nf, h->m->cols, h->val64, x, y);
     CR_CUDA(cudaGetLastError());
     return CR_OK;
+}
+
+int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* Wdev,
+                      cr_solve_stats* st) {
+    return h->m->d == 2 ? solve_fgmres<2>(h, rhs, pre, o, Wdev, st) : solve_fgmres<3>(h, rhs, pre, o, Wdev, st);
 }
 
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {

@@ -15,6 +15,7 @@ import pytest
 
 import synth
 from oracle import coupled, pipeline, topology
+from oracle import hybrid as ohyb
 from paper_2101_03777_gb300 import crhyb
 
 torch = pytest.importorskip("torch")
@@ -193,6 +194,83 @@ def test_solution_matches_coupled_direct_solve(name, opts, tol):
     Ul = np.where((t["elem_face"] >= 0)[:, :, None], U.reshape(-1, coords.shape[1])[np.maximum(t["elem_face"], 0)], 0)
     div = np.einsum("kld,kld->k", Ul, g["a"])
     assert np.abs(div).max() <= 1e-9 * np.abs(g["a"]).max() * np.abs(U).max()
+
+
+def stokes_preconditioner(mesh, case, keep_ff=True, keep_ff_bf16=True):
+    """The transient Stokes system with the case's nu and mu on the same mesh."""
+    coords, elems, nu, mu, conv, fbar, w = case
+    fb = torch.from_numpy(np.ascontiguousarray(fbar)).cuda()
+    return crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, nu, mu, fb), keep_fp32=False, keep_ff=keep_ff,
+                              keep_ff_bf16=keep_ff_bf16)
+
+
+@pytest.mark.parametrize("name,prec", [("ns_newton_9", "ff"), ("ns_newton_9", "fp64"), ("ns_oseen_9", "ff"),
+                                       ("ns_newton_9", "ff_bf16")])
+def test_stokes_preconditioned_fgmres_matches_direct_solve(name, prec):
+    """Flexible GMRES preconditioned by inner PCG solves with the Stokes G: the
+    outer residual is FP64, so every inner precision reaches the FP64 bound."""
+    case = make_case(name)
+    coords, elems, nu, mu, conv, fbar, w = case
+    mesh, _, hyb = gpu_setup(case)
+    pre = stokes_preconditioner(mesh, case)
+    ref = pipeline.direct(coords, elems, nu, mu, fbar[0], conv, w, dense=True)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-13, prec=prec)
+    assert st["status"] == 0 and st["relres"] <= 1e-12
+    assert 1 <= st["outer"] <= 30 and st["iterations"] >= st["outer"]
+    U = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(mesh.ne, dtype=torch.float64, device="cuda")
+    crhyb.cr_recover_up(hyb, W, U, P, normalise_p=True)
+    assert rel(U.cpu().numpy(), ref["U"].ravel()) <= 1e-9
+    assert rel(P.cpu().numpy(), coupled.normalise_pressure(ref["P"], ref["geom"]["vol"])) <= 1e-9
+    # warm start from the solution: no step needed
+    st2 = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-12, prec=prec, use_x0=True)
+    assert st2["status"] == 0 and st2["outer"] == 0
+
+
+def test_stokes_preconditioned_steps_do_not_grow_with_the_mesh():
+    """The GMRES steps of the Stokes-preconditioned Newton solve stay bounded as
+    the mesh is refined (G_pre^{-1} G differs from I by the convection term),
+    while Jacobi-GMRES(30) needs ever more (and stalls beyond about 64x64)."""
+    steps = []
+    for n in (16, 48):
+        p = synth.config_problem("cfg5", n=n)
+        t = topology.build_faces(p["elems"])
+        w = synth.stream_velocity(p["coords"][t["face_vertices"]].mean(axis=1), seed=3)
+        case = (p["coords"], p["elems"], p["nu"], 1000.0, "newton", p["fbar"], w)
+        mesh, _, hyb = gpu_setup(case)
+        pre = stokes_preconditioner(mesh, case)
+        W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+        st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-10, prec="ff")
+        assert st["status"] == 0 and st["relres"] <= 1e-9
+        # the oracle's G and S, for the residual of the returned W
+        topo, geom, A_K, D_K, R_K = pipeline.setup(p["coords"], p["elems"], p["nu"], 1000.0, p["fbar"][0],
+                                                   "newton", w)
+        h = ohyb.hybridise(topo, A_K, D_K, R_K, 1000.0)
+        Wn = W.cpu().numpy()
+        assert np.linalg.norm(h["S"] - h["G"] @ Wn) <= 1e-9 * np.linalg.norm(h["S"])
+        steps.append(st["outer"])
+    assert max(steps) <= 20 and steps[1] <= steps[0] + 4
+
+
+def test_stokes_preconditioned_error_paths():
+    case = make_case("ns_newton_9")
+    mesh, _, hyb = gpu_setup(case)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    # a preconditioner on another mesh handle, or one that is not SPD, is refused
+    other, _, _ = gpu_setup(case)
+    for bad in (stokes_preconditioner(other, case), hyb):
+        with pytest.raises(crhyb.CrError) as ei:
+            crhyb.cr_solve_preconditioned(hyb, bad, W, tol=1e-10)
+        assert ei.value.name == "CR_ERR_ARG"
+    pre = stokes_preconditioner(mesh, case, keep_ff=False, keep_ff_bf16=False)
+    for opts in (dict(method="pcg"), dict(prec="mixed"), dict(restart=0, tol=0.0), dict(prec="ff")):
+        with pytest.raises(crhyb.CrError) as ei:
+            crhyb.cr_solve_preconditioned(hyb, pre, W, **{"tol": 1e-10, **opts})
+        assert ei.value.name == "CR_ERR_ARG"
+    # a step limit is reported with the last iterate's residual
+    st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-13, prec="fp64", max_iter=2, raise_on_error=False)
+    assert st["status_name"] == "CR_ERR_NOT_CONVERGED" and st["outer"] == 2 and 0 < st["relres"] < 1
 
 
 @pytest.mark.parametrize("name", ["cfg1", "3d_kuhn_5"])
