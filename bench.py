@@ -176,6 +176,8 @@ def cpu_sample(name, iters):
     import synth
     from oracle import hybrid, krylov, pipeline
     counts = json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))
+    if name not in counts:
+        raise RuntimeError(f"the CPU oracle sample covers the one-system Stokes PCG workloads {sorted(counts)}")
     full = counts[name]["pcg_iterations"]
     p = synth.config_problem(name)
     t0 = time.perf_counter()
