@@ -91,6 +91,10 @@ PRECS = {
     "mixed": (dict(prec="mixed", max_iter=400000, inner_tol=1e-4), 4, 4,
               "FP32 Jacobi-PCG restarted inside FP64 iterative refinement"),
 }
+# DRAM bytes (read + write) per PCG iteration of the persistent kernel, from one ncu capture of
+# the kernel as committed (profiles/k_pcg_persist_cfg2_ff.md); "traffic" in the bench line is
+# this times the iterations of an average timed launch.  Re-measure whenever the kernel changes.
+DRAM_BYTES_PER_ITERATION = {("cfg2", "ff"): 9.717979e9 / 64}
 SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
                "mixed": "k_pcg_spmv<FP32>"}
 DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
@@ -375,19 +379,21 @@ def run_ours(args, rank, world):
             solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
                       f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
         elif args.persistent:
-            # the persistent PCG kernel: per iteration the SpMV plus the vector phases
-            # (x, r, p, q read and x, r, p, q written as the algorithm states: 11 vector passes,
-            # and the preconditioner read twice)
+            # the persistent PCG kernel: per iteration the SpMV plus the vector phases (the update
+            # reads x, r, p, q and writes x, r; the direction reads r, p and writes p: 9 vector
+            # passes) and the preconditioner read twice
             mb = 4 if prec != "fp64" else 8
             it_bytes = spmv_bytes + 9 * N * xb + 2 * N * mb
             piters = max(st_main["spmv_launches"], 1)
             kms = st_main["spmv_ms"]
             ach = it_bytes * piters / (kms * 1e-3) / 1e9
+            nlaunch = max(st_main["kernel_launches"] - 1, 1)
+            dram = DRAM_BYTES_PER_ITERATION.get((args.workload, prec))
             roof = {"kernel": f"k_pcg_persist<{PRECS[prec][0]['prec']}> (SpMV + update + direction phases)",
                     "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                    "traffic": None, "bytes_per_iteration": it_bytes, "iterations_timed": piters,
-                    "bytes_per_launch": it_bytes * piters / max(st_main["kernel_launches"] - 1, 1),
-                    "avg_launch_ms": kms / max(st_main["kernel_launches"] - 1, 1), "peak_note": peak_note}
+                    "traffic": dram * piters / nlaunch if dram else None, "bytes_per_iteration": it_bytes,
+                    "iterations_timed": piters, "bytes_per_launch": it_bytes * piters / nlaunch,
+                    "avg_launch_ms": kms / nlaunch, "peak_note": peak_note}
         else:
             roof = dict(spmv, traffic=None)
         return tts, {

@@ -57,8 +57,15 @@ namespace {
 #ifndef CRHYB_STAGE_D2
 #define CRHYB_STAGE_D2 0
 #endif
+// SpMV phase with per-thread loads: how many tiles ahead of the sweep one
+// thread of the block asks L2 to fetch the tile's values and columns (bulk L2
+// prefetch, no completion to wait for); 0 turns it off.
+#ifndef CRHYB_L2_PREFETCH
+#define CRHYB_L2_PREFETCH 0
+#endif
 
 constexpr int kPBlock = 256;   // rows per tile = threads per block
+static_assert(kPBlock == kSlice, "a tile is one slice of the sliced ELL");
 constexpr long long kSpinLimit = 1ll << 22;   // bounded barrier wait (about 0.3-1 s with the sleeps)
 
 enum PMode { kModeFP64 = 0, kModeFF32 = 1, kModeFFBF16 = 2 };
@@ -540,6 +547,27 @@ __device__ __forceinline__ unsigned update_mask(const PArgs& a, const PSys& S, i
     return m;
 }
 
+// Ask L2 for the sliced-ELL data of tile t (its values and columns: one
+// contiguous run each, 16-byte aligned, whole slices allocated).
+__device__ __forceinline__ void l2_prefetch(const void* ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+template <int D, bool FF, typename LT>
+__device__ __forceinline__ void prefetch_tile(const PArgs& a, int t) {
+    constexpr int NPV = (2 * D + 1) * D * D;
+    const int2 td = a.tiles[t];
+    const PSys& S = a.sys[td.x];
+    const size_t sl = size_t(td.y) / kSlice;
+    if (FF) {
+        l2_prefetch(S.vh + sl * NPV * kSlice, NPV * kSlice * sizeof(float));
+        l2_prefetch(static_cast<const LT*>(S.vl) + sl * NPV * kSlice, NPV * kSlice * sizeof(LT));
+    } else {
+        l2_prefetch(S.v64 + sl * NPV * kSlice, NPV * kSlice * sizeof(double));
+    }
+    l2_prefetch(S.cols + sl * 2 * D * kSlice, 2 * D * kSlice * sizeof(int32_t));
+}
+
 template <int D, int R, int MODE>
 __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : 2)) k_pcg_persist(PArgs a) {
     constexpr bool FF = MODE != kModeFP64;
@@ -857,7 +885,11 @@ __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CR
                     ++u;
                 }
             } else {
+                constexpr int PF = CRHYB_L2_PREFETCH;
+                if (PF > 0 && threadIdx.x == 0)
+                    for (int t = t0; t < t0 + PF && t < t1; ++t) prefetch_tile<D, FF, LT>(a, t);
                 for (int t = t0; t < t1; ++t) {
+                    if (PF > 0 && threadIdx.x == 0 && t + PF < t1) prefetch_tile<D, FF, LT>(a, t + PF);
                     const int2 td = a.tiles[t];
                     if (td.x != cur) {
                         if (cur >= 0 && amask) flush();

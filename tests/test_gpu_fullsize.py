@@ -118,3 +118,39 @@ def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
         diff = (Gx[rows] - G[rows]).tocsr()
         assert (abs(diff).max() if diff.nnz else 0.0) <= 1e-11 * abs(G).max()
         assert np.abs(Sx[0].ravel()[rows] - S[rows]).max() <= 1e-11 * np.abs(S).max()
+
+
+def test_full_size_batch_pairs_satisfy_their_coupled_systems():
+    """The batched workload as the bench runs it: 64 perturbed meshes (n from 9
+    to 234) x 4 right-hand sides in float-float, autotuned.  Every pair reports
+    an FP64 true residual <= 1.01e-10; for a sample of problems (the smallest,
+    the largest and two between, all four right-hand sides) the GPU's W, U and
+    P are checked in the oracle's G, S and coupled system as above."""
+    probs = synth.batch_problems(count=64, nrhs=4, lo=8, hi=256, seed=2)
+    hybs = []
+    for q in probs:
+        mesh = crhyb.cr_mesh_load(q["coords"], q["elems"])
+        fb = torch.from_numpy(q["fbar"]).cuda()
+        hybs.append(crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, q["nu"], q["mu"], fb), keep_fp32=False,
+                                       keep_ff=True))
+    batch = crhyb.cr_batch_create(hybs, prec="ff", autotune=True)
+    Ws = [torch.zeros(4 * h.n, dtype=torch.float64, device="cuda") for h in hybs]
+    stats = crhyb.cr_solve_batched(batch, Ws, tol=1e-10, max_iter=200000)
+    assert len(stats) == 256
+    assert all(s["status"] == 0 and s["relres"] <= 1.01e-10 for s in stats)
+    order = np.argsort([q["n"] for q in probs])
+    for k in sorted({int(order[0]), int(order[21]), int(order[42]), int(order[-1])}):
+        q, h = probs[k], hybs[k]
+        for r in range(4):
+            topo, geom, A_K, D_K, R_K = pipeline.setup(q["coords"], q["elems"], q["nu"], q["mu"], q["fbar"][r])
+            A, D, R = coupled.assemble(topo, A_K, D_K, R_K, 0)
+            hy = hybrid.hybridise(topo, A_K, D_K, R_K, q["mu"])
+            Wr = Ws[k][r * h.n:(r + 1) * h.n].contiguous()
+            Wn = Wr.cpu().numpy()
+            assert np.linalg.norm(hy["S"] - hy["G"] @ Wn) <= 1.01e-10 * np.linalg.norm(hy["S"])
+            U = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+            P = torch.zeros(h.mesh.ne, dtype=torch.float64, device="cuda")
+            crhyb.cr_recover_up(h, Wr, U, P, rhs=r, normalise_p=False)
+            Un, Pn = U.cpu().numpy(), P.cpu().numpy()
+            assert Pn[0] == 0.0
+            assert np.linalg.norm(A @ Un + D.T @ Pn[1:] - R) <= 1e-7 * np.linalg.norm(R)
