@@ -456,16 +456,21 @@ def run_batch(args, rank, world):
     keep = dict(keep_fp32=False, keep_ff=(prec == "ff"), keep_ff_bf16=(prec == "ff_bf16"))
     tuned = {"bps": 0, "tune": None}
 
-    def step(fbs, profile=False):
+    def step(fbs, profile=False, outs=None):
         hybs = [crhyb.cr_hybridise(crhyb.cr_assemble_coupled(m, q["nu"], q["mu"], f), **keep)
                 for m, q, f in zip(meshes, probs, fbs)]
         batch = crhyb.cr_batch_create(hybs, prec=prec, autotune=tuned["bps"] == 0, blocks_per_sm=tuned["bps"])
         st = crhyb.cr_solve_batched(batch, Ws, tol=args.tol, max_iter=200000, profile=profile)
         if tuned["bps"] == 0:
             tuned["bps"] = batch.info()["blocks_per_sm"]
-        for h, W, U, P in zip(hybs, Ws, Us, Ps):
+        for k, (h, W) in enumerate(zip(hybs, Ws)):
             for r in range(4):
-                crhyb.cr_recover_up(h, W[r * h.n:(r + 1) * h.n], U, P, rhs=r)
+                if outs is None:   # device U and P
+                    crhyb.cr_recover_up(h, W[r * h.n:(r + 1) * h.n], Us[k], Ps[k], rhs=r)
+                else:              # every pair's U and P into pinned host memory
+                    Uh, Ph = outs
+                    crhyb.cr_recover_up(h, W[r * h.n:(r + 1) * h.n], Uh[k][r * h.n:(r + 1) * h.n],
+                                        Ph[k][r * h.mesh.ne:(r + 1) * h.mesh.ne], rhs=r)
         return st, batch.info()
 
     for _ in range(args.warmup):
@@ -490,16 +495,24 @@ def run_batch(args, rank, world):
     stp, info = step(fb_dev, profile=True)
     tts = statistics.mean(times)
     st = stats[-1]
+    # end to end through the C-ABI with host buffers: pinned fbar in, U and P of all 256 pairs out
+    Uh = [torch.empty(4 * n, dtype=torch.float64).pin_memory() for n in ns]
+    Ph = [torch.empty(4 * m.ne, dtype=torch.float64).pin_memory() for m in meshes]
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(fb_host, outs=(Uh, Ph))
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    h2d = sum(int(q["fbar"].nbytes) for q in probs)
+    d2h = sum(8 * 4 * (n + m.ne) for n, m in zip(ns, meshes))
     # algorithmic bytes of one batched iteration (all pairs active): per problem the SpMM over
     # G (values once for its 4 right-hand sides) plus the vector passes of 4 right-hand sides
     vb = {"ff": 8, "ff_bf16": 6, "fp64": 8}[prec]
     mb = 8 if prec == "fp64" else 4
-    bytes_all = 0
-    for m in meshes:
-        fe, _ = crhyb.cr_mesh_face_elements(m)
-        sp, blocks, nnz = algorithmic_spmv_bytes(fe, m.nf, m.dim, vb, 8)
-        N = m.nf * m.dim
-        bytes_all += nnz * vb + blocks * 4 + 4 * (11 * N * 8 + 2 * N * mb)
     iters = [s["iterations"] for s in st]
     # the kernel runs every pair until its own convergence: weight each problem's bytes by its
     # mean iteration count over the timed persistent launches
@@ -527,6 +540,7 @@ def run_batch(args, rank, world):
         "roofline": {"kernel": f"k_pcg_persist<{prec}, 4 rhs> (batched SpMM + update + direction phases)",
                      "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                      "traffic": None, "bytes_timed": work, "kernel_ms": kms, "peak_note": peak_note},
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(st[0]["kernel_launches"]) + 64 * 2 + 256 * 2,
         "clocks": clk,
     }

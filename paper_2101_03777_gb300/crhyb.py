@@ -317,7 +317,8 @@ def cr_solve_preconditioned(hyb, pre, W, rhs=0, raise_on_error=True, **opts):
     rc = load_library().cr_solve_preconditioned(hyb.handle, int(rhs), pre.handle, ctypes.byref(o),
                                                 _ptr(W, np.float64, hyb.n, "W"), ctypes.byref(st))
     stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
-             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)), "kernel_launches": st.kernel_launches}
+             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
+             "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
     if rc != CR_OK and raise_on_error:
         _check(rc)
     return stats
