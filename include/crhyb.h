@@ -191,6 +191,19 @@ void cr_destroy_mesh(cr_mesh* m);
 int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double* fbar, int nrhs,
                         const double* w, cr_system** out, double* blocks_out);
 
+/* Implicit Euler time stepping of the transient problem (mu = 1/dt): make the
+ * right-hand side of the next step carry the previous time level,
+ *   R_K,(sigma, i) += mu |K|/(d+1) u_prev(sigma, i)   for every interior face sigma of K,
+ * the lumped mass that S_K already holds (Section 3.1, with mu = 1/dt as in
+ * Section 2), so that the step solves (u^{n+1} - u^n)/dt - nu Lap u^{n+1} + grad p = f.
+ *   u_prev  float64 [nrhs][nf_int][dim], host or device; copied.  NULL turns the
+ *           term off again.
+ * The term enters every later cr_hybridise (S), cr_recover_up (R_K) and export of
+ * a hybrid of this system: keep u_prev unchanged between the cr_hybridise and the
+ * cr_recover_up of one step.  Errors: CR_ERR_ARG (NULL system, mu <= 0),
+ * CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_system_set_previous(cr_system* s, const double* u_prev);
+
 void cr_destroy_system(cr_system* s);
 
 /* ---- hybridisation ------------------------------------------------------ */

@@ -15,7 +15,7 @@ import scipy.sparse.linalg as spla
 from . import convection, elements
 
 
-def element_blocks(topo, geom, nu, mu, fbar, conv="none", w=None):
+def element_blocks(topo, geom, nu, mu, fbar, conv="none", w=None, u_prev=None):
     """A_K, D_K, R_K for every simplex, zero outside the interior unknowns.
 
     conv = "none": A_K = S_K (x) Id (Section 3.1).
@@ -25,11 +25,15 @@ def element_blocks(topo, geom, nu, mu, fbar, conv="none", w=None):
       (S + J(w)) u + D^t P = R + c(w)  (Section 3.1, b_h != 0).
     conv = "oseen": A_K += N_K(w), R_K unchanged (Picard linearisation).
     fbar [ne, d]; w [nf, d] face velocities about which to linearise.
+    u_prev [nf, d] or None: the previous time level of an implicit Euler step
+      (mu = 1/dt), whose lumped mass term joins R_K (elements.local_R_previous).
     """
     S = elements.local_S(geom, nu, mu)
     A = elements.local_A(S)
     D = elements.local_D(geom)
     R = elements.local_R(geom, fbar)
+    if u_prev is not None:
+        R = R + elements.local_R_previous(topo, geom, mu, u_prev)
     if conv != "none":
         Wl = convection.gather_local(np.asarray(w, dtype=np.float64), topo)
         if conv == "newton":

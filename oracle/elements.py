@@ -93,6 +93,23 @@ def local_R(geom, fbar):
     return (a * rho[:, :, None]).reshape(a.shape[0], -1)
 
 
+def local_R_previous(topo, geom, mu, u_prev):
+    """Implicit Euler with mu = 1/dt (Section 2, the transient problem with the
+    time derivative discretised by one backward step): the mass term of S_K,
+    mu |K|/(d+1) per interior face (Section 3.1, the lumped mass), applied to
+    the previous time level and moved to the right-hand side.
+
+    (R_K)_{i,sigma} += mu |K|/(d+1) u^n_{sigma,i}; u_prev [nf, d] or [nf*d].
+    Returns [ne, (d+1) d], zero on exterior faces.
+    """
+    d = topo["d"]
+    ef = topo["elem_face"]
+    U = np.asarray(u_prev, dtype=np.float64).reshape(-1, d)
+    loc = np.where((ef >= 0)[:, :, None], U[np.maximum(ef, 0)], 0.0)
+    mass = mu * geom["vol"] / (d + 1)                     # [ne]
+    return (mass[:, None, None] * loc).reshape(ef.shape[0], -1)
+
+
 def interior_mask(topo):
     """[ne, (d+1) d] mask of the local unknowns that live on interior faces."""
     m = topo["elem_face"] >= 0

@@ -13,11 +13,12 @@ import scipy.sparse.linalg as spla
 from . import coupled, elements, hybrid as hyb_mod, krylov, topology
 
 
-def setup(coords, elems, nu, mu, fbar, conv="none", w=None):
-    """Topology, geometry and element blocks (Sections 2 and 3.1)."""
+def setup(coords, elems, nu, mu, fbar, conv="none", w=None, u_prev=None):
+    """Topology, geometry and element blocks (Sections 2 and 3.1); u_prev: the
+    previous level of an implicit Euler step, or None."""
     topo = topology.build_faces(elems)
     geom = elements.geometry(coords, elems)
-    A_K, D_K, R_K = coupled.element_blocks(topo, geom, nu, mu, fbar, conv, w)
+    A_K, D_K, R_K = coupled.element_blocks(topo, geom, nu, mu, fbar, conv, w, u_prev)
     return topo, geom, A_K, D_K, R_K
 
 
@@ -26,9 +27,9 @@ def face_centroids(coords, topo):
     return np.asarray(coords)[topo["face_vertices"]].mean(axis=1)
 
 
-def direct(coords, elems, nu, mu, fbar, conv="none", w=None, k0=0, dense=False):
+def direct(coords, elems, nu, mu, fbar, conv="none", w=None, k0=0, dense=False, u_prev=None):
     """U [nf, d] and P [ne] (P_{K_0} = 0) of Eq. 10 by a direct solve."""
-    topo, geom, A_K, D_K, R_K = setup(coords, elems, nu, mu, fbar, conv, w)
+    topo, geom, A_K, D_K, R_K = setup(coords, elems, nu, mu, fbar, conv, w, u_prev)
     A, D, R = coupled.assemble(topo, A_K, D_K, R_K, k0)
     U, P = coupled.solve_direct(A, D, R, k0, dense=dense)
     return {"U": U.reshape(-1, topo["d"]), "P": P, "topo": topo, "geom": geom,

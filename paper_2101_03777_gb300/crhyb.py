@@ -86,6 +86,7 @@ _SIGS = {
     "cr_hybridise": (_i32, [_vp, ctypes.POINTER(cr_hyb_opts), ctypes.POINTER(_vp)]),
     "cr_hybrid_export": (_i32, [_vp, _vp, _vp, _vp]),
     "cr_solve": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, ctypes.POINTER(cr_solve_stats)]),
+    "cr_system_set_previous": (_i32, [_vp, _vp]),
     "cr_solve_preconditioned": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(cr_solve_opts), _vp,
                                        ctypes.POINTER(cr_solve_stats)]),
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
@@ -259,6 +260,14 @@ def cr_assemble_coupled(mesh, nu, mu, fbar, conv="none", w=None, lambda_scale=0.
                                    nrhs, _ptr(w, np.float64, mesh.nf * mesh.dim, "w"), ctypes.byref(h),
                                    _ptr(blocks_out, np.float64, None, "blocks_out")))
     return System(h, mesh, nrhs)
+
+
+def cr_system_set_previous(system, u_prev):
+    """Implicit Euler: later hybridisations and recoveries of `system` add the lumped
+    mass term of the previous time level u_prev [nrhs, nf, d] (host or device) to the
+    right-hand side; None turns it off."""
+    n = system.nrhs * system.mesh.nf * system.mesh.dim
+    _check(load_library().cr_system_set_previous(system.handle, _ptr(u_prev, np.float64, n, "u_prev")))
 
 
 def cr_hybridise(system, keep_fp32=True, keep_bf16=False, keep_ff=False, keep_ff_bf16=False):

@@ -192,6 +192,22 @@ extern "C" int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double*
     return CR_OK;
 }
 
+extern "C" int cr_system_set_previous(cr_system* s, const double* u_prev) {
+    if (!s) return fail(CR_ERR_ARG, "cr_system_set_previous: NULL system");
+    if (!u_prev) {
+        s->uprev_on = false;
+        return CR_OK;
+    }
+    if (!(s->mu > 0.0)) return fail(CR_ERR_ARG, "cr_system_set_previous: an implicit Euler step needs mu = 1/dt > 0");
+    cr_mesh* m = s->m;
+    const size_t n = size_t(s->nrhs) * m->nf * m->d;
+    StreamScope scope(m);
+    if (!s->uprev) CR_TRY(s->arena.alloc_n(&s->uprev, n));
+    CR_TRY(copy_in(s->uprev, u_prev, n, m->stream));
+    s->uprev_on = true;
+    return CR_OK;
+}
+
 extern "C" void cr_destroy_system(cr_system* s) {
     if (!s) return;
     s->arena.release();

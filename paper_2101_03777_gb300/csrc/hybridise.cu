@@ -28,10 +28,14 @@ struct MeshView {
     const int32_t* face_elems;
     const uint8_t* mis;
     int k0;
+    // previous time level of an implicit Euler step, or NULL: [nrhs][nf][d] in the
+    // condensation and export kernels, the recovered right-hand side's [nf][d] in recovery
+    const double* uprev;
 };
 
 MeshView view(const cr_mesh* m) {
-    return MeshView{m->ne, m->nf, m->coords, m->elems, m->elem_face, m->elem_side, m->face_elems, m->mis, m->k0};
+    return MeshView{m->ne, m->nf, m->coords, m->elems, m->elem_face, m->elem_side, m->face_elems, m->mis, m->k0,
+                    nullptr};
 }
 
 struct Outputs {
@@ -232,7 +236,8 @@ __device__ __forceinline__ void stokes_local(const Geom<D>& g, const Topo<D>& t,
 // R_K (Eq. 8, Section 3.1): (R_K)_{l,i} = a_l^(i) fbar_K . (x_l - x_K).
 template <int D>
 __device__ __forceinline__ void rhs_local(const Geom<D>& g, const Topo<D>& t, const double* __restrict__ fb,
-                                          double (&R)[D + 1][D]) {
+                                          double (&R)[D + 1][D], const double* __restrict__ up = nullptr,
+                                          double mu = 0.0) {
     double f[D];
 #pragma unroll
     for (int b = 0; b < D; ++b) f[b] = __ldg(fb + b);
@@ -244,6 +249,21 @@ __device__ __forceinline__ void rhs_local(const Geom<D>& g, const Topo<D>& t, co
 #pragma unroll
         for (int i = 0; i < D; ++i) R[l][i] = t.in[l] ? g.a[l][i] * rho : 0.0;
     }
+    // implicit Euler (mu = 1/dt): the lumped mass of the previous time level,
+    // mu |K|/(d+1) u^n on each interior face, the same mass as in S_K
+    if (up) {
+        const double m = mu * g.vol / double(D + 1);
+#pragma unroll
+        for (int l = 0; l <= D; ++l)
+            if (t.in[l])
+#pragma unroll
+                for (int i = 0; i < D; ++i) R[l][i] += m * __ldg(up + size_t(t.face[l]) * D + i);
+    }
+}
+
+// The previous time level of right-hand side r (NULL if none).
+__device__ __forceinline__ const double* uprev_of(const MeshView& mv, int r, int d) {
+    return mv.uprev ? mv.uprev + size_t(r) * mv.nf * d : nullptr;
 }
 
 __device__ __forceinline__ void store_val(const Outputs& o, size_t idx, double v) {
@@ -331,7 +351,7 @@ __global__ void __launch_bounds__(kElemBlock) k_condense_stokes(MeshView mv, dou
     // S_K = C_K M_K R_K, M_K R = T^{-1} R - v (v.R)/B
     for (int r = 0; r < nrhs; ++r) {
         double R[NF][D];
-        rhs_local<D>(g, t, fbar + (size_t(r) * mv.ne + K) * D, R);
+        rhs_local<D>(g, t, fbar + (size_t(r) * mv.ne + K) * D, R, uprev_of(mv, r, D), mu);
         double vR = 0.0;
 #pragma unroll
         for (int m = 0; m < NF; ++m)
@@ -525,7 +545,7 @@ __global__ void __launch_bounds__(kElemBlock) k_condense_conv2(MeshView mv, doub
     }
     for (int r = 0; r < nrhs; ++r) {
         double R[3][2];
-        rhs_local<2>(g, t, fbar + (size_t(r) * mv.ne + K) * 2, R);
+        rhs_local<2>(g, t, fbar + (size_t(r) * mv.ne + K) * 2, R, uprev_of(mv, r, 2), mu);
         double Rv[kL2];
 #pragma unroll
         for (int p = 0; p < kL2; ++p) Rv[p] = R[p / 2][p % 2] + cw[p];
@@ -609,7 +629,7 @@ __global__ void __launch_bounds__(kElemBlock) k_export(MeshView mv, double nu, d
     for (int p = 0; p < L; ++p) o[L * L + p] = t.in[p / D] ? -g.a[p / D][p % D] : 0.0;
     for (int r = 0; r < nrhs; ++r) {
         double R[NF][D];
-        rhs_local<D>(g, t, fbar + (size_t(r) * mv.ne + K) * D, R);
+        rhs_local<D>(g, t, fbar + (size_t(r) * mv.ne + K) * D, R, uprev_of(mv, r, D), mu);
         for (int p = 0; p < L; ++p) o[L * L + L + size_t(r) * L + p] = R[p / D][p % D] + cw[p];
     }
 }
@@ -637,7 +657,7 @@ __global__ void __launch_bounds__(kBlock) k_recover_stokes(MeshView mv, double n
         StokesLocal<D> L;
         stokes_local<D>(g, t, e, nu, mu, K == mv.k0, L);
         double R[NF][D];
-        rhs_local<D>(g, t, fb + size_t(K) * D, R);
+        rhs_local<D>(g, t, fb + size_t(K) * D, R, mv.uprev, mu);
         double y[NF][D];
 #pragma unroll
         for (int l = 0; l < NF; ++l)
@@ -693,7 +713,7 @@ __global__ void __launch_bounds__(kBlock) k_recover_conv2(MeshView mv, double nu
         ConvLocal L;
         conv_local(g, t, e, A, K == mv.k0, L);
         double R[3][2];
-        rhs_local<2>(g, t, fb + size_t(K) * 2, R);
+        rhs_local<2>(g, t, fb + size_t(K) * 2, R, mv.uprev, mu);
         double y[kL2];
 #pragma unroll
         for (int p = 0; p < kL2; ++p) {
@@ -759,6 +779,7 @@ inline unsigned blocks_for(int64_t n, int b) { return unsigned((n + b - 1) / b);
 int launch_assemble_export(cr_system* s, double* blocks, cudaStream_t st) {
     cr_mesh* m = s->m;
     MeshView mv = view(m);
+    mv.uprev = s->uprev_on ? s->uprev : nullptr;
     const unsigned nb = blocks_for(m->ne, kElemBlock);
     if (m->d == 2) k_export<2><<<nb, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, s->fbar, s->nrhs, blocks);
     else k_export<3><<<nb, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, s->fbar, s->nrhs, blocks);
@@ -770,6 +791,7 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st) {
     cr_system* s = h->s;
     cr_mesh* m = h->m;
     MeshView mv = view(m);
+    mv.uprev = s->uprev_on ? s->uprev : nullptr;
     const unsigned nbe = blocks_for(m->ne, kElemBlock);
     const double* lam = nullptr;
     if (s->mu == 0.0) {
@@ -804,6 +826,7 @@ int launch_recover(cr_hybrid* h, int rhs, const double* W, double* U, double* P,
     cr_system* s = h->s;
     cr_mesh* m = h->m;
     MeshView mv = view(m);
+    mv.uprev = s->uprev_on ? s->uprev + size_t(rhs) * m->nf * m->d : nullptr;
     const unsigned nb = blocks_for(m->ne, kBlock);
     const double* lam = s->mu == 0.0 ? h->lam : nullptr;
     const double* fb = s->fbar + size_t(rhs) * m->ne * m->d;

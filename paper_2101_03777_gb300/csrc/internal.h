@@ -108,6 +108,8 @@ struct cr_system {
     crhyb::DevArena arena;
     double* fbar = nullptr;   // [nrhs][ne][d]
     double* w = nullptr;      // [nf][d] or null
+    double* uprev = nullptr;  // [nrhs][nf][d]: previous time level (implicit Euler), used when uprev_on
+    bool uprev_on = false;
 };
 
 struct cr_hybrid {
