@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--sample-iters", type=int, default=30)
     ap.add_argument("--check-every", type=int, default=16,
                     help="iterations per convergence check (persistent: x64 iterations per launch)")
+    ap.add_argument("--mesh-n", type=int, default=0,
+                    help="profiling runs only: mesh size n in place of the workload's (n x n or n^3 cells)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="profiling runs only: stop every solve after this many iterations (no convergence check)")
     return ap.parse_args()
@@ -70,11 +72,12 @@ def parse():
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def load_problem(name):
-    """Mesh, coefficients, sources and (for Navier-Stokes) the linearisation field."""
+def load_problem(name, n=None):
+    """Mesh, coefficients, sources and (for Navier-Stokes) the linearisation field;
+    n (profiling runs only) replaces the workload's mesh size."""
     import numpy as np
     import synth
-    p = synth.config_problem(name)
+    p = synth.config_problem(name, n=n or None)
     if name == "cfg5":
         p["mu"] = 1000.0   # transient Newton step (dt = 1e-3); see the design notes on mu = 0
         p["conv"] = "newton"
@@ -234,7 +237,7 @@ def run_ours(args, rank, world):
     build.build_library()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    p, _ = load_problem(args.workload)
+    p, _ = load_problem(args.workload, args.mesh_n)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -584,7 +587,9 @@ def main():
         torch.distributed.init_process_group("nccl")
     out = run_batch(args, rank, world) if args.workload == "cfg4" else run_ours(args, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if args.mesh_n:
+            out["config"]["mesh_n"] = args.mesh_n   # a profiling size, not the workload's
+        if world == 1 and not args.no_cpu_baseline and not args.mesh_n:
             try:
                 out["cpu_baseline"] = run_cpu_sample_child(args.workload, args.sample_iters)
             except Exception as e:  # reported, not fatal

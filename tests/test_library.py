@@ -33,7 +33,8 @@ def test_every_declared_entry_point_is_exported(lib):
     assert sorted(crhyb.EXPORTED) == names
 
 
-@pytest.mark.parametrize("case", ["three_simplices_share_a_face", "index_out_of_range", "flat_simplex"])
+@pytest.mark.parametrize("case", ["three_simplices_share_a_face", "index_out_of_range", "flat_simplex",
+                                  "no_interior_face"])
 def test_invalid_meshes_are_rejected(lib, case):
     if case == "three_simplices_share_a_face":
         coords = np.array([[0, 0], [1, 0], [0, 1], [0, -1], [1, 1]], dtype=np.float64)
@@ -41,9 +42,12 @@ def test_invalid_meshes_are_rejected(lib, case):
     elif case == "index_out_of_range":
         coords = np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.float64)
         elems = np.array([[0, 1, 2], [1, 3, 7]], dtype=np.int32)
-    else:
+    elif case == "flat_simplex":
         coords = np.array([[0, 0], [1, 0], [2, 0], [0, 1]], dtype=np.float64)
         elems = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    else:   # two triangles that share only a vertex: every face is on the boundary
+        coords = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1]], dtype=np.float64)
+        elems = np.array([[0, 1, 2], [0, 3, 4]], dtype=np.int32)
     with pytest.raises(crhyb.CrError) as ei:
         crhyb.cr_mesh_load(coords, elems)
     assert ei.value.name == "CR_ERR_MESH"
@@ -53,5 +57,15 @@ def test_bad_arguments_are_rejected(lib):
     with pytest.raises(crhyb.CrError) as ei:
         crhyb.cr_mesh_load(np.zeros((4, 2)), np.zeros((2, 3), dtype=np.int32), k0=5)
     assert ei.value.name == "CR_ERR_ARG"
+    # empty meshes: no simplex, or a single one (no interior face can exist)
+    for ne in (0, 1):
+        with pytest.raises(crhyb.CrError) as ei:
+            crhyb.cr_mesh_load(np.array([[0, 0], [1, 0], [0, 1]], dtype=np.float64),
+                               np.zeros((ne, 3), dtype=np.int32) + np.arange(3, dtype=np.int32))
+        assert ei.value.name == "CR_ERR_ARG"
+    # NULL handles of the later entry points
+    assert lib.cr_solve_preconditioned(None, 0, None, None, None, None) == -1
+    assert lib.cr_system_set_previous(None, None) == -1
+    assert lib.cr_solve_batched(None, None, None, None) == -1
     rc = lib.cr_solve(None, 0, None, None, None)
     assert rc == -1 and b"NULL" in lib.cr_last_error()
