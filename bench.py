@@ -94,6 +94,7 @@ PRECS = {
     "mixed": (dict(prec="mixed", max_iter=400000, inner_tol=1e-4), 4, 4,
               "FP32 Jacobi-PCG restarted inside FP64 iterative refinement"),
 }
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # DRAM bytes (read + write) per PCG iteration of the persistent kernel, from one ncu capture of
 # the kernel as committed (profiles/k_pcg_persist_cfg2_ff.md); "traffic" in the bench line is
 # this times the iterations of an average timed launch.  Re-measure whenever the kernel changes.
@@ -397,6 +398,14 @@ def run_ours(args, rank, world):
                     "traffic": dram * piters / nlaunch if dram else None, "bytes_per_iteration": it_bytes,
                     "iterations_timed": piters, "bytes_per_launch": it_bytes * piters / nlaunch,
                     "avg_launch_ms": kms / nlaunch, "peak_note": peak_note}
+            if prec == "fp64":
+                # the FP64 pipe: 2 flops per matrix entry and about 14 per unknown in the vector
+                # phases (update, dots, direction), against the nominal FP64 rate (no measured peak)
+                flops = 2 * nnz + 14 * N
+                fl = flops * piters / (kms * 1e-3) / 1e12
+                roof["alu"] = {"bound": "fp64", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": fl / FP64_PEAK_TFLOPS, "flops_per_iteration": flops,
+                               "peak_note": "nominal FP64 rate; no measured FP64 peak"}
         else:
             roof = dict(spmv, traffic=None)
         return tts, {
