@@ -12,7 +12,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import convection, elements
+from . import convection, elements, krylov
 
 
 def element_blocks(topo, geom, nu, mu, fbar, conv="none", w=None, u_prev=None):
@@ -71,6 +71,27 @@ def assemble(topo, A_K, D_K, R_K, k0=0):
 def saddle_matrix(A, D):
     """[A D^t; D 0] as CSR."""
     return sp.bmat([[A, D.T], [D, None]], format="csr")
+
+
+def saddle_preconditioner(A, D):
+    """Diagonal preconditioner of [A D^t; D 0] for MINRES: 1/diag(A) on the
+    velocities and 1/diag(D diag(A)^{-1} D^t) on the pressures (the diagonal
+    of the Schur complement with A replaced by its diagonal)."""
+    da = A.diagonal()
+    schur = np.asarray((D.multiply(D)) @ (1.0 / da)).ravel()
+    return np.concatenate([1.0 / da, 1.0 / schur])
+
+
+def solve_minres(A, D, R, rtol=1e-10, maxit=1000000, k0=0):
+    """Eq. 10 without hybridisation: preconditioned MINRES on the coupled
+    system (the comparison the paper draws against the hybrid method);
+    returns U, P (P_{K_0} = 0), the MINRES steps and the history."""
+    N = A.shape[0]
+    ne = D.shape[0] + 1
+    K = saddle_matrix(A, D)
+    rhs = np.concatenate([R, np.zeros(ne - 1)])
+    sol, it, hist = krylov.minres(K, rhs, saddle_preconditioner(A, D), rtol=rtol, maxit=maxit)
+    return sol[:N], np.insert(sol[N:], k0, 0.0), it, hist
 
 
 def solve_direct(A, D, R, k0=0, dense=False):

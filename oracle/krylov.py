@@ -6,7 +6,9 @@ Newton steps by GMRES (Section 4.3).  These are the standard algorithms
 (Saad, Iterative Methods for Sparse Linear Systems: Algorithm 9.1,
 preconditioned CG; Algorithm 9.5, right-preconditioned restarted GMRES with
 Givens rotations), written plainly; the preconditioner is Jacobi (the
-inverse of the diagonal of G).  ``refine`` is classical mixed-precision
+inverse of the diagonal of G).  ``minres`` is Paige and Saunders' MINRES
+with a diagonal preconditioner, for the symmetric indefinite coupled system
+of Eq. 10 solved without hybridisation.  ``refine`` is classical mixed-precision
 iterative refinement: inner solves in float32, residual and update in float64.
 """
 
@@ -104,6 +106,62 @@ def gmres(G, b, minv, x0=None, restart=30, rtol=1e-10, maxit=100000):
             if np.linalg.norm(r) / bn <= rtol:
                 hist.append(np.linalg.norm(r) / bn)
                 break
+    return x, it, hist
+
+
+def minres(K, b, minv, x0=None, rtol=1e-10, maxit=100000):
+    """Preconditioned MINRES (Paige and Saunders) for a symmetric, possibly
+    indefinite K with a symmetric positive semidefinite diagonal preconditioner
+    minv (entries 0 remove their unknown from the Krylov space).
+
+    The Lanczos process runs in the M-inner product (M^{-1} = diag(minv)):
+    v_1 = r_0, z_j = M^{-1} v_j, gamma_j = sqrt(z_j . v_j); the tridiagonal
+    system is reduced by Givens rotations (c, s) and the iterate is updated
+    along directions w_j, so that |eta| = ||b - K x_j||_{M^{-1}} after step j.
+    Stops when |eta| <= rtol * gamma_1, or after maxit steps.  Returns
+    (x, steps, history of |eta| / gamma_1).
+    """
+    x = np.zeros_like(b) if x0 is None else x0.astype(b.dtype).copy()
+    v_old = np.zeros_like(b)
+    v = b - K @ x
+    z = minv * v
+    gamma = np.sqrt(np.dot(z, v))
+    gamma1 = gamma
+    hist = [1.0 if gamma1 > 0 else 0.0]
+    if gamma1 == 0.0:
+        return x, 0, hist
+    gamma_old = 1.0
+    eta = gamma
+    c_old, c = 1.0, 1.0
+    s_old, s = 0.0, 0.0
+    w_old = np.zeros_like(b)
+    w = np.zeros_like(b)
+    it = 0
+    while it < maxit:
+        z = z / gamma
+        q = K @ z
+        delta = np.dot(q, z)
+        v_new = q - (delta / gamma) * v - (gamma / gamma_old) * v_old
+        z_new = minv * v_new
+        gamma_new = np.sqrt(max(np.dot(z_new, v_new), 0.0))
+        # the new column of the tridiagonal matrix, rotated by the last two rotations
+        a0 = c * delta - c_old * s * gamma
+        a1 = np.hypot(a0, gamma_new)
+        a2 = s * delta + c_old * c * gamma
+        a3 = s_old * gamma
+        c_old, s_old = c, s
+        c, s = a0 / a1, gamma_new / a1
+        w_new = (z - a3 * w_old - a2 * w) / a1
+        x = x + c * eta * w_new
+        eta = -s * eta
+        it += 1
+        hist.append(abs(eta) / gamma1)
+        if abs(eta) <= rtol * gamma1 or gamma_new == 0.0:
+            break
+        v_old, v = v, v_new
+        z = z_new
+        gamma_old, gamma = gamma, gamma_new
+        w_old, w = w, w_new
     return x, it, hist
 
 
