@@ -275,6 +275,38 @@ int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, 
 
 void cr_destroy_hybrid(cr_hybrid* h);
 
+/* ---- the coupled system without hybridisation ------------------------- */
+
+/* The comparison the paper draws against the hybrid method (Section 4): the
+ * coupled system of Eq. 10, [A D^t; D 0][U; P] = [R; 0] with P_{K_0} = 0,
+ * solved directly by preconditioned MINRES (Paige and Saunders) in FP64,
+ * without eliminating the pressure.  A = sum_K H_K A_K H_K^t (A_K = S_K (x) Id,
+ * the velocity stencil, stored like G), D_K = -a_{K,sigma}, R as for the hybrid
+ * method (including a previous time level set by cr_system_set_previous).
+ * The preconditioner is diagonal: 1/diag(A) on U and the inverse diagonal of
+ * D diag(A)^{-1} D^t on P (0 at K_0).
+ * Only symmetric systems (conv = NONE); mu >= 0. */
+typedef struct cr_coupled cr_coupled;
+
+/* Assemble A, R, D_K and the preconditioner of system s (which must outlive
+ * the handle).  Errors: CR_ERR_ARG (NULL, conv != NONE), CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_coupled_create(cr_system* s, cr_coupled** out);
+
+/* MINRES for right-hand side rhs until ||[R;0] - K [U;P]||_2 <= tol ||R||_2.
+ * Each cycle runs until its preconditioned residual estimate |eta| has fallen
+ * by a tenth of what the 2-norm still needs; the FP64 true residual then
+ * decides, and a shortfall restarts MINRES from the iterate (up to max_outer).
+ *   opts  prec FP64; tol; max_iter (MINRES steps in total); max_outer (cycles,
+ *         default 20); use_x0 (U, P hold the initial guess); check_every (steps
+ *         between host checks)
+ *   U     device float64 [nf_int][dim]; P device float64 [ne] (P_{K_0} = 0)
+ *   st    iterations = MINRES steps, outer = cycles, relres = the true relative
+ *         residual of the returned U, P
+ * Returns CR_OK, CR_ERR_NOT_CONVERGED, CR_ERR_BREAKDOWN, CR_ERR_ARG, CR_ERR_CUDA. */
+int cr_solve_coupled(cr_coupled* c, int rhs, const cr_solve_opts* opts, double* U, double* P, cr_solve_stats* st);
+
+void cr_destroy_coupled(cr_coupled* c);
+
 /* ---- batched solves ------------------------------------------------------ */
 
 /* Many transient Stokes systems (mu > 0, b_h = 0, so G is SPD: Section 3.2,

@@ -87,6 +87,10 @@ _SIGS = {
     "cr_hybrid_export": (_i32, [_vp, _vp, _vp, _vp]),
     "cr_solve": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, ctypes.POINTER(cr_solve_stats)]),
     "cr_system_set_previous": (_i32, [_vp, _vp]),
+    "cr_coupled_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
+    "cr_solve_coupled": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, _vp,
+                                ctypes.POINTER(cr_solve_stats)]),
+    "cr_destroy_coupled": (None, [_vp]),
     "cr_solve_preconditioned": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(cr_solve_opts), _vp,
                                        ctypes.POINTER(cr_solve_stats)]),
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
@@ -328,6 +332,40 @@ def cr_solve_preconditioned(hyb, pre, W, rhs=0, raise_on_error=True, **opts):
     stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
              "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
              "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
+    if rc != CR_OK and raise_on_error:
+        _check(rc)
+    return stats
+
+
+class Coupled:
+    """Owner of a cr_coupled handle (keeps its system alive)."""
+
+    def __init__(self, handle, system):
+        self.handle, self.system, self.mesh = handle, system, system.mesh
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _alive():
+            _lib.cr_destroy_coupled(self.handle)
+            self.handle = None
+
+
+def cr_coupled_create(system):
+    """A, D_K, R and the diagonal preconditioner of the coupled system (no hybridisation)."""
+    h = _vp()
+    _check(load_library().cr_coupled_create(system.handle, ctypes.byref(h)))
+    return Coupled(h, system)
+
+
+def cr_solve_coupled(cpl, U, P, rhs=0, raise_on_error=True, **opts):
+    """MINRES on the coupled system; U [nf, d] and P [ne] device float64 (P_{K_0} = 0)."""
+    opts.setdefault("method", "pcg")
+    o = make_solve_opts(**opts)
+    st = cr_solve_stats()
+    m = cpl.mesh
+    rc = load_library().cr_solve_coupled(cpl.handle, int(rhs), ctypes.byref(o), _ptr(U, np.float64, m.nf * m.dim, "U"),
+                                         _ptr(P, np.float64, m.ne, "P"), ctypes.byref(st))
+    stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
+             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)), "kernel_launches": st.kernel_launches}
     if rc != CR_OK and raise_on_error:
         _check(rc)
     return stats

@@ -593,6 +593,61 @@ __global__ void __launch_bounds__(256) k_merge(int64_t nf, int nrhs, const doubl
 }
 
 // ---------------------------------------------------------------------------
+// The coupled system without elimination (Eq. 10, Section 3.1), for the
+// non-hybrid comparison solve: A = sum_K H_K A_K H_K^t with A_K = S_K (x) Id in
+// the sliced ELL of G (the same stencil: the faces of one simplex), the
+// diagonal blocks and R = sum_K H_K R_K summed per face by k_merge, and
+// D_K = -a_{K, sigma} kept per simplex [ne][d+1][d] (zero on exterior faces).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double nu, double mu,
+                                                           const double* __restrict__ fbar, int nrhs, Outputs o,
+                                                           double* __restrict__ DK) {
+    constexpr int NF = D + 1;
+    const int64_t K = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (K >= mv.ne) return;
+    const int64_t nf = mv.nf;
+    Geom<D> g;
+    simplex_geometry<D>(mv.coords, mv.elems + K * NF, g);
+    Topo<D> t;
+    load_topo<D>(mv, K, t);
+#pragma unroll
+    for (int l = 0; l < NF; ++l) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) DK[(K * NF + l) * D + i] = t.in[l] ? -g.a[l][i] : 0.0;
+        if (!t.in[l]) continue;
+        const int64_t f = t.face[l];
+        const int s = t.side[l];
+#pragma unroll
+        for (int m = 0; m < NF; ++m) {
+            const double sv = t.in[m] ? s_entry<D>(g, l, m, nu, mu) : 0.0;
+            if (m == l) {
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) o.dpart[((size_t(s) * D + i) * D + j) * nf + f] = i == j ? sv : 0.0;
+            } else {
+                const int slot = 1 + s * D + (m < l ? m : m - 1);
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) store_val(o, sell(f, (slot * D + i) * D + j, o.npl), i == j ? sv : 0.0);
+            }
+        }
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        double R[NF][D];
+        rhs_local<D>(g, t, fbar + (size_t(r) * mv.ne + K) * D, R, uprev_of(mv, r, D), mu);
+#pragma unroll
+        for (int l = 0; l < NF; ++l) {
+            if (!t.in[l]) continue;
+#pragma unroll
+            for (int i = 0; i < D; ++i) o.spart[((size_t(r) * 2 + t.side[l]) * D + i) * nf + t.face[l]] = R[l][i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Export of the coupled element blocks A_K, D_K, R_K (Section 3.1)
 // ---------------------------------------------------------------------------
 template <int D>
@@ -817,6 +872,23 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st) {
     const unsigned nbf = blocks_for(m->nf, 256);
     if (m->d == 2) k_merge<2><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, h->dpart, h->spart, o, h->S, h->minv64, h->minv32);
     else k_merge<3><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, h->dpart, h->spart, o, h->S, h->minv64, h->minv32);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int launch_assemble_A(cr_system* s, double* val64, int npl, double* dpart, double* spart, double* R,
+                      double* minv64, double* DK, cudaStream_t st) {
+    cr_mesh* m = s->m;
+    MeshView mv = view(m);
+    mv.uprev = s->uprev_on ? s->uprev : nullptr;
+    Outputs o{val64, nullptr, nullptr, nullptr, nullptr, npl, dpart, spart, nullptr};
+    const unsigned nbe = blocks_for(m->ne, kElemBlock);
+    if (m->d == 2) k_assemble_A<2><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->fbar, s->nrhs, o, DK);
+    else k_assemble_A<3><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->fbar, s->nrhs, o, DK);
+    CR_CUDA(cudaGetLastError());
+    const unsigned nbf = blocks_for(m->nf, 256);
+    if (m->d == 2) k_merge<2><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, dpart, spart, o, R, minv64, nullptr);
+    else k_merge<3><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, dpart, spart, o, R, minv64, nullptr);
     CR_CUDA(cudaGetLastError());
     return CR_OK;
 }

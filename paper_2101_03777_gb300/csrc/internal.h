@@ -168,6 +168,8 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st);
 int launch_recover(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise,
                    double* jump_dev, cudaStream_t st);
 int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st);
+int launch_assemble_A(cr_system* s, double* val64, int npl, double* dpart, double* spart, double* R,
+                      double* minv64, double* DK, cudaStream_t st);
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st);
 int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* Wdev,
                       cr_solve_stats* st);
