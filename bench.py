@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--sample-iters", type=int, default=30)
     ap.add_argument("--check-every", type=int, default=16,
                     help="iterations per convergence check (persistent: x64 iterations per launch)")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="also time this many implicit Euler steps of the transient workload")
     ap.add_argument("--compare-coupled", action="store_true",
                     help="also time the coupled system solved without hybridisation (MINRES)")
     ap.add_argument("--mesh-n", type=int, default=0,
@@ -438,6 +440,36 @@ def run_ours(args, rank, world):
     }
     if "fp64" in sums and head != "fp64":
         out["speedup_vs_fp64"] = sums["fp64"][0] / tts
+    if args.time_steps and not newton:
+        # implicit Euler steps of the transient workload (mu = 1/dt) from rest: each step hands
+        # U^n to the next right-hand side, hybridises, solves from the previous W (warm start)
+        # and recovers U^{n+1}; timed as one region with CUDA events
+        prec = head
+        o = solve_opts(prec, args.tol, args.graph, False, args.persistent)
+        o["check_every"] = args.check_every
+        system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fbar_dev)
+        Ut = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Wt = torch.zeros(n, dtype=torch.float64, device="cuda")
+        iters = []
+
+        def time_step(use_x0):
+            crhyb.cr_system_set_previous(system, Ut)
+            hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_ff=(prec == "ff"),
+                                     keep_ff_bf16=(prec == "ff_bf16"))
+            st = crhyb.cr_solve(hyb, Wt, use_x0=use_x0, **o)
+            crhyb.cr_recover_up(hyb, Wt, Ut, P, normalise_p=True)
+            iters.append(st["iterations"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.time_steps):
+            time_step(k > 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tl = agg(e0.elapsed_time(e1) / 1e3)
+        out["time_loop"] = {"steps": args.time_steps, "value": tl / args.time_steps, "unit": "s per step",
+                            "precision": prec, "iterations_per_step": iters,
+                            "note": "implicit Euler from rest, dt = 1/mu; each step warm-starts from the previous W"}
     if args.compare_coupled and not newton:
         # the paper's comparison: the same coupled system solved without hybridisation
         # (assembly + preconditioned MINRES to the same relative residual), one warm-up and

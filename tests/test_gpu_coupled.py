@@ -102,3 +102,26 @@ def test_coupled_errors():
     # a step limit is reported
     st, _, _ = solve(system, mesh, tol=1e-13, prec="fp64", max_iter=3, raise_on_error=False)
     assert st["status_name"] == "CR_ERR_NOT_CONVERGED" and st["iterations"] == 3
+
+
+def test_second_rhs_other_k0_and_previous_level():
+    """Right-hand side 1 of two, K_0 = 7, and an implicit Euler previous level:
+    the same U and P as the oracle's direct solve with those choices."""
+    coords, elems = synth.mesh2d_square(9, perturb=0.2, seed=8)
+    fbar = np.stack([synth.element_means(lambda x, md=synth.fourier_modes(2, s): synth.fourier_force(x, md),
+                                         coords, elems, order=3) for s in (2, 5)])
+    mesh = crhyb.cr_mesh_load(coords, elems, k0=7)
+    system = crhyb.cr_assemble_coupled(mesh, 0.5, 80.0, torch.from_numpy(fbar).cuda())
+    t = topology.build_faces(elems)
+    u_prev = np.random.default_rng(4).standard_normal((2, t["nf"], 2))
+    crhyb.cr_system_set_previous(system, u_prev)
+    cpl = crhyb.cr_coupled_create(system)
+    U = torch.zeros(mesh.nf * 2, dtype=torch.float64, device="cuda")
+    P = torch.zeros(mesh.ne, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve_coupled(cpl, U, P, rhs=1, tol=1e-12, prec="fp64")
+    assert st["status"] == 0
+    ref = pipeline.direct(coords, elems, 0.5, 80.0, fbar[1], dense=True, k0=7, u_prev=u_prev[1])
+    Pn = P.cpu().numpy()
+    assert Pn[7] == 0.0
+    assert rel(U.cpu().numpy(), ref["U"].ravel()) <= 1e-9
+    assert rel(Pn, ref["P"]) <= 1e-9

@@ -228,6 +228,27 @@ def test_stokes_preconditioned_fgmres_matches_direct_solve(name, prec):
     assert st2["status"] == 0 and st2["outer"] == 0
 
 
+def test_stokes_preconditioned_second_rhs():
+    """Right-hand side 1 of a two-right-hand-side Newton system."""
+    coords, elems = synth.mesh2d_square(9, 0.1, 4)
+    t = topology.build_faces(elems)
+    w = synth.stream_velocity(coords[t["face_vertices"]].mean(axis=1), seed=3)
+    fbar = np.stack([synth.element_means(lambda x, md=synth.fourier_modes(2, s): synth.fourier_force(x, md),
+                                         coords, elems, order=3) for s in (1, 6)])
+    case = (coords, elems, 0.01, 100.0, "newton", fbar, w)
+    mesh, _, hyb = gpu_setup(case)
+    pre = stokes_preconditioner(mesh, case)
+    W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve_preconditioned(hyb, pre, W, rhs=1, tol=1e-13, prec="ff")
+    assert st["status"] == 0
+    U = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(mesh.ne, dtype=torch.float64, device="cuda")
+    crhyb.cr_recover_up(hyb, W, U, P, rhs=1, normalise_p=True)
+    ref = pipeline.direct(coords, elems, 0.01, 100.0, fbar[1], "newton", w, dense=True)
+    assert rel(U.cpu().numpy(), ref["U"].ravel()) <= 1e-9
+    assert rel(P.cpu().numpy(), coupled.normalise_pressure(ref["P"], ref["geom"]["vol"])) <= 1e-9
+
+
 def test_stokes_preconditioned_steps_do_not_grow_with_the_mesh():
     """The GMRES steps of the Stokes-preconditioned Newton solve stay bounded as
     the mesh is refined (G_pre^{-1} G differs from I by the convection term),
