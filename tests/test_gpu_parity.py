@@ -472,3 +472,45 @@ def test_determinism(prec, persistent):
     a = solve_and_recover(hyb, 0, tol=1e-12, prec=prec, persistent=persistent)
     b = solve_and_recover(hyb, 0, tol=1e-12, prec=prec, persistent=persistent)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3]) and a[0] == b[0]
+
+
+@pytest.mark.parametrize("opts", [dict(method="pcg", prec="fp64"), dict(method="pcg", prec="ff"),
+                                  dict(method="pcg", prec="ff", persistent=True),
+                                  dict(method="pcg", prec="fp64", persistent=True),
+                                  dict(method="pcg", prec="mixed"), dict(method="gmres", prec="fp64"),
+                                  dict(method="bicgstab", prec="fp64")],
+                         ids=lambda o: "-".join(str(v) for v in o.values()))
+def test_zero_source_gives_zero_solution(opts):
+    """f = 0: S = 0, and every solver returns W = 0 at once (no division by ||S||)."""
+    coords, elems = synth.mesh2d_square(7, 0.2, 5)
+    case = (coords, elems, 1.0, 100.0, "none", np.zeros((1, elems.shape[0], 2)), None)
+    mesh, _, hyb = gpu_setup(case)
+    W = torch.ones(hyb.n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve(hyb, W, tol=1e-10, **opts)
+    assert st["status"] == 0 and st["iterations"] == 0 and st["relres"] == 0.0
+    assert float(W.abs().max()) == 0.0
+    U = torch.ones(hyb.n, dtype=torch.float64, device="cuda")
+    P = torch.ones(mesh.ne, dtype=torch.float64, device="cuda")
+    crhyb.cr_recover_up(hyb, W, U, P)
+    assert float(U.abs().max()) == 0.0 and float(P.abs().max()) == 0.0
+
+
+def test_zero_source_other_solvers():
+    coords, elems = synth.mesh2d_square(7, 0.2, 5)
+    zero = np.zeros((1, elems.shape[0], 2))
+    case = (coords, elems, 1.0, 100.0, "none", zero, None)
+    mesh, system, hyb = gpu_setup(case)
+    pre = stokes_preconditioner(mesh, case)
+    W = torch.ones(hyb.n, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-10)
+    assert st["status"] == 0 and st["outer"] == 0 and float(W.abs().max()) == 0.0
+    cpl = crhyb.cr_coupled_create(system)
+    U = torch.ones(hyb.n, dtype=torch.float64, device="cuda")
+    P = torch.ones(mesh.ne, dtype=torch.float64, device="cuda")
+    st = crhyb.cr_solve_coupled(cpl, U, P, tol=1e-10, prec="fp64")
+    assert st["status"] == 0 and st["iterations"] == 0
+    assert float(U.abs().max()) == 0.0 and float(P.abs().max()) == 0.0
+    batch = crhyb.cr_batch_create([hyb], prec="fp64")
+    Wb = [torch.ones(hyb.n, dtype=torch.float64, device="cuda")]
+    stb = crhyb.cr_solve_batched(batch, Wb, tol=1e-10)
+    assert stb[0]["status"] == 0 and float(Wb[0].abs().max()) == 0.0
