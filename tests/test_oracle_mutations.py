@@ -7,9 +7,11 @@ the pin that should catch it; the pin has to fail.
 import numpy as np
 import pytest
 
-from oracle import elements, topology
+from oracle import elements, krylov, topology
 import test_oracle_geometry as tg
 import test_oracle_hybrid as th
+import test_oracle_minres as tm
+import test_oracle_time as tt
 
 
 def wrong_D(geom):
@@ -37,16 +39,35 @@ def wrong_geometry_normal(coords, elems):
     return g
 
 
+def wrong_previous(topo, geom, mu, u_prev):
+    d = topo["d"]
+    ef = topo["elem_face"]
+    U = np.asarray(u_prev, dtype=np.float64).reshape(-1, d)
+    loc = np.where((ef >= 0)[:, :, None], U[np.maximum(ef, 0)], 0.0)
+    return ((mu * geom["vol"] / d)[:, None, None] * loc).reshape(ef.shape[0], -1)   # |K|/d, not |K|/(d+1)
+
+
+_orig_minres = krylov.minres
+
+
+def wrong_minres(K, b, minv, x0=None, rtol=1e-10, maxit=100000):
+    # the preconditioner applied twice: a different (still symmetric) method
+    return _orig_minres(K, b, minv * minv, x0=x0, rtol=rtol, maxit=maxit)
+
+
 CASES = [
     ("local_D", elements, wrong_D, lambda: th.test_constant_source_gives_zero_velocity_and_exact_pressure(2, 100.0)),
     ("local_S", elements, wrong_S, lambda: tg.test_S_matches_closed_form_integrals(2)),
     ("local_R", elements, wrong_R, lambda: th.test_constant_source_gives_zero_velocity_and_exact_pressure(2, 100.0)),
     ("owner_signs", topology, wrong_signs, lambda: th.test_hybrid_equals_coupled(2, 4, 1.0, 100.0, "none")),
     ("geometry", elements, wrong_geometry_normal, lambda: tg.test_area_normal_is_barycentric_gradient(2)),
+    ("local_R_previous", elements, wrong_previous, lambda: tt.test_previous_level_term_is_the_lumped_mass(2, 6)),
+    ("local_R_previous", elements, wrong_previous, lambda: tt.test_steady_solution_is_a_fixed_point_of_the_time_step(2, 7)),
+    ("minres", krylov, wrong_minres, lambda: tm.test_iterates_equal_scipy_minres(2, 10, 1000.0)),
 ]
 
 
-@pytest.mark.parametrize("name,module,bad,pin", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("name,module,bad,pin", CASES, ids=[f"{c[0]}-{i}" for i, c in enumerate(CASES)])
 def test_planted_mistake_is_caught(monkeypatch, name, module, bad, pin):
     topology.__dict__["_orig_owner_signs"] = topology.owner_signs
     topology.__dict__["_orig_geometry"] = elements.geometry
