@@ -237,9 +237,9 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
     };
     if ((rc = h->arena.alloc_n(&h->val64, nv))) return bail(rc);
     const bool lo32 = o && o->keep_lo_fp32, lo16 = o && o->keep_lo_bf16;
-    if (o && (o->keep_fp32 || lo32 || lo16) && (rc = h->arena.alloc_n(&h->val32, nv))) return bail(rc);
+    if (o && (o->keep_fp32 || lo16) && (rc = h->arena.alloc_n(&h->val32, nv))) return bail(rc);
     if (o && o->keep_bf16 && (rc = h->arena.alloc_n(&h->val16, nv))) return bail(rc);
-    if (lo32 && (rc = h->arena.alloc_n(&h->vlo32, nv))) return bail(rc);
+    if (lo32 && (rc = h->arena.alloc_n(&h->vff, nv))) return bail(rc);
     if (lo16 && (rc = h->arena.alloc_n(&h->vlo16, nv))) return bail(rc);
     if ((rc = h->arena.alloc_n(&h->S, n * s->nrhs)) || (rc = h->arena.alloc_n(&h->minv64, n)) ||
         (rc = h->arena.alloc_n(&h->minv32, n)) || (rc = h->arena.alloc_n(&h->status, 1)) ||
@@ -263,7 +263,7 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
             return cudaMemsetAsync(static_cast<char*>(base) + off * es, 0, npl * kSlice * es, m->stream);
         };
         if ((e = zero_last(h->val64, 8)) != cudaSuccess || (e = zero_last(h->val32, 4)) != cudaSuccess ||
-            (e = zero_last(h->val16, 2)) != cudaSuccess || (e = zero_last(h->vlo32, 4)) != cudaSuccess ||
+            (e = zero_last(h->val16, 2)) != cudaSuccess || (e = zero_last(h->vff, 8)) != cudaSuccess ||
             (e = zero_last(h->vlo16, 2)) != cudaSuccess)
             return bail(cuda_fail(e, "cudaMemsetAsync"));
     }
@@ -368,7 +368,7 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
     if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_preconditioned: the outer method is GMRES");
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG runs in FP64, FF or FF_BF16");
-    if ((o->prec == CR_PREC_FF && (!pre->val32 || !pre->vlo32)) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
+    if ((o->prec == CR_PREC_FF && !pre->vff) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: the float-float values of pre were not kept");
     if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve_preconditioned: tol must be > 0");
     const int restart = o->restart > 0 ? o->restart : 30;

@@ -87,7 +87,7 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
             return bail(fail(CR_ERR_ARG, "cr_batch_create: PCG needs a transient Stokes system (mu > 0, b_h = 0)"));
         if (h->s->nrhs > kPMaxRhs) return bail(fail(CR_ERR_ARG, "cr_batch_create: more than 4 right-hand sides"));
         if (h->m->nf < 1) return bail(fail(CR_ERR_ARG, "cr_batch_create: a mesh without interior faces"));
-        if (ff && (!h->val32 || (b->mode == 1 && !h->vlo32) || (b->mode == 2 && !h->vlo16)))
+        if ((b->mode == 1 && !h->vff) || (b->mode == 2 && (!h->val32 || !h->vlo16)))
             return bail(fail(CR_ERR_ARG, "cr_batch_create: the float-float values were not kept by cr_hybridise"));
         b->probs.push_back(h);
         const int R = h->s->nrhs;
@@ -118,7 +118,7 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
         sy.R = R;
         sy.cols = h->m->cols;
         sy.vh = h->val32;
-        sy.vl = b->mode == 2 ? static_cast<const void*>(h->vlo16) : static_cast<const void*>(h->vlo32);
+        sy.vl = b->mode == 2 ? static_cast<const void*>(h->vlo16) : static_cast<const void*>(h->vff);
         sy.v64 = h->val64;
         sy.minv32 = h->minv32;
         sy.minv64 = h->minv64;

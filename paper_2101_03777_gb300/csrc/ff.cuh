@@ -124,4 +124,16 @@ __device__ __forceinline__ float lo_val(const __nv_bfloat16* p) {
     return __uint_as_float(unsigned(u) << 16);
 }
 
+// (hi, lo) of matrix value idx: an interleaved float-float pair (one 8-byte load;
+// vh unused), or an FP32 high plane with a BF16 low plane
+__device__ __forceinline__ void hl_val(const float* vh, const float2* vl, size_t idx, float& h, float& l) {
+    const float2 v = __ldcs(vl + idx);
+    h = v.x;
+    l = v.y;
+}
+__device__ __forceinline__ void hl_val(const float* vh, const __nv_bfloat16* vl, size_t idx, float& h, float& l) {
+    h = __ldcs(vh + idx);
+    l = lo_val(vl + idx);
+}
+
 }  // namespace crhyb

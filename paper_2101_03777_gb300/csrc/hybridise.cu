@@ -42,7 +42,7 @@ struct Outputs {
     double* val64;
     float* val32;
     __nv_bfloat16* val16;
-    float* vlo32;
+    float2* vff;
     __nv_bfloat16* vlo16;
     int npl;             // value planes of the sliced ELL: (2d+1) d^2
     double* dpart;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void store_val(const Outputs& o, size_t idx, double v
     if (o.val32) o.val32[idx] = hi;
     if (o.val16) o.val16[idx] = __double2bfloat16(v);
     // float-float low parts: v - hi is exact in FP64, then rounded once
-    if (o.vlo32) o.vlo32[idx] = __double2float_rn(v - double(hi));
+    if (o.vff) o.vff[idx] = make_float2(hi, __double2float_rn(v - double(hi)));
     if (o.vlo16) o.vlo16[idx] = __double2bfloat16(v - double(hi));
 }
 
@@ -860,7 +860,7 @@ int launch_hybridise(cr_hybrid* h, cudaStream_t st) {
         CR_CUDA(cudaGetLastError());
         lam = h->lam;
     }
-    Outputs o{h->val64, h->val32, h->val16, h->vlo32, h->vlo16, h->nslot * m->d * m->d, h->dpart, h->spart,
+    Outputs o{h->val64, h->val32, h->val16, h->vff, h->vlo16, h->nslot * m->d * m->d, h->dpart, h->spart,
               h->status};
     if (s->conv != CR_CONV_NONE)
         k_condense_conv2<<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, lam, s->fbar, s->nrhs, o);

@@ -120,7 +120,7 @@ struct cr_hybrid {
     double* val64 = nullptr;
     float* val32 = nullptr;
     __nv_bfloat16* val16 = nullptr;
-    float* vlo32 = nullptr;       // float-float low part: G - val32, rounded to FP32
+    float2* vff = nullptr;        // float-float values interleaved: (fl32(g), fl32(g - fl32(g)))
     __nv_bfloat16* vlo16 = nullptr; // the same rounded to BF16
     double* S = nullptr;          // [nrhs][nf][d]
     double* minv64 = nullptr;     // [nf*d]

@@ -319,8 +319,7 @@ __device__ __forceinline__ void ff_row(const PSys& S, int64_t f, unsigned amask,
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const size_t idx = sell(f, (s * D + i) * D + j, NPV);
-                h[i][j] = __ldcs(vh + idx);
-                l[i][j] = lo_val(vl + idx);
+                hl_val(vh, vl, idx, h[i][j], l[i][j]);
             }
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -383,7 +382,8 @@ __device__ __forceinline__ void d_row(const PSys& S, int64_t f, unsigned amask, 
 
 template <int D, int MODE>
 struct Stage {
-    static constexpr bool kOn = D == 2 && CRHYB_STAGE_D2 != 0;  // d = 3 tiles would not fit twice
+    // d = 3 tiles would not fit twice; interleaved float-float values (FF32) are not staged
+    static constexpr bool kOn = D == 2 && CRHYB_STAGE_D2 != 0 && MODE != kModeFF32;
     static constexpr int NST = CRHYB_STAGE_D2 >= 2 ? 2 : 1;    // stages per block (2: prefetch the next tile)
     static constexpr int NS = 2 * D + 1, NPV = NS * D * D, NC = 2 * D;
     static constexpr int VB = MODE == kModeFP64 ? 8 : 4;      // bytes of a (high) value
@@ -560,7 +560,7 @@ __device__ __forceinline__ void prefetch_tile(const PArgs& a, int t) {
     const PSys& S = a.sys[td.x];
     const size_t sl = size_t(td.y) / kSlice;
     if (FF) {
-        l2_prefetch(S.vh + sl * NPV * kSlice, NPV * kSlice * sizeof(float));
+        if (!std::is_same<LT, float2>::value) l2_prefetch(S.vh + sl * NPV * kSlice, NPV * kSlice * sizeof(float));
         l2_prefetch(static_cast<const LT*>(S.vl) + sl * NPV * kSlice, NPV * kSlice * sizeof(LT));
     } else {
         l2_prefetch(S.v64 + sl * NPV * kSlice, NPV * kSlice * sizeof(double));
@@ -571,7 +571,7 @@ __device__ __forceinline__ void prefetch_tile(const PArgs& a, int t) {
 template <int D, int R, int MODE>
 __global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : 2)) k_pcg_persist(PArgs a) {
     constexpr bool FF = MODE != kModeFP64;
-    using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float>::type;
+    using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float2>::type;
     PCtl* ctl = a.ctl;
     if (int(blockIdx.x) == a.stall_block) return;   // testing hook (failure detection), see PArgs
     const int t0 = int(blockIdx.x) * a.tpb, t1 = min(t0 + a.tpb, a.ntiles);

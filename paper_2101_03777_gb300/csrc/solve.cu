@@ -392,7 +392,9 @@ __device__ __forceinline__ void ff_ell_row(int64_t f, const int32_t* __restrict_
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const size_t idx = sell(f, (s * D + i) * D + j, NS * D * D);
-                acc[i].mad(__ldcs(vh + idx), lo_val(vl + idx), xv[j].x, xv[j].y);
+                float h, l;
+                hl_val(vh, vl, idx, h, l);
+                acc[i].mad(h, l, xv[j].x, xv[j].y);
             }
     }
 #pragma unroll
@@ -988,14 +990,14 @@ int persistent_pcg(Ctx& c, const double* b, const double* x0, double* x, int mod
     cr_hybrid* h = c.h;
     cr_mesh* m = h->m;
     const bool ff = mode != 0;
-    if (ff && (!h->val32 || (mode == 2 && !h->vlo16) || (mode == 1 && !h->vlo32)))
+    if ((mode == 2 && (!h->val32 || !h->vlo16)) || (mode == 1 && !h->vff))
         return fail(CR_ERR_ARG, "cr_solve: the float-float values were not kept by cr_hybridise");
     PSys sy{};
     sy.nf = m->nf;
     sy.R = 1;
     sy.cols = m->cols;
     sy.vh = h->val32;
-    sy.vl = mode == 2 ? static_cast<const void*>(h->vlo16) : static_cast<const void*>(h->vlo32);
+    sy.vl = mode == 2 ? static_cast<const void*>(h->vlo16) : static_cast<const void*>(h->vff);
     sy.v64 = h->val64;
     sy.minv32 = h->minv32;
     sy.minv64 = h->minv64;
@@ -1248,7 +1250,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         if (o->method != CR_METHOD_PCG)
             return fail(CR_ERR_ARG, "cr_solve: the float-float precisions are implemented for PCG");
         const bool bf = o->prec == CR_PREC_FF_BF16;
-        if (!h->val32 || (bf && !h->vlo16) || (!bf && !h->vlo32))
+        if ((bf && (!h->val32 || !h->vlo16)) || (!bf && !h->vff))
             return fail(CR_ERR_ARG, "cr_solve: the float-float values were not kept by cr_hybridise");
         const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (bf ? 0.1 : 0.01);
         const bool trace = std::getenv("CRHYB_TRACE") != nullptr;
@@ -1272,7 +1274,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         int it_mark = 0;
         auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
             if (bf) ff_iteration<D, __nv_bfloat16>(c, h->vlo16, h->xf, h->rf, h->pf, h->qf, e0, e1);
-            else ff_iteration<D, float>(c, h->vlo32, h->xf, h->rf, h->pf, h->qf, e0, e1);
+            else ff_iteration<D, float2>(c, h->vff, h->xf, h->rf, h->pf, h->qf, e0, e1);
         };
         while (status == CR_OK && !c.hs->conv) {
             CR_TRY(pcg_loop(c, iter, chunk, graph, bf ? 4 : 3));
