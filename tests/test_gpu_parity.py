@@ -514,3 +514,30 @@ def test_zero_source_other_solvers():
     Wb = [torch.ones(hyb.n, dtype=torch.float64, device="cuda")]
     stb = crhyb.cr_solve_batched(batch, Wb, tol=1e-10)
     assert stb[0]["status"] == 0 and float(Wb[0].abs().max()) == 0.0
+
+
+def test_user_stream_orders_inputs_and_outputs():
+    """Every call orders its work after the caller's stream (the one given to
+    cr_mesh_load) and the caller's stream after it: a source written late on
+    that stream is the one the solve sees, and the recovered U can be read on
+    it without a device-wide synchronisation."""
+    case = make_case("2d_perturbed_37")
+    coords, elems, nu, mu, conv, fbar, w = case
+    ref = pipeline.direct(coords, elems, nu, mu, fbar[0], dense=True)
+    s = torch.cuda.Stream()
+    src = torch.from_numpy(np.ascontiguousarray(fbar)).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        fb = torch.zeros_like(src)
+        torch.cuda._sleep(int(5e7))               # the source arrives late on the user stream
+        fb.copy_(src)
+        mesh = crhyb.cr_mesh_load(coords, elems, stream=s)
+        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, nu, mu, fb), keep_fp32=False, keep_ff=True)
+        W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+        U = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
+        P = torch.zeros(mesh.ne, dtype=torch.float64, device="cuda")
+        crhyb.cr_solve(hyb, W, tol=1e-13, prec="ff", persistent=True)
+        crhyb.cr_recover_up(hyb, W, U, P, normalise_p=True)
+        Uc = U * 1.0                              # consumed on the user stream
+    s.synchronize()
+    assert rel(Uc.cpu().numpy(), ref["U"].ravel()) <= 1e-9
