@@ -521,15 +521,20 @@ def run_batch(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     keep = dict(keep_fp32=False, keep_ff=(prec == "ff"), keep_ff_bf16=(prec == "ff_bf16"))
-    tuned = {"bps": 0, "tune": None}
+    tuned = {"bps": 0, "grouping": 0}
 
     def step(fbs, profile=False, outs=None):
         hybs = [crhyb.cr_hybridise(crhyb.cr_assemble_coupled(m, q["nu"], q["mu"], f), **keep)
                 for m, q, f in zip(meshes, probs, fbs)]
-        batch = crhyb.cr_batch_create(hybs, prec=prec, autotune=tuned["bps"] == 0, blocks_per_sm=tuned["bps"])
+        batch = crhyb.cr_batch_create(hybs, prec=prec, autotune=tuned["bps"] == 0, blocks_per_sm=tuned["bps"],
+                                      rhs_grouping=tuned["grouping"])
         st = crhyb.cr_solve_batched(batch, Ws, tol=args.tol, max_iter=200000, profile=profile)
         if tuned["bps"] == 0:
-            tuned["bps"] = batch.info()["blocks_per_sm"]
+            # later steps plan the batch with the autotuner's choice: its resident blocks per SM
+            # and its grouping of the right-hand sides, read back from the number of systems
+            info = batch.info()
+            tuned["bps"] = info["blocks_per_sm"]
+            tuned["grouping"] = {len(probs): 1, 4 * len(probs): 2}.get(info["nsys"], 3)
         for k, (h, W) in enumerate(zip(hybs, Ws)):
             for r in range(4):
                 if outs is None:   # device U and P
@@ -603,8 +608,10 @@ def run_batch(args, rank, world):
                    "solver": PRECS[prec][3] + ", batched persistent launch", "tol": args.tol,
                    "iterations_min_max": [min(iters), max(iters)], "relres_max": max(s["relres"] for s in st),
                    "tiles": info["ntiles"], "grid": info["grid"], "blocks_per_sm_autotuned": info["blocks_per_sm"],
+                   "rhs_per_system_autotuned": {1: 4, 2: 1, 3: 2}[tuned["grouping"]],
                    "l2": "512 MB flush between steps", "parallelism": "1 GPU"},
-        "roofline": {"kernel": f"k_pcg_persist<{prec}, 4 rhs> (batched SpMM + update + direction phases)",
+        "roofline": {"kernel": f"k_pcg_persist<{prec}, {({1: 4, 2: 1, 3: 2}[tuned['grouping']])} rhs> "
+                                "(batched SpMM + update + direction phases)",
                      "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                      "traffic": None, "bytes_timed": work, "kernel_ms": kms, "peak_note": peak_note},
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
