@@ -57,6 +57,14 @@ namespace {
 #ifndef CRHYB_STAGE_D2
 #define CRHYB_STAGE_D2 0
 #endif
+// blocks per SM the register allocation of the two- and four-right-hand-side kernels aims at
+// (measured on the 64-mesh batch: 3 for R = 2, 1.52 s against 1.82 s at 2)
+#ifndef CRHYB_R2_MINB
+#define CRHYB_R2_MINB 3
+#endif
+#ifndef CRHYB_R4_MINB
+#define CRHYB_R4_MINB 2
+#endif
 // SpMV phase with per-thread loads: how many tiles ahead of the sweep one
 // thread of the block asks L2 to fetch the tile's values and columns (bulk L2
 // prefetch, no completion to wait for); 0 turns it off.
@@ -569,7 +577,7 @@ __device__ __forceinline__ void prefetch_tile(const PArgs& a, int t) {
 }
 
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : 2)) k_pcg_persist(PArgs a) {
+__global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : (R == 2 ? CRHYB_R2_MINB : CRHYB_R4_MINB))) k_pcg_persist(PArgs a) {
     constexpr bool FF = MODE != kModeFP64;
     using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float2>::type;
     PCtl* ctl = a.ctl;
