@@ -65,6 +65,13 @@ namespace {
 #ifndef CRHYB_R4_MINB
 #define CRHYB_R4_MINB 2
 #endif
+// blocks per SM of the 3D one-right-hand-side kernel, FP64 and float-float apart
+#ifndef CRHYB_3D_MINB
+#define CRHYB_3D_MINB 3
+#endif
+#ifndef CRHYB_3D_FF_MINB
+#define CRHYB_3D_FF_MINB 2
+#endif
 // SpMV phase with per-thread loads: how many tiles ahead of the sweep one
 // thread of the block asks L2 to fetch the tile's values and columns (bulk L2
 // prefetch, no completion to wait for); 0 turns it off.
@@ -576,8 +583,14 @@ __device__ __forceinline__ void prefetch_tile(const PArgs& a, int t) {
     l2_prefetch(S.cols + sl * 2 * D * kSlice, 2 * D * kSlice * sizeof(int32_t));
 }
 
+// the register budget each instantiation is compiled for, as blocks per SM
+constexpr int persist_min_blocks(int D, int R, int MODE) {
+    return R == 1 ? (D == 3 ? (MODE == kModeFP64 ? CRHYB_3D_MINB : CRHYB_3D_FF_MINB) : CRHYB_PERSIST_MINB)
+                  : (R == 2 ? CRHYB_R2_MINB : CRHYB_R4_MINB);
+}
+
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(kPBlock, (R == 1 && D == 3) ? 3 : (R == 1 ? CRHYB_PERSIST_MINB : (R == 2 ? CRHYB_R2_MINB : CRHYB_R4_MINB))) k_pcg_persist(PArgs a) {
+__global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg_persist(PArgs a) {
     constexpr bool FF = MODE != kModeFP64;
     using LT = typename std::conditional<MODE == kModeFFBF16, __nv_bfloat16, float2>::type;
     PCtl* ctl = a.ctl;
