@@ -24,7 +24,8 @@
 // Every barrier wait is bounded: a wait that runs out sets an error flag,
 // after which every block returns; the host reports CR_ERR_TIMEOUT.  Loop
 // decisions are taken from a snapshot of the control counters that the block
-// releasing a barrier writes, so that every block takes the same branch.
+// releasing the barrier at the end of an iteration (P3, U3) writes, so that
+// every block takes the same branch.
 
 #include <cuda_bf16.h>
 
@@ -155,29 +156,42 @@ __device__ __forceinline__ void strow(V* p, const V (&v)[D]) {
         for (int j = 0; j < D; ++j) p[j] = v[j];
 }
 
-// Grid barrier with a bounded wait.  The releasing block snapshots the loop
-// control counters before it opens the barrier.  Returns false in every
-// block once any wait has run out.
-__device__ __forceinline__ bool pbar(PCtl* ctl) {
+// Grid barrier with a bounded wait, on one 64-bit word: arrivals in the low
+// half, the generation in bits 32-62, an error bit on top.  An arrival's
+// atomic returns the generation it waits to see change, and the last arrival
+// bumps it and clears the count in one atomic, so a barrier costs one atomic
+// round trip per block.  With snap, the last arrival first copies the loop
+// control counters, which every block reads at the top of the next iteration.
+// A wait that runs out sets the error bit, which ends every other wait.
+// Returns false in every block once any wait has run out.
+constexpr unsigned long long kBarErr = 1ull << 63;
+__device__ __forceinline__ bool pbar(PCtl* ctl, bool snap) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* genp = &ctl->bar_gen;
-        const unsigned g = *genp;
         __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            ctl->bar_count = 0u;
-            ctl->snap_active = ld_vol(&ctl->active);
-            ctl->snap_upd = ld_vol(&ctl->upd);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
+        const unsigned long long old = atomicAdd(&ctl->bar, 1ull);
+        const unsigned gen = unsigned(old >> 32);
+        int ok = (old & kBarErr) == 0;
+        if (unsigned(old) == gridDim.x - 1) {
+            if (snap) {
+                ctl->snap_active = ld_vol(&ctl->active);
+                ctl->snap_upd = ld_vol(&ctl->upd);
+                __threadfence();
+            }
+            atomicAdd(&ctl->bar, (1ull << 32) - gridDim.x);
+        } else if (ok) {
+            const volatile unsigned long long* w = &ctl->bar;
             long long n = 0;
-            while (*genp == g) {
+            for (;;) {
+                const unsigned long long v = *w;
+                if (unsigned(v >> 32) != gen) {
+                    if (v & kBarErr) ok = 0;
+                    break;
+                }
                 if (++n > kSpinLimit) {
                     atomicExch(&ctl->err, 1);
+                    atomicOr(&ctl->bar, kBarErr);
                     ok = 0;
                     break;
                 }
@@ -185,7 +199,6 @@ __device__ __forceinline__ bool pbar(PCtl* ctl) {
             }
         }
         __threadfence();
-        if (ld_vol(&ctl->err)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -645,7 +658,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
                         }
                     }
                 }
-                if (!pbar(ctl)) return;
+                if (!pbar(ctl, false)) return;
                 phase_mark(a, 0, t_last);
             }
             // ---------------- U2: r64 = b - G x64 (FP64); r.r, b.b, r.M^{-1}r ----------------
@@ -747,7 +760,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
                 }
                 if (cur >= 0 && umask) flush();
             }
-            if (!pbar(ctl)) return;
+            if (!pbar(ctl, false)) return;
             phase_mark(a, 1, t_last);
             // ---------------- U3: r = sigma r64 (float-float); p = M^{-1} r + beta p ----------------
             for (int t = t0; t < t1; ++t) {
@@ -778,7 +791,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
                     }
                 }
             }
-            if (!pbar(ctl)) return;
+            if (!pbar(ctl, true)) return;
             phase_mark(a, 2, t_last);
             continue;
         }
@@ -934,7 +947,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
             }
             if (cur >= 0 && amask) flush();
         }
-        if (!pbar(ctl)) return;
+        if (!pbar(ctl, false)) return;
         phase_mark(a, 3, t_last);
         // ---------------- P2: x += alpha p, r -= alpha q; r.z, r.r ----------------
         {
@@ -1046,7 +1059,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
             }
             if (cur >= 0 && amask) flush();
         }
-        if (!pbar(ctl)) return;
+        if (!pbar(ctl, false)) return;
         phase_mark(a, 4, t_last);
         // ---------------- P3: p = M^{-1} r + beta p ----------------
         {
@@ -1099,7 +1112,7 @@ __global__ void __launch_bounds__(kPBlock, persist_min_blocks(D, R, MODE)) k_pcg
                 }
             }
         }
-        if (!pbar(ctl)) return;
+        if (!pbar(ctl, true)) return;
         phase_mark(a, 5, t_last);
         ++piters;
         after_update = false;

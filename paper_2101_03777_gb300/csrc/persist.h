@@ -41,7 +41,7 @@ struct PScal {
 
 // Control block: barrier state and loop-control counters.
 struct PCtl {
-    unsigned bar_count, bar_gen;
+    unsigned long long bar;     // grid barrier: arrivals (bits 0-31), generation (32-62), error (63)
     int err;                    // a bounded barrier wait ran out
     int active;                 // pairs not done
     int upd;                    // pairs with a reliable update due
