@@ -102,7 +102,7 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # DRAM bytes (read + write) per PCG iteration of the persistent kernel, from one ncu capture of
 # the kernel as committed (profiles/k_pcg_persist_cfg2_ff.md); "traffic" in the bench line is
 # this times the iterations of an average timed launch.  Re-measure whenever the kernel changes.
-DRAM_BYTES_PER_ITERATION = {("cfg2", "ff"): 9.709664e9 / 64}
+DRAM_BYTES_PER_ITERATION = {("cfg2", "ff"): 9.694581e9 / 64}
 SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
                "mixed": "k_pcg_spmv<FP32>"}
 DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
