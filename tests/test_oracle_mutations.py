@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import elements, krylov, topology
+import test_oracle_chebyshev as tc
 import test_oracle_geometry as tg
 import test_oracle_hybrid as th
 import test_oracle_minres as tm
@@ -55,6 +56,26 @@ def wrong_minres(K, b, minv, x0=None, rtol=1e-10, maxit=100000):
     return _orig_minres(K, b, minv * minv, x0=x0, rtol=rtol, maxit=maxit)
 
 
+def chebyshev_variant(start_width=False, rho_sign=1.0, keep_rho=True):
+    def apply(G, minv, r, degree, lmax, ratio):
+        a, b = lmax / ratio, lmax
+        theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        d = minv * r / (delta if start_width else theta)
+        z = np.zeros_like(r)
+        for j in range(degree):
+            z = z + d
+            if j == degree - 1:
+                break
+            res = r - G @ z
+            rho_next = 1.0 / (2.0 * sigma - rho_sign * rho)
+            d = rho_next * (rho if keep_rho else 1.0) * d + (2.0 * rho_next / delta) * (minv * res)
+            rho = rho_next
+        return z
+    return apply
+
+
 CASES = [
     ("local_D", elements, wrong_D, lambda: th.test_constant_source_gives_zero_velocity_and_exact_pressure(2, 100.0)),
     ("local_S", elements, wrong_S, lambda: tg.test_S_matches_closed_form_integrals(2)),
@@ -64,6 +85,9 @@ CASES = [
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_previous_level_term_is_the_lumped_mass(2, 6)),
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_steady_solution_is_a_fixed_point_of_the_time_step(2, 7)),
     ("minres", krylov, wrong_minres, lambda: tm.test_iterates_equal_scipy_minres(2, 10, 1000.0)),
+    ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
+    ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
+    ("chebyshev_apply", krylov, chebyshev_variant(keep_rho=False), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
 ]
 
 
