@@ -9,10 +9,11 @@ mesh topology (cr_mesh_load, host) is set up once and reported separately.
 
 Metric: time to solution (seconds per step, lower is better) on the default
 workload (2D transient Stokes, 512x512 squares split into 524,288 perturbed
-triangles, nu = 1, dt = 1e-3).  `value` is the first precision of --precs
-(float-float Jacobi-PCG with FP64 reliable updates by default); every timed
-precision (native FP64, float-float, float-float with BF16 low parts, FP32
-inside FP64 refinement) is reported under "precisions" with its SpMV roofline.  Each timed step is bracketed by CUDA events on the
+triangles, nu = 1, dt = 1e-3).  `value` is the first solver of --precs (by
+default FP64 PCG with the Chebyshev polynomial preconditioner of degree 4);
+every timed solver (that one, float-float Jacobi-PCG with FP64 reliable
+updates, native FP64 Jacobi-PCG, float-float with BF16 low parts, FP32 inside
+FP64 refinement) is reported under "precisions" with its roofline.  Each timed step is bracketed by CUDA events on the
 caller's stream; a 512 MB buffer is written between steps to flush L2.
 
 With --gpus N > 1 (torchrun), every rank solves its own replica of the
@@ -55,7 +56,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--graph", type=int, default=1, help="multi-kernel path: replay iteration chunks as graphs")
     ap.add_argument("--persistent", type=int, default=1, help="PCG in one cooperative persistent launch")
-    ap.add_argument("--precs", default="ff,fp64,ff_bf16",
+    ap.add_argument("--precs", default="fp64_cheb,ff,fp64,ff_bf16",
                     help="comma-separated solve precisions to time (the first is the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
@@ -70,7 +71,12 @@ def parse():
                     help="profiling runs only: mesh size n in place of the workload's (n x n or n^3 cells)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="profiling runs only: stop every solve after this many iterations (no convergence check)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.workload in ("cfg4", "cfg5"):
+        # the Chebyshev-preconditioned PCG serves the single transient Stokes solve; the batch
+        # and the Newton step keep their Jacobi-preconditioned solvers
+        args.precs = ",".join(x for x in args.precs.split(",") if x and x != "fp64_cheb") or "ff"
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -97,16 +103,21 @@ PRECS = {
                 "Jacobi-PCG in float-float, G low plane in BF16 (6 B/value), FP64 reliable updates"),
     "mixed": (dict(prec="mixed", max_iter=400000, inner_tol=1e-4), 4, 4,
               "FP32 Jacobi-PCG restarted inside FP64 iterative refinement"),
+    "fp64_cheb": (dict(prec="fp64", max_iter=200000, precond="chebyshev", poly_degree=4), 8, 8,
+                  "PCG, native FP64, Chebyshev polynomial preconditioner of degree 4 (Jacobi-preconditioned "
+                  "Chebyshev steps under the Gershgorin bound; interval ratio 1000 in 2D, 100 in 3D), "
+                  "graph-replayed kernels"),
 }
+CHEB_RATIO = {2: 1000.0, 3: 100.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # DRAM bytes (read + write) per PCG iteration of the persistent kernel, from one ncu capture of
 # the kernel as committed (profiles/k_pcg_persist_cfg2_ff.md); "traffic" in the bench line is
 # this times the iterations of an average timed launch.  Re-measure whenever the kernel changes.
 DRAM_BYTES_PER_ITERATION = {("cfg2", "ff"): 9.694581e9 / 64}
 SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
-               "mixed": "k_pcg_spmv<FP32>"}
+               "mixed": "k_pcg_spmv<FP32>", "fp64_cheb": "k_cheb_step<FP64> (SpMV + Chebyshev update)"}
 DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
-         "mixed": "f32 (f64 refinement)"}
+         "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64"}
 
 
 def solve_opts(prec, tol, graph, profile, persistent):
@@ -288,6 +299,8 @@ def run_ours(args, rank, world):
                                  keep_ff_bf16=(prec == "ff_bf16"))
         o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
         o["check_every"] = args.check_every
+        if o.get("precond") == "chebyshev":
+            o["poly_ratio"] = CHEB_RATIO[d]
         if args.max_iter:
             o["max_iter"] = args.max_iter
         st = crhyb.cr_solve(hyb, Wt, raise_on_error=not args.max_iter, **o)
@@ -365,7 +378,18 @@ def run_ours(args, rank, world):
         st_main, st_spmv = prof[prec]
         solver = PRECS[prec][3]
         spmv = None
-        if st_spmv is not None:
+        if st_spmv is not None and prec == "fp64_cheb":
+            # the Chebyshev steps: degree - 1 launches per CG iteration, each the SpMV over G fused
+            # with the vector update (reads r, d, M^{-1}; writes d and the other z buffer)
+            deg = PRECS[prec][0]["poly_degree"]
+            step_bytes = spmv_bytes + 4 * N * xb
+            nit = max(st_spmv["spmv_launches"], 1)
+            ms = st_spmv["spmv_ms"] / (nit * (deg - 1))
+            spmv = {"kernel": SPMV_KERNEL[prec], "bound": "hbm", "achieved": step_bytes / (ms * 1e-3) / 1e9,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                    "traffic": None, "bytes_per_launch": step_bytes, "avg_launch_ms": ms,
+                    "launches_timed": nit * (deg - 1), "peak_note": peak_note}
+        elif st_spmv is not None:
             # stand-alone SpMV launches of the multi-kernel path
             nl = max(st_spmv["spmv_launches"], 1)
             ms = st_spmv["spmv_ms"] / nl
@@ -386,6 +410,8 @@ def run_ours(args, rank, world):
                     "iterations_timed": piters, "kernel_ms": kms, "peak_note": peak_note}
             solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
                       f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
+        elif prec == "fp64_cheb":
+            roof = dict(spmv)
         elif args.persistent:
             # the persistent PCG kernel: per iteration the SpMV plus the vector phases (the update
             # reads x, r, p, q and writes x, r; the direction reads r, p and writes p: 9 vector

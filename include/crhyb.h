@@ -98,6 +98,18 @@ enum cr_prec { CR_PREC_FP64 = 0, CR_PREC_MIXED_FP32 = 1, CR_PREC_MIXED_BF16 = 2,
  * a Jacobi preconditioner stalls (the Newton/Oseen steps on fine meshes). */
 enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1, CR_METHOD_BICGSTAB = 2 };
 
+/* Preconditioner of PCG.  JACOBI: z = M^{-1} r, M = diag(G).  CHEBYSHEV: z is
+ * poly_degree steps of the Jacobi-preconditioned Chebyshev iteration on G z = r
+ * from z = 0 (Saad, Iterative Methods for Sparse Linear Systems, Algorithm
+ * 12.1) over the interval [lmax/poly_ratio, lmax], lmax the Gershgorin bound
+ * of M^{-1} G (largest absolute row sum of M^{-1} G, computed once per
+ * hybridised system).  lmax bounds the spectrum, so the preconditioner is a
+ * symmetric positive definite polynomial in M^{-1} G times M^{-1}: CG keeps
+ * its guarantees and takes about poly_degree times fewer iterations, each
+ * applying G poly_degree times. */
+enum cr_precond { CR_PRECOND_JACOBI = 0, CR_PRECOND_CHEBYSHEV = 1 };
+#define CR_MAX_POLY_DEGREE 16
+
 typedef struct cr_hyb_opts {
     int32_t keep_fp32;  /* also keep FP32 values of G (needed by CR_PREC_MIXED_FP32) */
     int32_t keep_bf16;  /* also keep BF16 values of G (needed by CR_PREC_MIXED_BF16) */
@@ -125,6 +137,13 @@ typedef struct cr_solve_opts {
                            persistent launch (grid barriers with bounded waits between its phases;
                            up to check_every*64 iterations per launch) instead of three launches
                            per iteration; profile and use_graph are ignored then */
+    int32_t precond;    /* enum cr_precond (0: Jacobi).  CHEBYSHEV is implemented for PCG in FP64 on
+                           the multi-kernel path (persistent is ignored): an iteration is the SpMV of CG,
+                           the update, poly_degree - 1 Chebyshev steps (each one SpMV fused with its
+                           vector update) and the direction; profile = 1 times the Chebyshev steps.
+                           cr_solve_preconditioned, cr_solve_coupled and cr_solve_batched take Jacobi only */
+    int32_t poly_degree;/* CHEBYSHEV: polynomial degree, 2..CR_MAX_POLY_DEGREE (0 selects 4) */
+    double poly_ratio;  /* CHEBYSHEV: lmax / (lower end of the interval), > 1 (<= 0 selects 100) */
 } cr_solve_opts;
 
 #define CR_MAX_RESTART 64

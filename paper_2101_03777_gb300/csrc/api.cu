@@ -335,11 +335,23 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     const int restart = o->restart > 0 ? o->restart : 30;
     if (o->method == CR_METHOD_GMRES && (restart < 1 || restart > CR_MAX_RESTART))
         return fail(CR_ERR_ARG, "cr_solve: restart must be in [1, CR_MAX_RESTART]");
+    if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
+        return fail(CR_ERR_ARG, "cr_solve: bad preconditioner");
+    if (o->precond == CR_PRECOND_CHEBYSHEV) {
+        if (o->method != CR_METHOD_PCG || o->prec != CR_PREC_FP64)
+            return fail(CR_ERR_ARG, "cr_solve: the Chebyshev preconditioner is implemented for PCG in FP64");
+        const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+        if (deg < 2 || deg > CR_MAX_POLY_DEGREE)
+            return fail(CR_ERR_ARG, "cr_solve: poly_degree must be in [2, CR_MAX_POLY_DEGREE]");
+        if (!(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
+            return fail(CR_ERR_ARG, "cr_solve: poly_ratio must be > 1 (or <= 0 for the default)");
+    }
     cr_mesh* m = h->m;
     const size_t n = size_t(m->nf) * m->d;
     StreamScope scope(m);
     CR_TRY(ensure_workspace(h, o->method == CR_METHOD_GMRES, restart, o->prec));
     if (o->method == CR_METHOD_BICGSTAB) CR_TRY(ensure_workspace(h, false, restart, -1));
+    if (o->precond == CR_PRECOND_CHEBYSHEV && !h->cheb) CR_TRY(h->arena.alloc_n(&h->cheb, 3 * n + 1));
     double* Wd = W;
     const bool host = !is_device_pointer(W);
     if (host) {
@@ -366,6 +378,8 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: pre needs a transient Stokes system (mu > 0, b_h = 0), "
                                 "whose G is SPD");
     if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_preconditioned: the outer method is GMRES");
+    if (o->precond != CR_PRECOND_JACOBI)
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG is Jacobi-preconditioned");
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG runs in FP64, FF or FF_BF16");
     if ((o->prec == CR_PREC_FF && !pre->vff) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))

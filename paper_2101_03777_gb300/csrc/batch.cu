@@ -183,6 +183,7 @@ extern "C" int cr_batch_info(const cr_batch* b, int32_t* nsys, int32_t* ntiles, 
 extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* const* W, cr_solve_stats* st) {
     if (!b || !o || !W) return fail(CR_ERR_ARG, "cr_solve_batched: NULL argument");
     if (o->method != CR_METHOD_PCG) return fail(CR_ERR_ARG, "cr_solve_batched: the batched solve is PCG");
+    if (o->precond != CR_PRECOND_JACOBI) return fail(CR_ERR_ARG, "cr_solve_batched: the batched PCG is Jacobi-preconditioned");
     const int np = int(b->probs.size());
     for (int k = 0; k < np; ++k)
         if (!W[k] || !is_device_pointer(W[k])) return fail(CR_ERR_ARG, "cr_solve_batched: W[k] must be device memory");

@@ -438,6 +438,8 @@ extern "C" int cr_solve_coupled(cr_coupled* c, int rhs, const cr_solve_opts* o, 
     if (!c || !o || !U || !P) return fail(CR_ERR_ARG, "cr_solve_coupled: NULL argument");
     if (rhs < 0 || rhs >= c->s->nrhs) return fail(CR_ERR_ARG, "cr_solve_coupled: rhs out of range");
     if (o->prec != CR_PREC_FP64) return fail(CR_ERR_ARG, "cr_solve_coupled: MINRES runs in FP64");
+    if (o->precond != CR_PRECOND_JACOBI)
+        return fail(CR_ERR_ARG, "cr_solve_coupled: MINRES takes its own diagonal preconditioner (precond 0)");
     if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve_coupled: tol must be > 0");
     cr_mesh* m = c->m;
     if (!is_device_pointer(U) || !is_device_pointer(P))

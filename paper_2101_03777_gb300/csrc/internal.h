@@ -142,6 +142,8 @@ struct cr_hybrid {
     double* V64 = nullptr;        // GMRES basis FP64 [restart+1][N]
     float* Z32 = nullptr;         // GMRES scratch vector
     double* Z64 = nullptr;
+    double* cheb = nullptr;       // Chebyshev preconditioner: z (two buffers), d [3][N], lmax slot
+    double cheb_lmax = -1.0;      // Gershgorin bound of M^{-1} G (computed on first use)
     double* fgz = nullptr;        // flexible GMRES: preconditioned vectors FP64 [restart][N]
     int fgz_m = 0;
     void* scal = nullptr;         // device Krylov scalars

@@ -4,7 +4,11 @@
 //     Section 3.2 item 6) in FP64, or in FP32 (FP32 or BF16 matrix values)
 //     inside FP64 iterative refinement;
 //   * restarted GMRES(m) with right Jacobi preconditioning for the
-//     nonsymmetric or indefinite systems (Section 4.3), same precisions.
+//     nonsymmetric or indefinite systems (Section 4.3), same precisions;
+//   * PCG in FP64 with a Chebyshev polynomial preconditioner (Jacobi-
+//     preconditioned Chebyshev steps under a Gershgorin bound of the
+//     spectrum), which trades CG iterations, and their reductions, for
+//     SpMVs fused with the Chebyshev vector update.
 //
 // Every scalar of the iteration lives in device memory; the host only reads
 // a status record every `check_every` iterations.  Kernels of an iteration
@@ -42,6 +46,7 @@ struct KScal {
     float2 alpha_ff, beta_ff;                   // alpha and beta in float-float for the FF iteration
     double sigma;                               // FF vectors hold sigma * (the FP64 quantities)
     double omega, rho_old;                      // BiCGStab
+    double cheb[2 * CR_MAX_POLY_DEGREE];        // Chebyshev preconditioner: 1/theta, then (c1_j, c2_j)
     double hb[CR_MAX_RESTART + 1];              // Gram-Schmidt coefficients of the current step
     double H[(CR_MAX_RESTART + 1) * CR_MAX_RESTART];
     double cs[CR_MAX_RESTART], sn[CR_MAX_RESTART], g[CR_MAX_RESTART + 1];
@@ -174,6 +179,148 @@ __global__ void __launch_bounds__(kBlock) k_pcg_dir(int64_t n, XT* __restrict__ 
         const XT z = minv[k] * r[k];
         p[k] = first ? z : fma(beta, p[k], z);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev-preconditioned CG (FP64).  The preconditioner z = P(r) is
+// `degree` steps of the Chebyshev iteration on M^{-1} G z = M^{-1} r from
+// z = 0 over [lmax/ratio, lmax] (Saad, Algorithm 12.1), lmax the Gershgorin
+// bound of M^{-1} G.  With theta, delta the interval's centre and half width:
+//   d_0 = M^{-1} r / theta,  z_1 = d_0;
+//   step j = 1 .. degree-1:  d_j = c1_j d_{j-1} + c2_j M^{-1} (r - G z_j),
+//                            z_{j+1} = z_j + d_j,
+// with rho_0 = delta/theta, rho_j = 1/(2 theta/delta - rho_{j-1}),
+// c1_j = rho_j rho_{j-1}, c2_j = 2 rho_j / delta (host-computed, in KScal).
+// The first step is fused into the CG update, every later one into its SpMV
+// (z double-buffered: the SpMV gathers z_j while z_{j+1} is written).
+// ---------------------------------------------------------------------------
+
+// lmax = max over rows of sum_j |G_ij| / G_ii; the non-negative maximum is
+// taken on the bit pattern (integer order = numeric order for doubles >= 0).
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_gershgorin(int64_t nf, const double* __restrict__ vals,
+                                                       const double* __restrict__ minv, unsigned long long* out) {
+    constexpr int NS = 2 * D + 1;
+    double mx = 0.0;
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double rs = 0.0;
+#pragma unroll
+            for (int sl = 0; sl < NS; ++sl)
+#pragma unroll
+                for (int j = 0; j < D; ++j) rs += fabs(vals[sell(f, (sl * D + i) * D + j, NS * D * D)]);
+            mx = fmax(mx, rs * fabs(minv[f * D + i]));
+        }
+    }
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) sh[warp] = mx;
+    __syncthreads();
+    if (warp == 0) {
+        mx = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(mx)));
+    }
+}
+
+// z = d = M^{-1} r / theta (the first Chebyshev step)
+__global__ void __launch_bounds__(kBlock) k_cheb_start(int64_t n, const double* __restrict__ r,
+                                                      const double* __restrict__ minv, double* __restrict__ z,
+                                                      double* __restrict__ d, const KScal* sc) {
+    if (sc->done) return;
+    const double c0 = sc->cheb[0];
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double v = c0 * minv[k] * r[k];
+        z[k] = v;
+        d[k] = v;
+    }
+}
+
+// Chebyshev step j: zout = zin + d_j, d_j = c1_j d + c2_j M^{-1} (r - G zin);
+// on the last step r.z and, in the last block, beta = r.z / r.z(previous).
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_cheb_step(int64_t nf, const int32_t* __restrict__ cols,
+                                                     const double* __restrict__ vals, const double* __restrict__ minv,
+                                                     const double* __restrict__ r, const double* __restrict__ zin,
+                                                     double* __restrict__ zout, double* __restrict__ d, KScal* sc,
+                                                     RedBuf red, int j, int last) {
+    if (sc->done) return;
+    const double c1 = sc->cheb[2 * j - 1], c2 = sc->cheb[2 * j];
+    double part[1] = {0.0};
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        double y[D];
+        ell_row<D, double, double, double>(f, cols, vals, zin, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int64_t k = f * D + i;
+            const double rk = r[k];
+            const double dn = fma(c1, d[k], c2 * minv[k] * (rk - y[i]));
+            const double zn = zin[k] + dn;
+            d[k] = dn;
+            zout[k] = zn;
+            part[0] += rk * zn;
+        }
+    }
+    if (!last) return;
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double rz = tot[0];
+        if (!(rz > 0.0) || !isfinite(rz)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->rz_prev = sc->rz;
+            sc->beta = rz / sc->rz;
+            sc->rz = rz;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, r.r; then the first Chebyshev step z = d =
+// M^{-1} r / theta.  Last block: iteration count, convergence, the limit.
+__global__ void __launch_bounds__(kBlock) k_cpcg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                       const double* __restrict__ p, const double* __restrict__ q,
+                                                       const double* __restrict__ minv, double* __restrict__ z,
+                                                       double* __restrict__ d, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const double alpha = sc->alpha, c0 = sc->cheb[0];
+    double part[1] = {0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] = fma(alpha, p[k], x[k]);
+        const double rn = fma(-alpha, q[k], r[k]);
+        r[k] = rn;
+        const double v = c0 * minv[k] * rn;
+        z[k] = v;
+        d[k] = v;
+        part[0] += rn * rn;
+    }
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->it += 1;
+        if (!isfinite(tot[0])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[0] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// p = z + beta p   (first: p = z)
+__global__ void __launch_bounds__(kBlock) k_cpcg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                                                    const KScal* sc, int first) {
+    if (sc->done) return;
+    const double beta = first ? 0.0 : sc->beta;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        p[k] = first ? z[k] : fma(beta, p[k], z[k]);
 }
 
 // r = b - G x in FP64 (x optional: NULL means x = 0), optionally r32 = float(r);
@@ -872,11 +1019,13 @@ void ff_iteration(Ctx& c, const LT* vl, float2* x, float2* r, float2* p, float2*
 
 // Run PCG iterations until sc->done, in chunks of `chunk` iterations,
 // replayed as a CUDA graph when asked.  `iter(e0, e1)` launches one
-// iteration.  Assumes x, r, p, rz, tol2 are set.
+// iteration.  Assumes x, r, p, rz, tol2 are set.  `variant` distinguishes
+// iterations with different launch sequences under the same graph slot.
 template <typename Iter>
-int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey) {
+int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey, int variant = 0) {
     cr_hybrid* h = c.h;
-    if (graph && (h->graph_key[gkey] != chunk || !h->graph_exec[gkey])) {
+    const int key = chunk + (variant << 20);
+    if (graph && (h->graph_key[gkey] != key || !h->graph_exec[gkey])) {
         if (h->graph_exec[gkey]) { cudaGraphExecDestroy(h->graph_exec[gkey]); h->graph_exec[gkey] = nullptr; }
         cudaGraph_t gr;
         const int64_t before = c.launches;
@@ -888,7 +1037,7 @@ int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey) {
         cudaError_t e = cudaGraphInstantiate(&h->graph_exec[gkey], gr, 0);
         cudaGraphDestroy(gr);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        h->graph_key[gkey] = chunk;
+        h->graph_key[gkey] = key;
     }
     const bool prof = c.profile && !graph;
     if (prof && int(h->prof_ev.size()) < 2 * chunk) {
@@ -1170,6 +1319,39 @@ int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, 
     return status;
 }
 
+// The Chebyshev preconditioner's coefficients for this solve (into hs->cheb):
+// the Gershgorin bound lmax of M^{-1} G is computed once per hybridised system.
+template <int D>
+int chebyshev_setup(cr_hybrid* h, const cr_solve_opts* o, cudaStream_t st, KScal* hs) {
+    const int64_t n = h->m->nf * D;
+    if (n == 0) h->cheb_lmax = 1.0;   // no unknowns: any interval will do
+    if (h->cheb_lmax < 0.0) {
+        unsigned long long* slot = reinterpret_cast<unsigned long long*>(h->cheb + 3 * n);
+        CR_CUDA(cudaMemsetAsync(slot, 0, sizeof(unsigned long long), st));
+        k_gershgorin<D><<<grid_for(h->m->nf), kBlock, 0, st>>>(h->m->nf, h->val64, h->minv64, slot);
+        CR_CUDA(cudaGetLastError());
+        double lmax = 0.0;
+        CR_CUDA(cudaMemcpyAsync(&lmax, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CR_CUDA(cudaStreamSynchronize(st));
+        if (!(lmax > 0.0) || !std::isfinite(lmax))
+            return fail(CR_ERR_BREAKDOWN, "cr_solve: no positive Gershgorin bound for the Chebyshev preconditioner");
+        h->cheb_lmax = lmax;
+    }
+    const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+    const double ratio = o->poly_ratio > 0.0 ? o->poly_ratio : 100.0;
+    const double b = h->cheb_lmax, a = b / ratio;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+    double rho = delta / theta;
+    hs->cheb[0] = 1.0 / theta;
+    for (int j = 1; j < deg; ++j) {
+        const double rn = 1.0 / (2.0 * theta / delta - rho);
+        hs->cheb[2 * j - 1] = rn * rho;
+        hs->cheb[2 * j] = 2.0 * rn / delta;
+        rho = rn;
+    }
+    return CR_OK;
+}
+
 template <int D>
 int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
     cr_mesh* m = h->m;
@@ -1188,6 +1370,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     std::memset(c.hs, 0, sizeof(KScal));
     c.hs->max_it = gmax;
     c.hs->m = o->restart > 0 ? o->restart : 30;
+    const bool cheb = o->precond == CR_PRECOND_CHEBYSHEV;
+    if (cheb) CR_TRY(chebyshev_setup<D>(h, o, c.st, c.hs));
     CR_CUDA(cudaMemcpyAsync(c.sc, c.hs, sizeof(KScal), cudaMemcpyHostToDevice, c.st));
     if (o->use_x0) CR_CUDA(cudaMemcpyAsync(h->x64, W, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.st));
     else CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
@@ -1229,6 +1413,38 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (c.hs->done || restart >= max_outer) break;
                 ++outer;
             }
+        } else if (o->method == CR_METHOD_PCG && cheb) {
+            // CG iteration: SpMV + p.q, update + r.r + first Chebyshev step, the
+            // remaining degree - 1 steps (SpMV each; the last one forms r.z and
+            // beta), direction.  profile = 1 brackets the Chebyshev steps.
+            const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+            double* zb[2] = {h->cheb, h->cheb + c.n};
+            double* dv = h->cheb + 2 * c.n;
+            auto cheb_steps = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                if (e0) cudaEventRecord(e0, c.st);
+                for (int j = 1; j < deg; ++j)
+                    k_cheb_step<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->minv64, h->r64,
+                                                               zb[(j - 1) & 1], zb[j & 1], dv, c.sc, h->red, j,
+                                                               j == deg - 1);
+                if (e1) cudaEventRecord(e1, c.st);
+                c.launches += deg - 1;
+            };
+            k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
+            ++c.launches;
+            cheb_steps(nullptr, nullptr);
+            k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 1);
+            ++c.launches;
+            CR_CUDA(cudaGetLastError());
+            auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                k_pcg_spmv<D, double, double><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->p64, h->q64,
+                                                                          c.sc, h->red);
+                k_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->p64, h->q64, h->minv64, zb[0], dv,
+                                                       c.sc, h->red);
+                cheb_steps(e0, e1);
+                k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 0);
+                c.launches += 3;
+            };
+            CR_TRY(pcg_loop(c, iter, chunk, graph, 6, deg));
         } else if (o->method == CR_METHOD_PCG) {
             k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
             ++c.launches;
@@ -1425,7 +1641,7 @@ int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts
 }
 
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {
-    if (o->persistent && o->method == CR_METHOD_PCG &&
+    if (o->persistent && o->method == CR_METHOD_PCG && o->precond == CR_PRECOND_JACOBI &&
         (o->prec == CR_PREC_FP64 || o->prec == CR_PREC_FF || o->prec == CR_PREC_FF_BF16))
         return h->m->d == 2 ? solve_persistent<2>(h, rhs, o, Wdev, st) : solve_persistent<3>(h, rhs, o, Wdev, st);
     return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);

@@ -19,7 +19,7 @@ checked on properties that the oracle computes from the paper at any size:
     perturbed 512x512 mesh have condition numbers near 3e3, so the two FP64
     evaluation orders differ by about 1e-12 of max|G|).
 The solves run as bench.py times them: persistent float-float and FP64
-Jacobi-PCG for transient Stokes; for the Newton step, flexible GMRES
+Jacobi-PCG and FP64 Chebyshev-preconditioned PCG for transient Stokes; for the Newton step, flexible GMRES
 preconditioned by inner float-float PCG solves with the transient Stokes G of
 the same mesh (Jacobi-GMRES(30) does not reach 1e-10 on it: 28,538 iterations
 at 64x64, no convergence within 60,000 at 128x128; Jacobi-BiCGStab converges up
@@ -69,13 +69,16 @@ def oracle(name, with_g):
 CASES = [
     ("cfg2", dict(method="pcg", prec="ff", persistent=True), True),
     ("cfg2", dict(method="pcg", prec="fp64", persistent=True), True),
+    ("cfg2", dict(method="pcg", prec="fp64", precond="chebyshev", poly_degree=4, poly_ratio=1000.0,
+                  use_graph=True), True),
     ("cfg3", dict(method="pcg", prec="fp64", persistent=True), False),
     ("cfg3", dict(method="pcg", prec="ff", persistent=True), False),
     ("cfg5", dict(method="stokes-fgmres", prec="ff"), True),
 ]
 
 
-@pytest.mark.parametrize("name,opts,with_g", CASES, ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}" for c in CASES])
+@pytest.mark.parametrize("name,opts,with_g", CASES,
+                         ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}-{c[1].get('precond', 'jacobi')}" for c in CASES])
 def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
     p, w = problem(name)
     o = oracle(name, with_g)
