@@ -2,7 +2,8 @@
 
 Each solver is checked against a library direct solve (scipy's sparse LU)
 on matrices of the kinds the method produces: the SPD hybridised matrix of
-transient Stokes and the nonsymmetric one of a Newton step.
+transient Stokes and the nonsymmetric one of a Newton step.  PCG's iterates
+are also checked against SciPy's CG with the same preconditioner.
 """
 
 import numpy as np
@@ -38,6 +39,23 @@ def test_pcg_matches_direct():
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-10
     # the recursive residual tracks the true residual
     assert np.linalg.norm(S - G @ x) / np.linalg.norm(S) < 1e-12
+
+
+@pytest.mark.parametrize("dim,n,mu", [(2, 10, 1000.0), (3, 2, 100.0)])
+def test_pcg_iterates_equal_scipy_cg(dim, n, mu):
+    """After k steps the oracle's PCG iterate is SciPy's CG iterate with the
+    same Jacobi preconditioner (the same recurrences; only rounding differs),
+    which fixes alpha, beta and the preconditioned inner products."""
+    import inspect
+    G, S = hybridised(dim, n, 1.0, mu)
+    minv = krylov.jacobi(G)
+    M = spla.LinearOperator(G.shape, matvec=lambda v: minv * v)
+    kw = {"rtol": 0.0, "atol": 0.0} if "rtol" in inspect.signature(spla.cg).parameters else {"tol": 0.0, "atol": 0.0}
+    for k in (3, 20):
+        ours, it, _ = krylov.pcg(G, S, minv, rtol=0.0, maxit=k)
+        theirs, _ = spla.cg(G, S, M=M, maxiter=k, **kw)
+        assert it == k
+        assert np.linalg.norm(ours - theirs) <= 1e-10 * np.linalg.norm(theirs)
 
 
 def test_pcg_zero_rhs_and_warm_start():

@@ -10,6 +10,7 @@ import pytest
 from oracle import elements, krylov, topology
 import test_oracle_chebyshev as tc
 import test_oracle_geometry as tg
+import test_oracle_krylov as tk
 import test_oracle_hybrid as th
 import test_oracle_minres as tm
 import test_oracle_time as tt
@@ -56,6 +57,33 @@ def wrong_minres(K, b, minv, x0=None, rtol=1e-10, maxit=100000):
     return _orig_minres(K, b, minv * minv, x0=x0, rtol=rtol, maxit=maxit)
 
 
+def wrong_pcg(G, b, minv, x0=None, rtol=1e-10, maxit=100000):
+    # beta from the unpreconditioned residuals (r.r) instead of r.M^{-1}r
+    x = np.zeros_like(b) if x0 is None else x0.astype(b.dtype).copy()
+    r = b - G @ x
+    bn = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / bn]
+    z = minv * r
+    p = z.copy()
+    rz = np.dot(r, z)
+    rr = np.dot(r, r)
+    it = 0
+    while it < maxit:
+        q = G @ p
+        alpha = rz / np.dot(p, q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        hist.append(np.linalg.norm(r) / bn)
+        if hist[-1] <= rtol:
+            break
+        z = minv * r
+        rr_new = np.dot(r, r)
+        p = z + (rr_new / rr) * p
+        rz, rr = np.dot(r, z), rr_new
+    return x, it, hist
+
+
 def chebyshev_variant(start_width=False, rho_sign=1.0, keep_rho=True):
     def apply(G, minv, r, degree, lmax, ratio):
         a, b = lmax / ratio, lmax
@@ -85,6 +113,7 @@ CASES = [
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_previous_level_term_is_the_lumped_mass(2, 6)),
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_steady_solution_is_a_fixed_point_of_the_time_step(2, 7)),
     ("minres", krylov, wrong_minres, lambda: tm.test_iterates_equal_scipy_minres(2, 10, 1000.0)),
+    ("pcg", krylov, wrong_pcg, lambda: tk.test_pcg_iterates_equal_scipy_cg(2, 10, 1000.0)),
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(keep_rho=False), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
