@@ -3,7 +3,8 @@
 Each solver is checked against a library direct solve (scipy's sparse LU)
 on matrices of the kinds the method produces: the SPD hybridised matrix of
 transient Stokes and the nonsymmetric one of a Newton step.  PCG's iterates
-are also checked against SciPy's CG with the same preconditioner.
+are also checked against SciPy's CG with the same preconditioner, and a GMRES
+cycle against the minimal-residual iterate it is defined as.
 """
 
 import numpy as np
@@ -56,6 +57,29 @@ def test_pcg_iterates_equal_scipy_cg(dim, n, mu):
         theirs, _ = spla.cg(G, S, M=M, maxiter=k, **kw)
         assert it == k
         assert np.linalg.norm(ours - theirs) <= 1e-10 * np.linalg.norm(theirs)
+
+
+@pytest.mark.parametrize("m", [3, 6, 9])
+def test_gmres_cycle_is_the_minimal_residual_iterate(m):
+    """One cycle of m right-preconditioned GMRES steps from x = 0 gives the
+    x in M K_m(G M, S) of least ||S - G x||_2 (the definition, solved here by a
+    dense least-squares problem on an orthonormalised Krylov basis), and its
+    running estimate is that iterate's relative residual."""
+    G, S = hybridised(2, 8, 0.01, 100.0, "newton")
+    minv = krylov.jacobi(G)
+    A = G.toarray()
+    x, it, hist = krylov.gmres(G, S, minv, restart=m, rtol=0.0, maxit=m)
+    assert it == m
+    basis, v = [], minv * S
+    for _ in range(m):
+        v = v / np.linalg.norm(v)
+        basis.append(v)
+        v = minv * (A @ v)
+    Q, _ = np.linalg.qr(np.column_stack(basis))
+    y, *_ = np.linalg.lstsq(A @ Q, S, rcond=None)
+    xmin = Q @ y
+    assert np.linalg.norm(x - xmin) <= 1e-9 * np.linalg.norm(xmin)
+    assert abs(hist[-1] - np.linalg.norm(S - A @ x) / np.linalg.norm(S)) <= 1e-10
 
 
 def test_pcg_zero_rhs_and_warm_start():

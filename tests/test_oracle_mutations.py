@@ -50,6 +50,12 @@ def wrong_previous(topo, geom, mu, u_prev):
 
 
 _orig_minres = krylov.minres
+_orig_gmres = krylov.gmres
+
+
+def wrong_gmres(G, b, minv, x0=None, restart=30, rtol=1e-10, maxit=100000):
+    # the preconditioner applied twice: another Krylov space
+    return _orig_gmres(G, b, minv * minv, x0=x0, restart=restart, rtol=rtol, maxit=maxit)
 
 
 def wrong_minres(K, b, minv, x0=None, rtol=1e-10, maxit=100000):
@@ -114,6 +120,7 @@ CASES = [
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_steady_solution_is_a_fixed_point_of_the_time_step(2, 7)),
     ("minres", krylov, wrong_minres, lambda: tm.test_iterates_equal_scipy_minres(2, 10, 1000.0)),
     ("pcg", krylov, wrong_pcg, lambda: tk.test_pcg_iterates_equal_scipy_cg(2, 10, 1000.0)),
+    ("gmres", krylov, wrong_gmres, lambda: tk.test_gmres_cycle_is_the_minimal_residual_iterate(6)),
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(keep_rho=False), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
