@@ -7,7 +7,7 @@ the pin that should catch it; the pin has to fail.
 import numpy as np
 import pytest
 
-from oracle import elements, krylov, topology
+from oracle import elements, hybrid, krylov, topology
 import test_oracle_chebyshev as tc
 import test_oracle_geometry as tg
 import test_oracle_krylov as tk
@@ -90,6 +90,17 @@ def wrong_pcg(G, b, minv, x0=None, rtol=1e-10, maxit=100000):
     return x, it, hist
 
 
+def _edited(module, name, old, new):
+    """The function `name` of `module` with one source line replaced (a planted mistake)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(module, name)))
+    assert old in src
+    ns = dict(vars(module))
+    exec(compile(src.replace(old, new, 1), f"<mutated {name}>", "exec"), ns)
+    return ns[name]
+
+
 def chebyshev_variant(start_width=False, rho_sign=1.0, keep_rho=True):
     def apply(G, minv, r, degree, lmax, ratio):
         a, b = lmax / ratio, lmax
@@ -119,6 +130,12 @@ CASES = [
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_previous_level_term_is_the_lumped_mass(2, 6)),
     ("local_R_previous", elements, wrong_previous, lambda: tt.test_steady_solution_is_a_fixed_point_of_the_time_step(2, 7)),
     ("minres", krylov, wrong_minres, lambda: tm.test_iterates_equal_scipy_minres(2, 10, 1000.0)),
+    ("hybridise", hybrid,
+     _edited(hybrid, "hybridise", "M = Ainv - np.einsum(", "M = Ainv + 0.0 * np.einsum("),   # pressure not eliminated
+     lambda: th.test_hybrid_equals_coupled(2, 4, 1.0, 100.0, "none")),
+    ("hybridise", hybrid,
+     _edited(hybrid, "hybridise", "M[k0] = Ainv[k0]", "pass"),                                # K_0 not special-cased
+     lambda: th.test_hybrid_equals_coupled(2, 4, 1.0, 100.0, "none")),
     ("pcg", krylov, wrong_pcg, lambda: tk.test_pcg_iterates_equal_scipy_cg(2, 10, 1000.0)),
     ("gmres", krylov, wrong_gmres, lambda: tk.test_gmres_cycle_is_the_minimal_residual_iterate(6)),
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
