@@ -12,7 +12,9 @@ of Eq. 10 solved without hybridisation.  ``refine`` is classical mixed-precision
 iterative refinement: inner solves in float32, residual and update in float64.
 ``chebyshev_pcg`` is CG with a polynomial preconditioner (a fixed number of
 Jacobi-preconditioned Chebyshev steps, Saad Algorithm 12.1) on the interval
-below a Gershgorin bound of the spectrum.
+below a Gershgorin bound of the spectrum.  ``deflated_pcg`` keeps the CG
+directions G-orthogonal to given vectors (deflated CG), removing their
+eigenvalues from the convergence.
 """
 
 import numpy as np
@@ -123,6 +125,50 @@ def chebyshev_pcg(G, b, minv, degree, ratio, lmax=None, x0=None, rtol=1e-10, max
         z = chebyshev_apply(G, minv, r, degree, lmax, ratio)
         rz_new = np.dot(r, z)
         p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, hist
+
+
+def deflated_pcg(G, b, precond, V, rtol=1e-10, maxit=100000):
+    """CG on G x = b with the directions kept G-orthogonal to the columns of V
+    (deflated CG: Saad, Yeung, Erhel and Guyomarc'h, SIAM J. Sci. Comput. 21,
+    2000), preconditioned by the function `precond` (z = precond(r)).
+
+    With E = V^t G V: x_0 = V E^{-1} V^t b, so that V^t r_0 = 0; then
+    z = precond(r), p = z + beta p - V E^{-1} (G V)^t z.  Every residual stays
+    orthogonal to V, and the eigenvalues of the columns of V drop out of the
+    convergence.  V may have no columns (plain PCG).  Stops when
+    ||r||_2 <= rtol ||b||_2 (recursive r).  Returns (x, iterations, history)."""
+    V = np.asarray(V, dtype=b.dtype).reshape(b.shape[0], -1)
+    GV = G @ V if V.shape[1] else V
+    E = V.T @ GV
+
+    def project(z):   # remove the G-components along V
+        return z - V @ np.linalg.solve(E, GV.T @ z) if V.shape[1] else z
+
+    x = V @ np.linalg.solve(E, V.T @ b) if V.shape[1] else np.zeros_like(b)
+    r = b - G @ x
+    bn = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / bn if bn > 0 else 0.0]
+    if bn == 0.0:
+        return x, 0, hist
+    z = precond(r)
+    p = project(z)
+    rz = np.dot(r, z)
+    it = 0
+    while it < maxit:
+        q = G @ p
+        alpha = rz / np.dot(p, q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        rn = np.linalg.norm(r) / bn
+        hist.append(rn)
+        if rn <= rtol:
+            break
+        z = precond(r)
+        rz_new = np.dot(r, z)
+        p = project(z) + (rz_new / rz) * p
         rz = rz_new
     return x, it, hist
 

@@ -11,6 +11,7 @@ import pytest
 
 from oracle import elements, hybrid, krylov, topology
 import test_oracle_chebyshev as tc
+import test_oracle_deflation as tdf
 import test_oracle_geometry as tg
 import test_oracle_krylov as tk
 import test_oracle_hybrid as th
@@ -139,6 +140,9 @@ CASES = [
      _edited(hybrid, "hybridise", "M[k0] = Ainv[k0]", "pass"),                                # K_0 not special-cased
      lambda: th.test_hybrid_equals_coupled(2, 4, 1.0, 100.0, "none")),
     ("pcg", krylov, wrong_pcg, lambda: tk.test_pcg_iterates_equal_scipy_cg(2, 10, 1000.0)),
+    ("deflated_pcg", krylov,
+     _edited(krylov, "deflated_pcg", "p = project(z) + (rz_new / rz) * p", "p = z + (rz_new / rz) * p"),   # no projection
+     lambda: tdf.test_residuals_stay_orthogonal_to_the_vectors()),
     ("gmres", krylov, wrong_gmres, lambda: tk.test_gmres_cycle_is_the_minimal_residual_iterate(6)),
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
