@@ -30,7 +30,12 @@
  * - Array arguments are owned by the caller.  Unless stated otherwise an array
  *   argument may be a device pointer or a host pointer: the library asks the
  *   CUDA driver which one it is and copies host data through its own staging
- *   buffers (the copies are part of the call and are stream ordered).
+ *   buffers (the copies are part of the call and are stream ordered).  Device
+ *   arrays must live on the GPU that is current during the call; device
+ *   memory of another GPU is rejected with CR_ERR_ARG before any device work
+ *   (the library enables no peer access).
+ * - A mesh and every handle made from it belong to the GPU that was current
+ *   at cr_mesh_load: a call with another GPU current fails with CR_ERR_ARG.
  * - All device work is ordered on the CUDA stream given to cr_mesh_load (NULL
  *   = the legacy default stream).  Calls that return results to the host
  *   (statistics, host output arrays) synchronise that stream before returning.
@@ -399,13 +404,16 @@ void cr_destroy_batch(cr_batch* b);
  *   b, x    float64 [nf][dim], device
  *   r       float64 [nf][dim], device, or NULL (norms only)
  *   norms2  float64 [2], host or device
- *   stream  cudaStream_t (NULL = the legacy default stream); the call synchronises it
- * The first call on a device looks up the device address of the scratch array
- * (cudaGetSymbolAddress, once per device, with that device current); make that
- * first call before any stream capture.  Every call shares the one scratch
- * array, whose counters the call clears first: calls that overlap on the same
- * GPU (from several threads or streams) race and must be serialised by the
- * caller.  Errors: CR_ERR_ARG, CR_ERR_CUDA. */
+ *   stream  cudaStream_t (NULL = the legacy default stream); every call, nf = 0
+ *           included, synchronises it before returning
+ * Every call reads its results back to the host and synchronises its stream,
+ * so it cannot be recorded inside a CUDA stream capture.  The first call on a
+ * device looks up the device address of the scratch array (cudaGetSymbolAddress,
+ * once per device, with that device current).  Every call shares the one
+ * scratch array, whose counters the call clears first: calls that overlap on
+ * the same GPU (from several threads or streams) race and must be serialised
+ * by the caller.  Arrays on another GPU than the current one are rejected with
+ * CR_ERR_ARG.  Errors: CR_ERR_ARG, CR_ERR_CUDA. */
 int cr_residual_noalloc(int dim, int64_t nf, int nslot, const int32_t* cols, const double* vals, const double* b,
                         const double* x, double* r, double* norms2, void* stream);
 

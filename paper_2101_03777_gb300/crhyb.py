@@ -317,8 +317,10 @@ def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):
     stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
              "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
              "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
-    if rc != CR_OK and raise_on_error:
-        _check(rc)
+    if rc != CR_OK:
+        stats["error"] = load_library().cr_last_error().decode()
+        if raise_on_error:
+            _check(rc)
     return stats
 
 

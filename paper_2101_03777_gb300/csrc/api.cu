@@ -3,6 +3,7 @@
 // hybridise.cu (element kernels) and solve.cu (Krylov kernels).
 
 #include <cstdio>
+#include <initializer_list>
 #include <cstring>
 #include <string>
 
@@ -29,14 +30,41 @@ int cuda_fail(cudaError_t e, const char* what) {
     return code;
 }
 
-bool is_device_pointer(const void* p) {
-    if (!p) return false;
+int pointer_place(const void* p, int* owner) {
+    if (owner) *owner = -1;
+    if (!p) return 0;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();   // clear the sticky-free error of an unknown pointer
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type != cudaMemoryTypeDevice) return 0;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (owner) *owner = a.device;
+    return a.device == cur ? 1 : -1;
+}
+
+bool is_device_pointer(const void* p) { return pointer_place(p, nullptr) == 1; }
+
+int check_call(const cr_mesh* m, const char* fn, std::initializer_list<const void*> ptrs) {
+    int cur = -1;
+    CR_CUDA(cudaGetDevice(&cur));
+    if (m && m->device != cur)
+        return fail(CR_ERR_ARG, std::string(fn) + ": the handle belongs to GPU " + std::to_string(m->device) +
+                                    " but GPU " + std::to_string(cur) + " is current");
+    for (const void* p : ptrs) {
+        int owner = -1;
+        if (pointer_place(p, &owner) < 0)
+            return fail(CR_ERR_ARG, std::string(fn) + ": an array argument is device memory of GPU " +
+                                        std::to_string(owner) + " but GPU " + std::to_string(cur) +
+                                        " is current (no peer access is set up)");
+    }
+    return CR_OK;
 }
 
 int DevArena::alloc(void** p, size_t bytes) {
@@ -145,6 +173,7 @@ extern "C" int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double*
         return fail(CR_ERR_ARG, "cr_assemble_coupled: the convection term needs dim 2 and the field w");
     if (p->mu == 0.0 && !m->has_mis)
         return fail(CR_ERR_ARG, "cr_assemble_coupled: mu = 0 needs a mesh loaded with need_mis = 1");
+    CR_TRY(check_call(m, "cr_assemble_coupled", {fbar, w, blocks_out}));
     cr_system* s = new cr_system();
     s->m = m;
     s->nu = p->nu;
@@ -199,6 +228,7 @@ extern "C" int cr_system_set_previous(cr_system* s, const double* u_prev) {
         return CR_OK;
     }
     if (!(s->mu > 0.0)) return fail(CR_ERR_ARG, "cr_system_set_previous: an implicit Euler step needs mu = 1/dt > 0");
+    CR_TRY(check_call(s->m, "cr_system_set_previous", {u_prev}));
     cr_mesh* m = s->m;
     const size_t n = size_t(s->nrhs) * m->nf * m->d;
     StreamScope scope(m);
@@ -219,6 +249,7 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
     if (!out) return fail(CR_ERR_ARG, "cr_hybridise: out is NULL");
     *out = nullptr;
     if (!s) return fail(CR_ERR_ARG, "cr_hybridise: NULL system");
+    CR_TRY(check_call(s->m, "cr_hybridise", {}));
     cr_mesh* m = s->m;
     const int d = m->d;
     cr_hybrid* h = new cr_hybrid();
@@ -282,6 +313,7 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
 
 extern "C" int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S) {
     if (!h) return fail(CR_ERR_ARG, "cr_hybrid_export: NULL handle");
+    CR_TRY(check_call(h->m, "cr_hybrid_export", {cols, vals, S}));
     cr_mesh* m = h->m;
     const size_t nf = size_t(m->nf);
     cudaError_t e;
@@ -315,6 +347,7 @@ extern "C" int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals,
 
 extern "C" int cr_apply_G(cr_hybrid* h, const double* x, double* y) {
     if (!h || !x || !y) return fail(CR_ERR_ARG, "cr_apply_G: NULL argument");
+    CR_TRY(check_call(h->m, "cr_apply_G", {x, y}));
     if (!is_device_pointer(x) || !is_device_pointer(y)) return fail(CR_ERR_ARG, "cr_apply_G: device pointers expected");
     StreamScope scope(h->m);
     return launch_spmv64(h, x, y, h->m->stream);
@@ -323,6 +356,7 @@ extern "C" int cr_apply_G(cr_hybrid* h, const double* x, double* y) {
 extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
     if (st) std::memset(st, 0, sizeof(*st));
     if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
+    CR_TRY(check_call(h->m, "cr_solve", {W}));
     if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve: rhs out of range");
     if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES && o->method != CR_METHOD_BICGSTAB)
         return fail(CR_ERR_ARG, "cr_solve: bad method");
@@ -372,6 +406,7 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
                                        cr_solve_stats* st) {
     if (st) std::memset(st, 0, sizeof(*st));
     if (!h || !pre || !o || !W) return fail(CR_ERR_ARG, "cr_solve_preconditioned: NULL argument");
+    CR_TRY(check_call(h->m, "cr_solve_preconditioned", {W}));
     if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve_preconditioned: rhs out of range");
     if (pre->m != h->m) return fail(CR_ERR_ARG, "cr_solve_preconditioned: pre must be hybridised on the same mesh");
     if (pre->s->mu <= 0.0 || pre->s->conv != CR_CONV_NONE)
@@ -419,6 +454,7 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
 extern "C" int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise_p,
                              double* jump) {
     if (!h || !W || !U || !P) return fail(CR_ERR_ARG, "cr_recover_up: NULL argument");
+    CR_TRY(check_call(h->m, "cr_recover_up", {W, U, P}));
     if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_recover_up: rhs out of range");
     cr_mesh* m = h->m;
     const size_t n = size_t(m->nf) * m->d, ne = size_t(m->ne);

@@ -65,6 +65,8 @@ extern "C" int cr_batch_create(cr_hybrid* const* probs, int nprob, const cr_batc
     const int prec = o ? o->prec : CR_PREC_FF;
     if (prec != CR_PREC_FP64 && prec != CR_PREC_FF && prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_batch_create: the batched solve runs in FP64, FF or FF_BF16");
+    for (int k = 0; k < nprob; ++k)
+        if (probs[k]) CR_TRY(check_call(probs[k]->m, "cr_batch_create", {}));
     cr_batch* b = new cr_batch();
     auto bail = [&](int rc) {
         cr_destroy_batch(b);
@@ -185,8 +187,10 @@ extern "C" int cr_solve_batched(cr_batch* b, const cr_solve_opts* o, double* con
     if (o->method != CR_METHOD_PCG) return fail(CR_ERR_ARG, "cr_solve_batched: the batched solve is PCG");
     if (o->precond != CR_PRECOND_JACOBI) return fail(CR_ERR_ARG, "cr_solve_batched: the batched PCG is Jacobi-preconditioned");
     const int np = int(b->probs.size());
+    CR_TRY(check_call(b->probs[0]->m, "cr_solve_batched", {}));
     for (int k = 0; k < np; ++k)
-        if (!W[k] || !is_device_pointer(W[k])) return fail(CR_ERR_ARG, "cr_solve_batched: W[k] must be device memory");
+        if (!W[k] || !is_device_pointer(W[k]))
+            return fail(CR_ERR_ARG, "cr_solve_batched: W[k] must be device memory of the current GPU");
     cudaStream_t s = b->stream;
     StreamScope scope(b->probs[0]->m);
     const double delta = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : (b->mode == 2 ? 0.1 : 0.01);

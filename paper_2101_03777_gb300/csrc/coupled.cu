@@ -388,6 +388,7 @@ extern "C" int cr_coupled_create(cr_system* s, cr_coupled** out) {
     if (!out) return fail(CR_ERR_ARG, "cr_coupled_create: out is NULL");
     *out = nullptr;
     if (!s) return fail(CR_ERR_ARG, "cr_coupled_create: NULL system");
+    CR_TRY(check_call(s->m, "cr_coupled_create", {}));
     if (s->conv != CR_CONV_NONE)
         return fail(CR_ERR_ARG, "cr_coupled_create: MINRES needs the symmetric (Stokes) system, conv = NONE");
     cr_mesh* m = s->m;
@@ -436,6 +437,7 @@ extern "C" int cr_solve_coupled(cr_coupled* c, int rhs, const cr_solve_opts* o, 
                                 cr_solve_stats* st) {
     if (st) std::memset(st, 0, sizeof(*st));
     if (!c || !o || !U || !P) return fail(CR_ERR_ARG, "cr_solve_coupled: NULL argument");
+    CR_TRY(check_call(c->m, "cr_solve_coupled", {U, P}));
     if (rhs < 0 || rhs >= c->s->nrhs) return fail(CR_ERR_ARG, "cr_solve_coupled: rhs out of range");
     if (o->prec != CR_PREC_FP64) return fail(CR_ERR_ARG, "cr_solve_coupled: MINRES runs in FP64");
     if (o->precond != CR_PRECOND_JACOBI)

@@ -23,10 +23,13 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <initializer_list>
 #include <string>
 #include <vector>
 
 #include "../../include/crhyb.h"
+
+struct cr_mesh;
 
 namespace crhyb {
 
@@ -53,7 +56,15 @@ int cuda_fail(cudaError_t e, const char* what);
         if (_rc != CR_OK) return _rc;                                   \
     } while (0)
 
+// Where an array argument lives: 1 device memory of the current GPU (or
+// managed memory), 0 host memory, -1 device memory of another GPU (*owner
+// receives that GPU).  is_device_pointer(p) is pointer_place(p) == 1.
+int pointer_place(const void* p, int* owner);
 bool is_device_pointer(const void* p);
+// Argument check of an entry point: the handle's mesh (may be NULL) was
+// loaded on the current GPU, and no pointer is device memory of another GPU
+// (the library launches on the current GPU and enables no peer access).
+int check_call(const cr_mesh* m, const char* fn, std::initializer_list<const void*> ptrs);
 
 // Device allocation helper: records the pointer for release by the owner.
 struct DevArena {
@@ -78,6 +89,7 @@ struct RedBuf {
 
 struct cr_mesh {
     int d = 0;
+    int device = 0;    // the GPU that was current at cr_mesh_load; every later call on it must run there
     int64_t ne = 0, nv = 0, nf = 0, nf_ext = 0;
     int64_t nfp = 0;   // face rows rounded up to whole slices of the sliced ELL (a multiple of 256)
     int k0 = 0;

@@ -47,7 +47,7 @@ extern "C" int cr_mesh_load(int dim, const double* coords, int64_t nv, const int
     if (dim != 2 && dim != 3) return fail(CR_ERR_ARG, "cr_mesh_load: dim must be 2 or 3");
     if (!coords || !elems || nv <= 0 || ne <= 1) return fail(CR_ERR_ARG, "cr_mesh_load: empty mesh");
     if (ne >= (int64_t(1) << 31) / (dim + 1)) return fail(CR_ERR_ARG, "cr_mesh_load: too many simplices");
-    if (is_device_pointer(coords) || is_device_pointer(elems))
+    if (pointer_place(coords, nullptr) != 0 || pointer_place(elems, nullptr) != 0)
         return fail(CR_ERR_ARG, "cr_mesh_load: coords and elems must be host arrays");
     const int d = dim, dp1 = dim + 1;
     int k0 = opts ? opts->k0 : 0;
@@ -185,7 +185,9 @@ extern "C" int cr_mesh_load(int dim, const double* coords, int64_t nv, const int
     // ---- device copies ----
     m->user_stream = static_cast<cudaStream_t>(stream);
     auto cleanup = [&](int rc) { cr_destroy_mesh(m); return rc; };
-    cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice"));
+    e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreateWithFlags"));
     if ((e = cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming)) != cudaSuccess)
@@ -240,11 +242,13 @@ static int copy_out(void* dst, const void* src, size_t bytes) {
 
 extern "C" int cr_mesh_faces(const cr_mesh* m, int32_t* fv) {
     if (!m || !fv) return crhyb::fail(CR_ERR_ARG, "cr_mesh_faces: NULL argument");
+    CR_TRY(crhyb::check_call(m, "cr_mesh_faces", {fv}));
     return copy_out(fv, m->h_face_vertices.data(), sizeof(int32_t) * m->h_face_vertices.size());
 }
 
 extern "C" int cr_mesh_face_elements(const cr_mesh* m, int32_t* fe, int32_t* fl) {
     if (!m) return crhyb::fail(CR_ERR_ARG, "cr_mesh_face_elements: NULL mesh");
+    CR_TRY(crhyb::check_call(m, "cr_mesh_face_elements", {fe, fl}));
     if (fe) CR_TRY(copy_out(fe, m->h_face_elems.data(), sizeof(int32_t) * m->h_face_elems.size()));
     if (fl) CR_TRY(copy_out(fl, m->h_face_local.data(), sizeof(int32_t) * m->h_face_local.size()));
     return CR_OK;
@@ -253,6 +257,7 @@ extern "C" int cr_mesh_face_elements(const cr_mesh* m, int32_t* fe, int32_t* fl)
 extern "C" int cr_mesh_mis(const cr_mesh* m, uint8_t* in_m1) {
     if (!m || !in_m1) return crhyb::fail(CR_ERR_ARG, "cr_mesh_mis: NULL argument");
     if (!m->has_mis) return crhyb::fail(CR_ERR_ARG, "cr_mesh_mis: mesh loaded without need_mis");
+    CR_TRY(crhyb::check_call(m, "cr_mesh_mis", {in_m1}));
     return copy_out(in_m1, m->h_mis.data(), m->h_mis.size());
 }
 

@@ -131,11 +131,16 @@ extern "C" int cr_residual_noalloc(int dim, int64_t nf, int nslot, const int32_t
                                 "capacity of " + std::to_string(kNaMaxRows) + " rows");
     if (nslot < 1 || nslot > 2 * dim + 1) return fail(CR_ERR_ARG, "cr_residual_noalloc: nslot must be in [1, 2*dim+1]");
     if (!norms2) return fail(CR_ERR_ARG, "cr_residual_noalloc: norms2 is NULL");
+    CR_TRY(check_call(nullptr, "cr_residual_noalloc", {cols, vals, b, x, r, norms2}));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool dev_out = is_device_pointer(norms2);
     if (nf == 0) {
-        if (dev_out) CR_CUDA(cudaMemsetAsync(norms2, 0, 2 * sizeof(double), st));
-        else norms2[0] = norms2[1] = 0.0;
+        if (dev_out) {
+            CR_CUDA(cudaMemsetAsync(norms2, 0, 2 * sizeof(double), st));
+            CR_CUDA(cudaStreamSynchronize(st));
+        } else {
+            norms2[0] = norms2[1] = 0.0;
+        }
         return CR_OK;
     }
     if (!is_device_pointer(cols) || !is_device_pointer(vals) || !is_device_pointer(b) || !is_device_pointer(x) ||

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 
 #include "device_common.cuh"
 #include "ff.cuh"
@@ -1195,7 +1196,7 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
     int status = P.status;
     if (status == CR_OK && !P.conv) status = CR_ERR_NOT_CONVERGED;
     const double relres = P.bb > 0 ? std::sqrt(P.orr / P.bb) : 0.0;
-    if (status == CR_OK && !(relres <= o->tol) && !(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
+    if (status == CR_OK && !(relres <= o->tol)) status = CR_ERR_NOT_CONVERGED;
     if (st) {
         st->iterations = P.it;
         st->outer = P.outer;
@@ -1303,7 +1304,7 @@ int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, 
     CR_CUDA(cudaGetLastError());
     CR_TRY(read_scal(c));
     const double relres = c.hs->obb > 0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
-    if (status == CR_OK && !(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
+    if (status == CR_OK && !(relres <= o->tol)) status = CR_ERR_NOT_CONVERGED;
     if (st) {
         st->iterations = int32_t(inner_its);
         st->outer = steps;
@@ -1317,6 +1318,39 @@ int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, 
     if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve_preconditioned: step limit reached before the tolerance");
     if (status == CR_ERR_BREAKDOWN) return fail(status, "cr_solve_preconditioned: breakdown (zero Arnoldi vector, NaN, or p.Gp <= 0 in the inner PCG)");
     return status;
+}
+
+// FP64 PCG whose recursively updated residual decides the stop: once it meets
+// the tolerance, the FP64 true residual b - G x decides.  A true residual still
+// above the tolerance (the recursive one drifts from it on ill-conditioned
+// systems) restarts CG from the iterate with r = b - G x, up to max_outer
+// times, so that CR_OK always means ||b - G x|| <= tol ||b||.  `start` forms
+// the first direction from r; `run` iterates until the device flags done.
+template <int D, typename Start, typename Run>
+int restarted_pcg(Ctx& c, Start start, Run run, const double* b, int max_outer, double tol, int& outer) {
+    cr_hybrid* h = c.h;
+    const int ggrid = grid_for(c.nf);
+    for (;;) {
+        CR_TRY(read_scal(c));
+        if (c.hs->done) return CR_OK;   // the start (true) residual already meets the tolerance
+        start();
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(run());
+        CR_TRY(read_scal(c));
+        if (c.hs->status != CR_OK) return CR_OK;
+        // mode 1: r = b - G x, rz, rr, tol2; done when the true residual meets tol
+        k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, h->m->cols, h->val64, b, h->x64, h->r64, nullptr,
+                                                    h->minv64, c.sc, h->red, 1, tol, 0.0);
+        ++c.launches;
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->done) return CR_OK;
+        if (outer >= max_outer || c.hs->it >= c.hs->max_it) {
+            c.hs->status = CR_ERR_NOT_CONVERGED;
+            return CR_OK;
+        }
+        ++outer;
+    }
 }
 
 // The Chebyshev preconditioner's coefficients for this solve (into hs->cheb):
@@ -1378,6 +1412,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
 
     int status = CR_OK;   // decided on the host; device statuses are folded in below
     int outer = 0;
+    std::string why;      // which exit of a refinement loop ended an unsuccessful solve
     if (o->prec == CR_PREC_FP64) {
         k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, nullptr, h->minv64, c.sc,
                                                     h->red, 1, o->tol, 0.0);
@@ -1429,12 +1464,13 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e1) cudaEventRecord(e1, c.st);
                 c.launches += deg - 1;
             };
-            k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
-            ++c.launches;
-            cheb_steps(nullptr, nullptr);
-            k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 1);
-            ++c.launches;
-            CR_CUDA(cudaGetLastError());
+            auto start = [&]() {
+                k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
+                ++c.launches;
+                cheb_steps(nullptr, nullptr);
+                k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 1);
+                ++c.launches;
+            };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 k_pcg_spmv<D, double, double><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->p64, h->q64,
                                                                           c.sc, h->red);
@@ -1444,19 +1480,24 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 0);
                 c.launches += 3;
             };
-            CR_TRY(pcg_loop(c, iter, chunk, graph, 6, deg));
+            CR_TRY(restarted_pcg<D>(c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 6, deg); }, b, max_outer,
+                                 o->tol, outer));
         } else if (o->method == CR_METHOD_PCG) {
-            k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
-            ++c.launches;
+            auto start = [&]() {
+                k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
+                ++c.launches;
+            };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, e0, e1);
             };
-            CR_TRY(pcg_loop(c, iter, chunk, graph, 0));
+            CR_TRY(restarted_pcg<D>(c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 0); }, b, max_outer,
+                                 o->tol, outer));
         } else {
             CR_TRY((gmres_loop<D, double, double>(c, h->val64, h->minv64, b, h->x64, h->r64, h->V64, h->Z64)));
         }
+        const int restart_status = c.hs->status;   // restarted_pcg may have set it on the host
         CR_TRY(read_scal(c));
-        status = c.hs->status;
+        status = restart_status != CR_OK ? restart_status : c.hs->status;
     } else if (o->prec == CR_PREC_FF || o->prec == CR_PREC_FF_BF16) {
         // Float-float PCG with reliable updates (FP32 pipes only inside the
         // iteration).  Each time the iterated residual has fallen by `delta`,
@@ -1528,11 +1569,13 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         if ((bf && !h->val16) || (!bf && !h->val32))
             return fail(CR_ERR_ARG, "cr_solve: the values for this precision were not kept by cr_hybridise");
         const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+        const bool trace = std::getenv("CRHYB_TRACE") != nullptr;
         auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
             if (bf) pcg_iteration<D, __nv_bfloat16, float>(c, h->val16, h->minv32, h->x32, h->r32, h->p32, h->q32, e0, e1);
             else pcg_iteration<D, float, float>(c, h->val32, h->minv32, h->x32, h->r32, h->p32, h->q32, e0, e1);
         };
         double last = -1.0;
+        const char* exit_reason = "converged";
         for (;;) {
             k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x0, h->r64, h->r32, h->minv64,
                                                         c.sc, h->red, 0, o->tol, 0.0);
@@ -1541,10 +1584,21 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             CR_CUDA(cudaGetLastError());
             CR_TRY(read_scal(c));
             const double rel2 = c.hs->obb > 0 ? c.hs->orr / c.hs->obb : 0.0;
-            if (!std::isfinite(rel2)) { status = CR_ERR_BREAKDOWN; break; }
+            if (trace)
+                std::fprintf(stderr, "[crhyb] fp32 refinement step %d: FP64 relres %.3e, inner iterations so far %d\n",
+                             outer, std::sqrt(rel2), c.hs->it);
+            if (!std::isfinite(rel2)) { status = CR_ERR_BREAKDOWN; exit_reason = "non-finite FP64 residual"; break; }
             if (rel2 <= o->tol * o->tol) break;
-            if (outer >= max_outer || c.hs->it >= gmax) { status = CR_ERR_NOT_CONVERGED; break; }
-            if (last >= 0.0 && rel2 > 100.0 * last) { status = CR_ERR_BREAKDOWN; break; }   // diverging
+            if (outer >= max_outer || c.hs->it >= gmax) {
+                status = CR_ERR_NOT_CONVERGED;
+                exit_reason = outer >= max_outer ? "refinement step limit" : "inner iteration limit";
+                break;
+            }
+            if (last >= 0.0 && rel2 > 100.0 * last) {   // diverging
+                status = CR_ERR_BREAKDOWN;
+                exit_reason = "divergence guard: the FP64 residual grew more than 100-fold in one step";
+                break;
+            }
             last = rel2;
             const int it_start = c.hs->it;
             k_inner_start<float><<<gn, kBlock, 0, c.st>>>(c.n, h->x32, h->r32, h->p32, h->minv32, c.sc, h->red, itol);
@@ -1552,12 +1606,22 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             CR_CUDA(cudaGetLastError());
             CR_TRY(pcg_loop(c, iter, chunk, graph, bf ? 2 : 1));
             CR_TRY(read_scal(c));
-            if (c.hs->status == CR_ERR_BREAKDOWN && c.hs->it == it_start) { status = CR_ERR_BREAKDOWN; break; }
+            if (trace)
+                std::fprintf(stderr, "[crhyb]   inner FP32 PCG: %d iterations, inner relres %.3e, status %d\n",
+                             c.hs->it - it_start, c.hs->bb > 0 ? std::sqrt(c.hs->rr / c.hs->bb) : 0.0,
+                             c.hs->status);
+            if (c.hs->status == CR_ERR_BREAKDOWN && c.hs->it == it_start) {
+                status = CR_ERR_BREAKDOWN;
+                exit_reason = "inner FP32 PCG broke down in its first iteration (p.Gp <= 0 or NaN)";
+                break;
+            }
             k_add32<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->x32);
             ++c.launches;
             CR_CUDA(cudaGetLastError());
             ++outer;
         }
+        if (trace) std::fprintf(stderr, "[crhyb] fp32 refinement exit: %s\n", exit_reason);
+        if (status != CR_OK) why = exit_reason;
     } else {
         // GMRES in FP32 (or BF16 values) inside FP64 iterative refinement
         const bool bf = o->prec == CR_PREC_MIXED_BF16;
@@ -1602,11 +1666,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     CR_CUDA(cudaGetLastError());
     CR_TRY(read_scal(c));
     const double relres = c.hs->obb > 0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
-    if (status == CR_OK && !(relres <= o->tol)) {
-        // the recursive residual can sit slightly below the true one
-        if (iters >= gmax) status = CR_ERR_NOT_CONVERGED;
-        else if (!(relres <= 10.0 * o->tol)) status = CR_ERR_NOT_CONVERGED;
-    }
+    // CR_OK means the FP64 true residual of the returned W meets the tolerance
+    if (status == CR_OK && !(relres <= o->tol)) status = CR_ERR_NOT_CONVERGED;
     if (st) {
         st->iterations = iters;
         st->outer = outer;
@@ -1616,10 +1677,12 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         st->spmv_ms = h->prof_ms;
         st->kernel_launches = c.launches;
     }
-    if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve: iteration limit reached before the tolerance");
+    const std::string detail = why.empty() ? std::string() : " [" + why + "]";
+    if (status == CR_ERR_NOT_CONVERGED)
+        return fail(status, "cr_solve: iteration limit reached before the tolerance" + detail);
     if (status == CR_ERR_BREAKDOWN)
         return fail(status, "cr_solve: Krylov breakdown or divergence (p.Gp <= 0, NaN, zero Arnoldi vector, "
-                            "or the low-precision values made the iteration diverge)");
+                            "or the low-precision values made the iteration diverge)" + detail);
     return status;
 }
 

@@ -3,7 +3,10 @@
 The headline (first) solver is the fastest measured one of each workload:
 the Chebyshev-preconditioned FP64 PCG in 2D, float-float Jacobi-PCG on the
 3D workload, and the Jacobi-preconditioned solvers of the batch and the
-Newton step, which do not take the Chebyshev preconditioner.
+Newton step, which do not take the Chebyshev preconditioner.  Also the
+host-side rules of a bench line: the default workload, the rejection of a step
+that missed the tolerance, and the DRAM traffic reported only for the kernel
+build it was captured on.
 """
 
 import os
@@ -39,9 +42,42 @@ def test_explicit_list_is_kept_except_where_unsupported(monkeypatch):
 
 
 def test_defaults_meet_the_timing_rules(monkeypatch):
+    """The metric (mixed precision against FP64 at relative residual 1e-10) is quoted on the
+    3D 64^3 workload, the largest one-GPU configuration: it is the default, with FP64
+    Jacobi-PCG among the timed solvers and the 2D 512^2 workload timed after it."""
     args = parse(monkeypatch)
     assert args.gpus == 1 and args.warmup >= 3 and args.steps >= 1
-    assert args.workload == "cfg2" and args.precs.split(",")[0] == "fp64_cheb"
+    assert args.workload == "cfg3" and args.precs.split(",")[0] == "ff"
+    assert "fp64" in args.precs.split(",") and args.tol == 1e-10
+    assert args.also == ["cfg2"] and args.mixed_attempt == 1
     o = bench.PRECS["fp64_cheb"][0]
     assert o["precond"] == "chebyshev" and o["prec"] == "fp64" and 2 <= o["poly_degree"] <= 16
     assert set(bench.CHEB_RATIO) == {2, 3} and all(r > 1 for r in bench.CHEB_RATIO.values())
+
+
+def test_also_rejects_workloads_it_cannot_time(monkeypatch):
+    assert parse(monkeypatch, "--workload", "cfg2").also == []
+    assert parse(monkeypatch, "--also", "none").also == []
+    with pytest.raises(SystemExit):
+        parse(monkeypatch, "--also", "cfg4")
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_build(monkeypatch):
+    sha = bench.sources_sha("persist")
+    assert len(sha) == 64 and sha == bench.sources_sha("persist")
+    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff"): {"per": "iteration", "bytes": 123.0,
+                                                            "sources": "persist", "sha256": sha}})
+    assert bench.measured_traffic("cfgX", "ff") == (123.0, "iteration")
+    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff"): {"per": "iteration", "bytes": 123.0,
+                                                            "sources": "persist", "sha256": "0" * 64}})
+    tb, why = bench.measured_traffic("cfgX", "ff")
+    assert tb is None and "changed" in why
+    assert bench.measured_traffic("cfgY", "ff")[0] is None
+
+
+def test_a_step_above_the_tolerance_is_rejected():
+    bench.check_step({"status": 0, "relres": 9.9e-11}, 1e-10, "ok")
+    with pytest.raises(RuntimeError):
+        bench.check_step({"status": 0, "relres": 1.2e-10}, 1e-10, "drifted")
+    with pytest.raises(RuntimeError):
+        bench.check_step({"status": -4, "relres": 5e-11}, 1e-10, "limit")

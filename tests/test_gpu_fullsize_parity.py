@@ -1,0 +1,166 @@
+"""Element-wise U/P parity on meshes large enough to take the full-size code paths.
+
+The smaller parity meshes (test_gpu_parity, test_gpu_chebyshev, test_gpu_batch)
+fit in one pass of every kernel.  These meshes do not:
+  * 2D 384 x 384 perturbed squares (cfg2 family): 441,600 face rows, more than
+    the 311,296 rows (8 blocks of 256 threads on each of 152 SMs) at which the
+    grid-stride loops of the three-kernel, Chebyshev and GMRES kernels start a
+    second pass, and 1,725 tiles, more than the persistent kernel's resident
+    blocks, so each block sweeps several tiles per phase;
+  * 3D 32^3 Kuhn cubes (cfg3 family): 387,072 face rows, 1,512 tiles;
+  * the batched workload itself (64 meshes, n from 9 to 234, 4 right-hand sides
+    each, float-float, autotuned), whose largest problem runs alone on
+    rebalanced tiles at the end of the solve;
+  * a transient Newton step on 384 x 384 squares (flexible GMRES with inner
+    float-float PCG).
+The GPU solves to a relative residual of 1e-13 and recovers U and P (P
+normalised to zero mean, Section 2 item 5); they must match the oracle's
+within 1e-9 relative L2 (FP64, float-float, Chebyshev) or 1e-8 (float-float
+with BF16 low parts), the tolerances of the parity tests.  The oracle's
+truths (fullsize_truth.py) are computed in spawned worker processes while the
+GPU solves run.
+"""
+
+import multiprocessing
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+import pytest
+
+import fullsize_truth as truth
+import synth
+from paper_2101_03777_gb300 import crhyb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N2D, N3D, NNEWTON = 384, 32, 384
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _largest_batch_problem():
+    return int(np.argmax(synth.batch_sizes(64, 8, 256, 2)))
+
+
+@pytest.fixture(scope="module")
+def truths():
+    """Futures of the oracle truths, started before the first GPU call of this module."""
+    ex = ProcessPoolExecutor(max_workers=4, mp_context=multiprocessing.get_context("spawn"))
+    k = _largest_batch_problem()
+    fut = {
+        "3d": ex.submit(truth.stokes_3d, N3D, 1e-12),
+        "2d": ex.submit(truth.stokes_2d, N2D),
+        "newton": ex.submit(truth.newton_2d, NNEWTON),
+        "batch": ex.submit(truth.batch_problem, k),
+        "batch_small": ex.submit(truth.batch_problem, int(np.argmin(synth.batch_sizes(64, 8, 256, 2)))),
+    }
+    yield fut
+    ex.shutdown(wait=True, cancel_futures=True)
+
+
+_GPU = {}
+
+
+def gpu_problem(name):
+    """Mesh and hybridised system (all value precisions kept) of a 2D or 3D case, cached."""
+    if name not in _GPU:
+        _GPU.clear()
+        p = synth.config_problem("cfg2" if name == "2d" else "cfg3", n=N2D if name == "2d" else N3D)
+        mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
+        fb = torch.from_numpy(p["fbar"]).cuda()
+        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
+                                 keep_ff=True, keep_ff_bf16=True)
+        _GPU[name] = (mesh, hyb)
+    return _GPU[name]
+
+
+def solve_recover(hyb, rhs=0, solver=None, **opts):
+    n, ne = hyb.n, hyb.mesh.ne
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = solver(W) if solver else crhyb.cr_solve(hyb, W, rhs=rhs, **opts)
+    U = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P = torch.zeros(ne, dtype=torch.float64, device="cuda")
+    crhyb.cr_recover_up(hyb, W, U, P, rhs=rhs, normalise_p=True)
+    return st, U.cpu().numpy(), P.cpu().numpy()
+
+
+SOLVERS = {
+    "fp64-persistent": (dict(method="pcg", prec="fp64", persistent=True), 1e-9),
+    "ff-persistent": (dict(method="pcg", prec="ff", persistent=True), 1e-9),
+    "ff_bf16-persistent": (dict(method="pcg", prec="ff_bf16", persistent=True), 1e-8),
+    "fp64-three-kernel-graph": (dict(method="pcg", prec="fp64", use_graph=True), 1e-9),
+    "ff-three-kernel": (dict(method="pcg", prec="ff"), 1e-9),
+    "fp64-chebyshev": (dict(method="pcg", prec="fp64", precond="chebyshev", poly_degree=4, use_graph=True), 1e-9),
+}
+CASES_2D = list(SOLVERS)
+CASES_3D = ["fp64-persistent", "ff-persistent", "ff-three-kernel", "fp64-chebyshev"]
+
+
+@pytest.mark.parametrize("solver", CASES_2D)
+def test_2d_384_matches_oracle(truths, solver):
+    mesh, hyb = gpu_problem("2d")
+    assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
+    opts, tol = SOLVERS[solver]
+    opts = dict(opts, **({"poly_ratio": 1000.0} if "chebyshev" in solver else {}))
+    st, U, P = solve_recover(hyb, tol=1e-13, max_iter=400000, **opts)
+    assert st["status"] == 0 and st["relres"] <= 1e-13
+    Uo, Po = truths["2d"].result()[0]
+    assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))
+
+
+def test_newton_384_matches_oracle(truths):
+    coords, elems, fbar, w = truth.newton_2d_inputs(NNEWTON)
+    mesh = crhyb.cr_mesh_load(coords, elems)
+    assert mesh.nf > 8 * 152 * 256
+    fb = torch.from_numpy(fbar).cuda()
+    hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb, conv="newton",
+                                                       w=torch.from_numpy(w).cuda()), keep_fp32=False)
+    pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb), keep_fp32=False, keep_ff=True)
+    st, U, P = solve_recover(hyb, solver=lambda W: crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-13,
+                                                                                 prec="ff", max_iter=2000))
+    assert st["status"] == 0 and st["relres"] <= 1e-13
+    Uo, Po = truths["newton"].result()
+    assert rel(U, Uo) <= 1e-9 and rel(P, Po) <= 1e-9, (rel(U, Uo), rel(P, Po))
+
+
+def test_full_batch_largest_and_smallest_problems_match_oracle(truths):
+    """The batched workload as the bench runs it (float-float, autotuned), every pair to
+    1e-13; the largest problem (n = 234) and the smallest (n = 9) against the oracle."""
+    probs = synth.batch_problems(count=64, nrhs=4, lo=8, hi=256, seed=2)
+    hybs = []
+    for q in probs:
+        mesh = crhyb.cr_mesh_load(q["coords"], q["elems"])
+        fb = torch.from_numpy(q["fbar"]).cuda()
+        hybs.append(crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, q["nu"], q["mu"], fb), keep_fp32=False,
+                                       keep_ff=True))
+    batch = crhyb.cr_batch_create(hybs, prec="ff", autotune=True)
+    Ws = [torch.zeros(4 * h.n, dtype=torch.float64, device="cuda") for h in hybs]
+    stats = crhyb.cr_solve_batched(batch, Ws, tol=1e-13, max_iter=400000)
+    assert all(s["status"] == 0 and s["relres"] <= 1e-13 for s in stats)
+    sizes = [q["n"] for q in probs]
+    for key, k in (("batch", _largest_batch_problem()), ("batch_small", int(np.argmin(sizes)))):
+        h = hybs[k]
+        ref = truths[key].result()
+        for r in range(4):
+            Wr = Ws[k][r * h.n:(r + 1) * h.n].contiguous()
+            U = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+            P = torch.zeros(h.mesh.ne, dtype=torch.float64, device="cuda")
+            crhyb.cr_recover_up(h, Wr, U, P, rhs=r, normalise_p=True)
+            Uo, Po = ref[r]
+            assert rel(U.cpu().numpy(), Uo) <= 1e-9 and rel(P.cpu().numpy(), Po) <= 1e-9, (key, r)
+
+
+@pytest.mark.parametrize("solver", CASES_3D)
+def test_3d_32cubed_matches_oracle(truths, solver):
+    mesh, hyb = gpu_problem("3d")
+    assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
+    opts, tol = SOLVERS[solver]
+    opts = dict(opts, **({"poly_ratio": 100.0} if "chebyshev" in solver else {}))
+    st, U, P = solve_recover(hyb, tol=1e-13, max_iter=400000, **opts)
+    assert st["status"] == 0 and st["relres"] <= 1e-13
+    Uo, Po, _ = truths["3d"].result()
+    assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))
