@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--also", default=None,
                     help="comma-separated further workloads timed after the headline with their own default "
                          "solvers (default: cfg2 after cfg3; 'none' for none)")
+    ap.add_argument("--steady", type=int, default=0,
+                    help="cfg5: the steady (mu = 0) Newton step, solved by flexible GMRES on the coupled system "
+                         "preconditioned by transient Stokes solves (mu_pre = --mu-pre)")
+    ap.add_argument("--mu-pre", type=float, default=1.0, help="steady solves: mu of the preconditioning step")
     ap.add_argument("--mixed-attempt", type=int, default=1,
                     help="attempt FP32 PCG inside FP64 refinement once (bounded) and report its exit")
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -114,14 +118,15 @@ def supported_precs(workload, precs):
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def load_problem(name, n=None):
+def load_problem(name, n=None, steady=False):
     """Mesh, coefficients, sources and (for Navier-Stokes) the linearisation field;
-    n (profiling runs only) replaces the workload's mesh size."""
+    n (profiling runs only) replaces the workload's mesh size.  cfg5 is a transient
+    Newton step (dt = 1e-3), or with `steady` the steady (mu = 0) one."""
     import numpy as np
     import synth
     p = synth.config_problem(name, n=n or None)
     if name == "cfg5":
-        p["mu"] = 1000.0   # a transient Newton step (dt = 1e-3)
+        p["mu"] = 0.0 if steady else 1000.0
         p["conv"] = "newton"
     return p, np
 
@@ -372,7 +377,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
     build.build_library()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    p, _ = load_problem(workload, args.mesh_n)
+    p, _ = load_problem(workload, args.mesh_n, steady=bool(args.steady) and workload == "cfg5")
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -380,7 +385,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
 
     w_dev = None
     tm0 = time.perf_counter()
-    mesh = crhyb.cr_mesh_load(p["coords"], p["elems"], need_mis=(p["mu"] == 0.0))
+    mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
     mesh_load_s = time.perf_counter() - tm0
     if p["conv"] != "none":
         import synth
@@ -402,6 +407,22 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
     def step(prec, fb, Wt, Ut, Pt, profile=False, persistent=None, extra=None):
         persistent = args.persistent if persistent is None else persistent
         system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=w_dev)
+        if newton and p["mu"] == 0.0:
+            # the steady Newton step: flexible GMRES on its coupled system, each step
+            # preconditioned by a transient Stokes solve (SPD G, persistent PCG)
+            pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], args.mu_pre, fb), keep_fp32=False,
+                                     keep_ff=(prec == "ff"), keep_ff_bf16=(prec == "ff_bf16"))
+            o = dict(tol=args.tol, prec=prec, profile=profile, check_every=args.check_every, restart=60)
+            if args.max_iter:
+                o["max_iter"] = args.max_iter
+            # the steady solve writes device arrays: the end-to-end run copies them to its host buffers
+            Ud = Ut if Ut.is_cuda else torch.zeros(Ut.shape, dtype=torch.float64, device="cuda")
+            Pd = Pt if Pt.is_cuda else torch.zeros(Pt.shape, dtype=torch.float64, device="cuda")
+            st = crhyb.cr_solve_steady(system, pre, Ud, Pd, raise_on_error=not args.max_iter, **o)
+            if not Ut.is_cuda:
+                Ut.copy_(Ud)
+                Pt.copy_(Pd)
+            return st
         if newton:
             # the nonsymmetric Newton system (FP64 values for the outer GMRES) and the transient
             # Stokes system on the same mesh, whose PCG solves precondition it
@@ -548,8 +569,13 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                               "direction phases)", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": ach / hbm_peak, "traffic": None, "bytes_per_iteration": it_bytes,
                     "iterations_timed": piters, "kernel_ms": kms, "peak_note": peak_note}
-            solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
-                      f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
+            if p["mu"] == 0.0:
+                solver = ("steady Newton step: flexible GMRES(60) in FP64 on the coupled system (Eq. 10, mu = 0), "
+                          f"each step preconditioned by one transient Stokes step (mu = {args.mu_pre:g}) of the hybrid "
+                          f"method, inner {solver} to max(tol/100, 1e-13)")
+            else:
+                solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
+                          f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
         elif prec == "fp64_cheb":
             roof = dict(spmv)
         elif args.persistent:
@@ -598,7 +624,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         "metric": METRIC, "value": tts, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tts * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[head], "data": "synthetic (seeded generators in synth/)",
-        "config": {"workload": f"{workload}: {WORKLOADS[workload]}", "nf_int": nf, "unknowns": n,
+        "config": {"workload": f"{workload}: {WORKLOADS[workload]}" + (" (steady, mu = 0)" if p["mu"] == 0.0 else ""),
+                   "nf_int": nf, "unknowns": n,
                    "elements": ne, "solver": hs["solver"], "tol": args.tol, "iterations": hs["iterations"],
                    "outer": hs["outer"], "relres": hs["relres"], "mesh_load_s": mesh_load_s,
                    "l2": "512 MB flush between steps",

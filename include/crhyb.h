@@ -237,7 +237,8 @@ void cr_destroy_system(cr_system* s);
  * 4, 5, 7).  Atomic free: every off-diagonal block of G belongs to one simplex;
  * the two contributions to a diagonal block and to S are summed per face.
  * Errors: CR_ERR_SINGULAR (an Â_K or B_K with a vanishing pivot; the
- * handle is not created), CR_ERR_OOM, CR_ERR_CUDA. */
+ * handle is not created), CR_ERR_ARG (mu = 0 on a mesh loaded without
+ * need_mis), CR_ERR_OOM, CR_ERR_CUDA. */
 int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out);
 
 /* Export G as block ELL: cols int32 [nslot][nf_int] (slot 0 is the diagonal),
@@ -282,6 +283,72 @@ int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_sol
  * Returns CR_OK, CR_ERR_NOT_CONVERGED, CR_ERR_BREAKDOWN, CR_ERR_ARG, CR_ERR_CUDA. */
 int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* opts, double* W,
                             cr_solve_stats* st);
+
+/* The steady problem (mu = 0) solved without the indefinite G of its E_K
+ * elimination: flexible GMRES(m) (Saad, Iterative Methods for Sparse Linear
+ * Systems, Algorithm 9.6) on the steady coupled system of Eq. 10,
+ *   K_s [U; P] = [R; 0],  K_s = [A_0 D^t; D 0],  P_{K_0} = 0,
+ * right-preconditioned by the transient Stokes step of `pre`: each
+ * preconditioner application solves K_mu [z_u; z_p] = [v; g] by the hybrid
+ * method (Section 3.2: the SPD G_mu of `pre`, persistent Jacobi-PCG, then the
+ * element-wise recovery), v entering as the previous level v/(mu m) of an
+ * implicit Euler step with no source (m_sigma = sum_{K ni sigma} |K|/(d+1),
+ * the lumped mass of S_K) and g as a divergence D_K^t U_K = g_K that the
+ * element-wise elimination carries (P_K = (D_K^t Â^{-1} y - g_K)/B_K).  On divergence-free fields K_s K_mu^{-1} has the
+ * eigenvalues lambda/(lambda + mu), so the number of steps does not grow with
+ * the mesh.  The minimised residual is that of K_s.
+ *   sys   assembled with mu = 0 (conv NONE, NEWTON or OSEEN with its field w);
+ *         its mesh need not hold M_1; the coupled operator is built on the
+ *         first call and kept with sys
+ *   pre   hybridised on the same mesh handle, conv = NONE, mu > 0 (e.g. mu = 30
+ *         for nu = 1, mu = 1 for nu = 0.01); its own S and W are untouched
+ *   opts  method GMRES; prec: precision of the inner PCG (FP64, FF, FF_BF16;
+ *         FF needs keep_lo_fp32 on pre); restart m (default 30); tol on the
+ *         FP64 residual ||[R;0] - K_s [U;P]|| / ||R||; inner_tol: relative
+ *         residual of each inner PCG (default 1e-4; an inner solve that
+ *         stagnates stops at four times the iterations of the first one);
+ *         max_iter caps the GMRES steps (default 1000); use_x0: U, P hold the
+ *         start; check_every x 64 inner iterations per persistent launch
+ *   U     device float64 [nf_int][dim]; P device float64 [ne] (P_{K_0} = 0, not
+ *         normalised)
+ *   st    iterations = inner PCG iterations in total, outer = GMRES steps,
+ *         relres = the FP64 coupled residual of the returned U, P
+ * Returns CR_OK, CR_ERR_NOT_CONVERGED, CR_ERR_BREAKDOWN, CR_ERR_ARG, CR_ERR_CUDA. */
+int cr_solve_steady(cr_system* sys, cr_hybrid* pre, int rhs, const cr_solve_opts* opts, double* U, double* P,
+                    cr_solve_stats* st);
+
+/* Newton's method for the steady Navier-Stokes problem (Section 3.1: the
+ * scheme with the convection term b_h of Eq. 9, mu = 0, homogeneous Dirichlet
+ * data), each step a steady linear solve by cr_solve_steady:
+ *   U_0 = U on entry (zeros: the first step is the steady Stokes problem);
+ *   step k: the coupled system linearised about w = U_k (conv = NEWTON:
+ *   Jacobian of b_h at w, right-hand side R + c_K(w)) solved from [U_k; P_k]
+ *   to lin->tol, giving U_{k+1}, P_{k+1};
+ *   stop when ||U_{k+1} - U_k||_2 <= newton_tol ||U_{k+1}||_2.
+ *   m           2D mesh; nu = 1/Re
+ *   fbar        float64 [ne][2] element means of the source, host or device
+ *   pre         transient Stokes hybrid of the same mesh (as for cr_solve_steady)
+ *   lin         options of every linear solve (as for cr_solve_steady; use_x0 is implied)
+ *   U, P        device float64 [nf_int][2] (in: U_0; out: the last iterate) and [ne]
+ *               (in: P_0; out: P with P_{K_0} = 0)
+ *   st          host, may be NULL: Newton steps, GMRES steps and inner PCG
+ *               iterations summed, the last increment, the nonlinear relative
+ *               residual ||[R + c(U); 0] - K(U)[U; P]|| / ||[R + c(U); 0]|| at
+ *               the returned U, P and at U_0
+ * Returns CR_OK, CR_ERR_NOT_CONVERGED (max_newton steps without meeting
+ * newton_tol), or the error of a linear solve.  */
+typedef struct cr_newton_stats {
+    int32_t iterations;        /* Newton steps taken */
+    int32_t linear_steps;      /* flexible GMRES steps over all Newton steps */
+    int64_t inner_iterations;  /* inner PCG iterations over all Newton steps */
+    double increment;          /* ||U_{k+1} - U_k|| / ||U_{k+1}|| of the last step */
+    double residual;           /* nonlinear relative residual at the returned U, P */
+    double first_residual;     /* the same at U_0, P_0 */
+    int32_t status;
+} cr_newton_stats;
+
+int cr_solve_newton(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin,
+                    double newton_tol, int max_newton, double* U, double* P, cr_newton_stats* st);
 
 /* y = G x in FP64 (x, y float64 [nf_int][dim], device pointers). */
 int cr_apply_G(cr_hybrid* h, const double* x, double* y);

@@ -11,15 +11,18 @@ right-preconditioned by the transient coupled operator
     K_mu = [A_0 + mu M, D^t; D 0]
 (the same problem with the lumped mass M of S_K added, Section 3.1), which
 the hybrid method solves exactly with an SPD G when the convection term is
-absent (Section 3.2, item 6).  A residual block [v; 0] enters K_mu^{-1} as the
-right-hand side of an implicit Euler step from the previous level
+absent (Section 3.2, item 6).  A residual [v; g] enters K_mu^{-1} as follows:
+v is the right-hand side of an implicit Euler step from the previous level
 u_prev = v / (mu m) with zero source, m_sigma = sum_{K ni sigma} |K|/(d+1)
-(elements.local_R_previous assembles mu m u_prev = v).  On divergence-free
-velocities K_s K_mu^{-1} has the eigenvalues lambda/(lambda + mu), lambda
-those of the steady operator, so the number of outer steps does not depend on
-the mesh.  The preconditioner ignores the pressure block of its argument
-(zero for exact inner solves); the flexible form keeps the minimised
-residual that of K_s whatever the inner solves return.
+(elements.local_R_previous assembles mu m u_prev = v); g is a non-zero
+divergence D_K^t U_K = g_K per simplex, which the element-wise elimination of
+Section 3.2 (items 2-4) carries through: P_K = (D_K^t Â^{-1} y - g_K)/B_K, so
+Û_K = M_K y + Â^{-1} D_K g_K / B_K and S gains sum_K H_K C_K Â^{-1} D_K g_K / B_K
+(g_{K_0} plays no part: P_{K_0} = 0).  On divergence-free velocities K_s
+K_mu^{-1} has the eigenvalues lambda/(lambda + mu), lambda those of the steady
+operator, so the number of outer steps does not depend on the mesh.  The
+flexible form keeps the minimised residual that of K_s whatever the inner
+solves return; with the divergence block carried, inner solves to 1e-4 do.
 """
 
 import numpy as np
@@ -62,22 +65,36 @@ class TransientPreconditioner:
         self.solve = solve
         self.applications = 0
 
-    def __call__(self, v):
-        """(z_u [N], z_p [ne] with z_p[K_0] = 0) for the velocity residual v [N]."""
+    def __call__(self, v, g=None):
+        """(z_u [N], z_p [ne] with z_p[K_0] = 0) solving K_mu [z_u; z_p] = [v; g] for
+        the velocity residual v [N] and the divergence residual g [ne] (None: 0;
+        the entry of K_0 is not used)."""
         u_prev = v / (self.mu * self.m)
         R_K = elements.local_R_previous(self.topo, self.geom, self.mu, u_prev)
         R_K = R_K * elements.interior_mask(self.topo)
-        h = dict(self.h)
-        h["R_K"] = R_K
-        # S = sum_K H_K C_K M_K R_K with the G_K = C_K M_K C_K already formed (C_K^2 = 1)
-        S = np.zeros(self.m.shape[0])
-        dofs, Cv = h["dofs"], h["Cv"]
+        h = self.h
+        dofs, Cv, Ainv, D_K, B = h["dofs"], h["Cv"], h["Ainv"], h["D_K"], h["B"]
+        k0 = h["k0"]
+        gK = np.zeros(B.shape[0]) if g is None else np.asarray(g, dtype=np.float64).copy()
+        gK[k0] = 0.0
+        invB = 1.0 / np.where(B == 0.0, 1.0, B)
+        invB[k0] = 0.0
+        u = np.einsum("kab,kb->ka", Ainv, D_K)                       # Â^{-1} D_K
+        # S = sum_K H_K C_K (M_K R_K + Â^{-1} D_K g_K / B_K); M_K from G_K = C_K M_K C_K (C_K^2 = 1)
         M = h["GK"] * Cv[:, :, None] * Cv[:, None, :]
-        SK = Cv * np.einsum("kab,kb->ka", M, R_K)
+        SK = Cv * (np.einsum("kab,kb->ka", M, R_K) + u * (gK * invB)[:, None])
+        S = np.zeros(self.m.shape[0])
         kp = dofs >= 0
         np.add.at(S, dofs[kp], SK[kp])
         W = self.solve(self.h["G"], S)
-        U, P, _ = hybrid.recover(h, self.topo, W, R_K)
+        # recovery (Section 3.2, items 2 and 4) with the divergence g_K
+        Wl = np.where(kp, W[np.maximum(dofs, 0)], 0.0)
+        y = R_K - Cv * Wl
+        Ay = np.einsum("kab,kb->ka", Ainv, y)
+        P = (np.einsum("ka,ka->k", D_K, Ay) - gK) * invB
+        Uh = Ay - u * P[:, None]
+        fe, fl = self.topo["face_elems"], self.topo["face_local"]
+        U = Uh.reshape(-1, self.d + 1, self.d)[fe[:, 0], fl[:, 0]].ravel()
         self.applications += 1
         return U, P
 
@@ -160,7 +177,7 @@ def solve_steady(coords, elems, nu, fbar, conv="none", w=None, mu_pre=100.0, pre
         return np.concatenate([A @ u + D.T @ p, D @ u])
 
     def precond(v):
-        zu, zp = pre(v[:N])
+        zu, zp = pre(v[:N], np.insert(v[N:], k0, 0.0))
         return np.concatenate([zu, zp[1:]])
 
     b = np.concatenate([R, np.zeros(ne - 1)])
@@ -168,3 +185,45 @@ def solve_steady(coords, elems, nu, fbar, conv="none", w=None, mu_pre=100.0, pre
     U, P = x[:N], np.insert(x[N:], k0, 0.0)
     return U, P, {"steps": steps, "hist": hist, "applications": pre.applications,
                   "relres": coupled.coupled_residual(A, D, R, U, P, k0)}
+
+
+def newton(coords, elems, nu, fbar, tol=5e-7, maxit=30):
+    """Newton's method for the steady Navier-Stokes problem (Section 3.1 with the
+    convection form b_h of Eq. 9, mu = 0): from U_0 = 0, U_{k+1} solves the
+    coupled system linearised about w = U_k (coupled.element_blocks with
+    conv = "newton": Jacobian of b_h at w, right-hand side R + c(w)) by the
+    direct solve; stop when ||U_{k+1} - U_k|| <= tol ||U_{k+1}||.
+    Returns (U, P with P_{K_0} = 0, increments per step)."""
+    d = coords.shape[1]
+    U = np.zeros(0)
+    hist = []
+    for _ in range(maxit):
+        w = U.reshape(-1, d) if U.size else None
+        if w is None:
+            ref = pipeline.direct(coords, elems, nu, 0.0, fbar)          # w = 0: the Stokes problem
+        else:
+            ref = pipeline.direct(coords, elems, nu, 0.0, fbar, "newton", w)
+        Un = ref["U"].ravel()
+        inc = np.linalg.norm(Un - (U if U.size else 0.0)) / np.linalg.norm(Un)
+        U, P = Un, ref["P"]
+        hist.append(inc)
+        if inc <= tol:
+            break
+    return U, P, hist
+
+
+def navier_stokes_residual(coords, elems, nu, fbar, U, P, k0=0):
+    """||S U + B(U) + D^t P - R|| / ||R|| and ||D U|| / ||R|| for the steady problem,
+    B(U) assembled from the element convection terms c_K(U) of Eq. 9."""
+    from . import convection
+    d = coords.shape[1]
+    topo, geom, A_K, D_K, R_K = pipeline.setup(coords, elems, nu, 0.0, fbar)
+    A, D, R = coupled.assemble(topo, A_K, D_K, R_K, k0)
+    c = convection.element_convection(convection.gather_local(U.reshape(-1, d), topo), geom["a"])
+    c = c.reshape(c.shape[0], -1) * elements.interior_mask(topo)
+    B = np.zeros_like(R)
+    dofs = elements.local_dofs(topo)
+    kp = dofs >= 0
+    np.add.at(B, dofs[kp], c[kp])
+    mom = A @ U + B + D.T @ np.delete(P, k0) - R
+    return float(np.linalg.norm(mom) / np.linalg.norm(R)), float(np.linalg.norm(D @ U) / np.linalg.norm(R))

@@ -72,6 +72,12 @@ class cr_solve_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class cr_newton_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("linear_steps", ctypes.c_int32),
+                ("inner_iterations", ctypes.c_int64), ("increment", ctypes.c_double),
+                ("residual", ctypes.c_double), ("first_residual", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
@@ -93,6 +99,10 @@ _SIGS = {
     "cr_solve_coupled": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, _vp,
                                 ctypes.POINTER(cr_solve_stats)]),
     "cr_destroy_coupled": (None, [_vp]),
+    "cr_solve_steady": (_i32, [_vp, _vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, _vp,
+                                ctypes.POINTER(cr_solve_stats)]),
+    "cr_solve_newton": (_i32, [_vp, ctypes.c_double, _vp, _vp, ctypes.POINTER(cr_solve_opts), ctypes.c_double,
+                                ctypes.c_int, _vp, _vp, ctypes.POINTER(cr_newton_stats)]),
     "cr_solve_preconditioned": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(cr_solve_opts), _vp,
                                        ctypes.POINTER(cr_solve_stats)]),
     "cr_apply_G": (_i32, [_vp, _vp, _vp]),
@@ -340,6 +350,54 @@ def cr_solve_preconditioned(hyb, pre, W, rhs=0, raise_on_error=True, **opts):
              "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
     if rc != CR_OK and raise_on_error:
         _check(rc)
+    return stats
+
+
+def cr_solve_steady(system, pre, U, P, rhs=0, raise_on_error=True, **opts):
+    """The steady problem (system assembled with mu = 0) by flexible GMRES on its
+    coupled system, preconditioned by transient Stokes solves with the SPD G of
+    `pre` (same mesh, mu > 0).  U float64 [nf*d], P float64 [ne] on the device
+    (P_{K_0} = 0).  opts as for cr_solve; method defaults to "gmres", prec (the
+    inner PCG's precision) to "ff".  Returns the statistics (iterations = inner
+    PCG iterations, outer = GMRES steps, relres = the coupled residual)."""
+    opts.setdefault("method", "gmres")
+    opts.setdefault("prec", "ff")
+    o = make_solve_opts(**opts)
+    st = cr_solve_stats()
+    n = system.mesh.nf * system.mesh.dim
+    rc = load_library().cr_solve_steady(system.handle, pre.handle, int(rhs), ctypes.byref(o),
+                                        _ptr(U, np.float64, n, "U"), _ptr(P, np.float64, system.mesh.ne, "P"),
+                                        ctypes.byref(st))
+    stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
+             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
+             "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
+    if rc != CR_OK:
+        stats["error"] = load_library().cr_last_error().decode()
+        if raise_on_error:
+            _check(rc)
+    return stats
+
+
+def cr_solve_newton(mesh, nu, fbar, pre, U, P, newton_tol=5e-7, max_newton=20, raise_on_error=True, **opts):
+    """Newton's method for the steady Navier-Stokes problem (2D), each step a
+    cr_solve_steady solve of the system linearised about the current U.  U and P
+    (device) hold the start on entry and the last iterate on exit; fbar
+    float64 [ne, 2] host or device.  opts: the linear solves' options (as for
+    cr_solve_steady).  Returns the Newton statistics."""
+    opts.setdefault("method", "gmres")
+    opts.setdefault("prec", "ff")
+    o = make_solve_opts(**opts)
+    st = cr_newton_stats()
+    rc = load_library().cr_solve_newton(mesh.handle, float(nu), _ptr(fbar, np.float64, mesh.ne * mesh.dim, "fbar"),
+                                        pre.handle, ctypes.byref(o), float(newton_tol), int(max_newton),
+                                        _ptr(U, np.float64, mesh.nf * mesh.dim, "U"), _ptr(P, np.float64, mesh.ne, "P"),
+                                        ctypes.byref(st))
+    stats = {k: getattr(st, k) for k, _ in cr_newton_stats._fields_}
+    stats["status_name"] = "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc))
+    if rc != CR_OK:
+        stats["error"] = load_library().cr_last_error().decode()
+        if raise_on_error:
+            _check(rc)
     return stats
 
 

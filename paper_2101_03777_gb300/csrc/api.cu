@@ -171,8 +171,6 @@ extern "C" int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double*
         return fail(CR_ERR_ARG, "cr_assemble_coupled: unknown convection option");
     if (p->conv != CR_CONV_NONE && (m->d != 2 || !w))
         return fail(CR_ERR_ARG, "cr_assemble_coupled: the convection term needs dim 2 and the field w");
-    if (p->mu == 0.0 && !m->has_mis)
-        return fail(CR_ERR_ARG, "cr_assemble_coupled: mu = 0 needs a mesh loaded with need_mis = 1");
     CR_TRY(check_call(m, "cr_assemble_coupled", {fbar, w, blocks_out}));
     cr_system* s = new cr_system();
     s->m = m;
@@ -240,6 +238,7 @@ extern "C" int cr_system_set_previous(cr_system* s, const double* u_prev) {
 
 extern "C" void cr_destroy_system(cr_system* s) {
     if (!s) return;
+    if (s->steady_op) cr_destroy_coupled(s->steady_op);
     s->arena.release();
     delete s;
 }
@@ -250,6 +249,8 @@ extern "C" int cr_hybridise(cr_system* s, const cr_hyb_opts* o, cr_hybrid** out)
     *out = nullptr;
     if (!s) return fail(CR_ERR_ARG, "cr_hybridise: NULL system");
     CR_TRY(check_call(s->m, "cr_hybridise", {}));
+    if (s->mu == 0.0 && !s->m->has_mis)
+        return fail(CR_ERR_ARG, "cr_hybridise: mu = 0 needs the set M_1 of a mesh loaded with need_mis = 1");
     cr_mesh* m = s->m;
     const int d = m->d;
     cr_hybrid* h = new cr_hybrid();
@@ -451,6 +452,64 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
     return rc;
 }
 
+extern "C" int cr_solve_steady(cr_system* sys, cr_hybrid* pre, int rhs, const cr_solve_opts* o, double* U, double* P,
+                               cr_solve_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    if (!sys || !pre || !o || !U || !P) return fail(CR_ERR_ARG, "cr_solve_steady: NULL argument");
+    CR_TRY(check_call(sys->m, "cr_solve_steady", {U, P}));
+    if (rhs < 0 || rhs >= sys->nrhs) return fail(CR_ERR_ARG, "cr_solve_steady: rhs out of range");
+    if (sys->mu != 0.0) return fail(CR_ERR_ARG, "cr_solve_steady: the system to solve is steady (mu = 0)");
+    if (pre->m != sys->m) return fail(CR_ERR_ARG, "cr_solve_steady: pre must be hybridised on the same mesh");
+    if (!(pre->s->mu > 0.0) || pre->s->conv != CR_CONV_NONE)
+        return fail(CR_ERR_ARG, "cr_solve_steady: pre needs a transient Stokes system (mu > 0, b_h = 0), whose G is SPD");
+    if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_steady: the outer method is (flexible) GMRES");
+    if (o->precond != CR_PRECOND_JACOBI)
+        return fail(CR_ERR_ARG, "cr_solve_steady: the inner PCG is Jacobi-preconditioned");
+    if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
+        return fail(CR_ERR_ARG, "cr_solve_steady: the inner PCG runs in FP64, FF or FF_BF16");
+    if ((o->prec == CR_PREC_FF && !pre->vff) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
+        return fail(CR_ERR_ARG, "cr_solve_steady: the float-float values of pre were not kept");
+    if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve_steady: tol must be > 0");
+    const int restart = o->restart > 0 ? o->restart : 30;
+    if (restart < 1 || restart > CR_MAX_RESTART)
+        return fail(CR_ERR_ARG, "cr_solve_steady: restart must be in [1, CR_MAX_RESTART]");
+    if (!is_device_pointer(U) || !is_device_pointer(P))
+        return fail(CR_ERR_ARG, "cr_solve_steady: U and P must be device pointers");
+    cr_mesh* m = sys->m;
+    StreamScope scope(m);
+    CR_TRY(ensure_workspace(pre, false, 0, o->prec));
+    if (!sys->steady_op) CR_TRY(coupled_build(sys, &sys->steady_op, false));
+    return solve_steady_impl(sys->steady_op, m, pre, rhs, o, U, P, st);
+}
+
+extern "C" int cr_solve_newton(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin,
+                               double newton_tol, int max_newton, double* U, double* P, cr_newton_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    if (!m || !fbar || !pre || !lin || !U || !P) return fail(CR_ERR_ARG, "cr_solve_newton: NULL argument");
+    CR_TRY(check_call(m, "cr_solve_newton", {fbar, U, P}));
+    if (m->d != 2) return fail(CR_ERR_ARG, "cr_solve_newton: the convection term is implemented in 2D");
+    if (!(nu > 0.0)) return fail(CR_ERR_ARG, "cr_solve_newton: nu must be > 0");
+    if (!(newton_tol > 0.0) || max_newton < 1)
+        return fail(CR_ERR_ARG, "cr_solve_newton: need newton_tol > 0 and max_newton >= 1");
+    if (pre->m != m) return fail(CR_ERR_ARG, "cr_solve_newton: pre must be hybridised on the same mesh");
+    if (!(pre->s->mu > 0.0) || pre->s->conv != CR_CONV_NONE)
+        return fail(CR_ERR_ARG, "cr_solve_newton: pre needs a transient Stokes system (mu > 0, b_h = 0)");
+    if (lin->method != CR_METHOD_GMRES || lin->precond != CR_PRECOND_JACOBI)
+        return fail(CR_ERR_ARG, "cr_solve_newton: the linear solves are cr_solve_steady's flexible GMRES");
+    if (lin->prec != CR_PREC_FP64 && lin->prec != CR_PREC_FF && lin->prec != CR_PREC_FF_BF16)
+        return fail(CR_ERR_ARG, "cr_solve_newton: the inner PCG runs in FP64, FF or FF_BF16");
+    if ((lin->prec == CR_PREC_FF && !pre->vff) || (lin->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
+        return fail(CR_ERR_ARG, "cr_solve_newton: the float-float values of pre were not kept");
+    const int restart = lin->restart > 0 ? lin->restart : 30;
+    if (!(lin->tol > 0.0) || restart < 1 || restart > CR_MAX_RESTART)
+        return fail(CR_ERR_ARG, "cr_solve_newton: bad tol or restart of the linear solves");
+    if (!is_device_pointer(U) || !is_device_pointer(P))
+        return fail(CR_ERR_ARG, "cr_solve_newton: U and P must be device pointers");
+    StreamScope scope(m);
+    CR_TRY(ensure_workspace(pre, false, 0, lin->prec));
+    return solve_newton_impl(m, nu, fbar, pre, lin, newton_tol, max_newton, U, P, st);
+}
+
 extern "C" int cr_recover_up(cr_hybrid* h, int rhs, const double* W, double* U, double* P, int normalise_p,
                              double* jump) {
     if (!h || !W || !U || !P) return fail(CR_ERR_ARG, "cr_recover_up: NULL argument");
@@ -493,6 +552,7 @@ extern "C" void cr_destroy_hybrid(cr_hybrid* h) {
     for (auto& g : h->graph_exec)
         if (g) cudaGraphExecDestroy(g);
     destroy_persistent_plans(h);
+    h->steady.release();
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->arena.release();
     if (h->V32) cudaFree(h->V32);

@@ -118,6 +118,27 @@ __device__ __forceinline__ double op_elem(const Op& o, int64_t K, const double* 
     return y * scale;
 }
 
+// y = K x, or y = b - K x when b is given (no reductions).  Blocks [0, nbf)
+// take face rows, the rest simplices.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_cp_apply(Op o, int nbf, const double* __restrict__ x,
+                                                     const double* __restrict__ b, double* __restrict__ y) {
+    const int64_t N = o.nf * D;
+    if (int(blockIdx.x) < nbf) {
+        const int64_t f = int64_t(blockIdx.x) * kBlock + threadIdx.x;
+        if (f >= o.nf) return;
+        double v[D];
+        op_face<D>(o, f, x, 1.0, v);
+#pragma unroll
+        for (int i = 0; i < D; ++i) y[f * D + i] = b ? b[f * D + i] - v[i] : v[i];
+    } else {
+        const int64_t K = int64_t(blockIdx.x - nbf) * kBlock + threadIdx.x;
+        if (K >= o.ne) return;
+        const double v = op_elem<D>(o, K, x, 1.0);
+        y[N + K] = b ? b[N + K] - v : v;
+    }
+}
+
 // Blocks [0, nbf) take face rows, the rest simplices.  mode 0: q = K (z/gamma),
 // delta = q.(z/gamma) (a MINRES step j, skipped past stop_it); mode 1: q = b - K x
 // with ||q||^2 and ||b||^2 (true residual; z = x, b given).
@@ -384,13 +405,12 @@ int solve_coupled_dim(cr_coupled* c, int rhs, const cr_solve_opts* o, double* U,
 
 using namespace crhyb;
 
-extern "C" int cr_coupled_create(cr_system* s, cr_coupled** out) {
-    if (!out) return fail(CR_ERR_ARG, "cr_coupled_create: out is NULL");
+namespace crhyb {
+
+// The coupled operator [A D^t; D 0] of system s (any convection option), its
+// right-hand sides and, when `minres`, the MINRES workspace.
+int coupled_build(cr_system* s, cr_coupled** out, bool minres) {
     *out = nullptr;
-    if (!s) return fail(CR_ERR_ARG, "cr_coupled_create: NULL system");
-    CR_TRY(check_call(s->m, "cr_coupled_create", {}));
-    if (s->conv != CR_CONV_NONE)
-        return fail(CR_ERR_ARG, "cr_coupled_create: MINRES needs the symmetric (Stokes) system, conv = NONE");
     cr_mesh* m = s->m;
     StreamScope scope(m);
     cr_coupled* c = new cr_coupled();
@@ -408,18 +428,24 @@ extern "C" int cr_coupled_create(cr_system* s, cr_coupled** out) {
     int rc;
     if ((rc = c->arena.alloc_n(&c->A, size_t(c->npl) * m->nfp)) || (rc = c->arena.alloc_n(&c->R, N * s->nrhs)) ||
         (rc = c->arena.alloc_n(&c->DK, ne * (d + 1) * d)) || (rc = c->arena.alloc_n(&c->minv, n)) ||
-        (rc = c->arena.alloc_n(&c->x, n)) || (rc = c->arena.alloc_n(&c->b, n)) || (rc = c->arena.alloc_n(&c->q, n)) ||
-        (rc = c->arena.alloc_n(&c->V, 3 * n)) || (rc = c->arena.alloc_n(&c->W, 3 * n)) ||
-        (rc = c->arena.alloc_n(&c->Z, 2 * n)) || (rc = c->arena.alloc(&c->scal, sizeof(MScal))) ||
-        (rc = c->arena.alloc_n(&c->red.partial, size_t(kRedSlots) * kMaxRedBlocks)) ||
-        (rc = c->arena.alloc_n(&c->red.count, 1)) ||
         (rc = tmp.alloc_n(&c->dpart, size_t(2) * d * d * m->nf)) ||
         (rc = tmp.alloc_n(&c->spart, size_t(s->nrhs) * 2 * d * m->nf)))
         return bail(rc);
+    if (minres &&
+        ((rc = c->arena.alloc_n(&c->x, n)) || (rc = c->arena.alloc_n(&c->b, n)) || (rc = c->arena.alloc_n(&c->q, n)) ||
+         (rc = c->arena.alloc_n(&c->V, 3 * n)) || (rc = c->arena.alloc_n(&c->W, 3 * n)) ||
+         (rc = c->arena.alloc_n(&c->Z, 2 * n)) || (rc = c->arena.alloc(&c->scal, sizeof(MScal))) ||
+         (rc = c->arena.alloc_n(&c->red.partial, size_t(kRedSlots) * kMaxRedBlocks)) ||
+         (rc = c->arena.alloc_n(&c->red.count, 1))))
+        return bail(rc);
     cudaError_t e;
-    if ((e = cudaMallocHost(&c->h_scal, sizeof(MScal))) != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
-    if ((e = cudaMemsetAsync(c->red.count, 0, sizeof(unsigned), m->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->A, 0, sizeof(double) * c->npl * m->nfp, m->stream)) != cudaSuccess)
+    if (minres) {
+        if ((e = cudaMallocHost(&c->h_scal, sizeof(MScal))) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMallocHost"));
+        if ((e = cudaMemsetAsync(c->red.count, 0, sizeof(unsigned), m->stream)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMemsetAsync"));
+    }
+    if ((e = cudaMemsetAsync(c->A, 0, sizeof(double) * c->npl * m->nfp, m->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
     if ((rc = launch_assemble_A(s, c->A, c->npl, c->dpart, c->spart, c->R, c->minv, c->DK, m->stream))) return bail(rc);
     const unsigned nb = unsigned((ne + kBlock - 1) / kBlock);
@@ -431,6 +457,36 @@ extern "C" int cr_coupled_create(cr_system* s, cr_coupled** out) {
     c->dpart = c->spart = nullptr;
     *out = c;
     return CR_OK;
+}
+
+int launch_coupled_apply(cr_coupled* c, const double* x, const double* b, double* y, cudaStream_t st) {
+    cr_mesh* m = c->m;
+    Op op{m->nf, m->ne, c->npl, m->cols, c->A, c->DK, m->elem_face, m->face_elems, m->face_local};
+    const int nbf = int((m->nf + kBlock - 1) / kBlock), nbe = int((m->ne + kBlock - 1) / kBlock);
+    if (m->d == 2) k_cp_apply<2><<<nbf + nbe, kBlock, 0, st>>>(op, nbf, x, b, y);
+    else k_cp_apply<3><<<nbf + nbe, kBlock, 0, st>>>(op, nbf, x, b, y);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int launch_coupled_rhs(cr_coupled* c, int rhs, double* b, cudaStream_t st) {
+    cr_mesh* m = c->m;
+    const int64_t N = m->nf * m->d, ne = m->ne;
+    k_mr_rhs<<<grid_vec(N + ne), kBlock, 0, st>>>(N, ne, c->R + size_t(rhs) * N, b);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+}  // namespace crhyb
+
+extern "C" int cr_coupled_create(cr_system* s, cr_coupled** out) {
+    if (!out) return fail(CR_ERR_ARG, "cr_coupled_create: out is NULL");
+    *out = nullptr;
+    if (!s) return fail(CR_ERR_ARG, "cr_coupled_create: NULL system");
+    CR_TRY(check_call(s->m, "cr_coupled_create", {}));
+    if (s->conv != CR_CONV_NONE)
+        return fail(CR_ERR_ARG, "cr_coupled_create: MINRES needs the symmetric (Stokes) system, conv = NONE");
+    return coupled_build(s, out, true);
 }
 
 extern "C" int cr_solve_coupled(cr_coupled* c, int rhs, const cr_solve_opts* o, double* U, double* P,

@@ -238,9 +238,9 @@ template <int D>
 __device__ __forceinline__ void rhs_local(const Geom<D>& g, const Topo<D>& t, const double* __restrict__ fb,
                                           double (&R)[D + 1][D], const double* __restrict__ up = nullptr,
                                           double mu = 0.0) {
-    double f[D];
+    double f[D];   // fb == NULL: no source (the right-hand side is the previous level alone)
 #pragma unroll
-    for (int b = 0; b < D; ++b) f[b] = __ldg(fb + b);
+    for (int b = 0; b < D; ++b) f[b] = fb ? __ldg(fb + b) : 0.0;
 #pragma unroll
     for (int l = 0; l <= D; ++l) {
         double rho = 0.0;
@@ -600,10 +600,11 @@ __global__ void __launch_bounds__(256) k_merge(int64_t nf, int nrhs, const doubl
 // D_K = -a_{K, sigma} kept per simplex [ne][d+1][d] (zero on exterior faces).
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double nu, double mu,
+__global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double nu, double mu, int conv,
+                                                           const double* __restrict__ w,
                                                            const double* __restrict__ fbar, int nrhs, Outputs o,
                                                            double* __restrict__ DK) {
-    constexpr int NF = D + 1;
+    constexpr int NF = D + 1, L = NF * D;
     const int64_t K = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (K >= mv.ne) return;
     const int64_t nf = mv.nf;
@@ -611,6 +612,21 @@ __global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double n
     simplex_geometry<D>(mv.coords, mv.elems + K * NF, g);
     Topo<D> t;
     load_topo<D>(mv, K, t);
+    // A_K: S_K (x) Id, completed with the linearised convection N_K(w) (2D, Newton or
+    // Oseen), whose Newton form also adds c_K(w) to R_K (Section 3.1)
+    double A2[kL2][kL2], cw[L];   // A2: the 2D convective A_K (used when conv != NONE)
+#pragma unroll
+    for (int p = 0; p < L; ++p) cw[p] = 0.0;
+    const bool use_conv = D == 2 && conv != CR_CONV_NONE;
+    if constexpr (D == 2) {
+        if (use_conv) conv_matrix2(g, t, w, nu, mu, conv, A2, cw);
+    }
+    auto aval = [&](int l, int i, int m, int j) -> double {
+        if constexpr (D == 2) {
+            if (use_conv) return A2[l * 2 + i][m * 2 + j];
+        }
+        return (t.in[l] && t.in[m] && i == j) ? s_entry<D>(g, l, m, nu, mu) : 0.0;
+    };
 #pragma unroll
     for (int l = 0; l < NF; ++l) {
 #pragma unroll
@@ -620,18 +636,18 @@ __global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double n
         const int s = t.side[l];
 #pragma unroll
         for (int m = 0; m < NF; ++m) {
-            const double sv = t.in[m] ? s_entry<D>(g, l, m, nu, mu) : 0.0;
             if (m == l) {
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
-                    for (int j = 0; j < D; ++j) o.dpart[((size_t(s) * D + i) * D + j) * nf + f] = i == j ? sv : 0.0;
+                    for (int j = 0; j < D; ++j) o.dpart[((size_t(s) * D + i) * D + j) * nf + f] = aval(l, i, l, j);
             } else {
                 const int slot = 1 + s * D + (m < l ? m : m - 1);
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
-                    for (int j = 0; j < D; ++j) store_val(o, sell(f, (slot * D + i) * D + j, o.npl), i == j ? sv : 0.0);
+                    for (int j = 0; j < D; ++j)
+                        store_val(o, sell(f, (slot * D + i) * D + j, o.npl), aval(l, i, m, j));
             }
         }
     }
@@ -642,9 +658,85 @@ __global__ void __launch_bounds__(kElemBlock) k_assemble_A(MeshView mv, double n
         for (int l = 0; l < NF; ++l) {
             if (!t.in[l]) continue;
 #pragma unroll
-            for (int i = 0; i < D; ++i) o.spart[((size_t(r) * 2 + t.side[l]) * D + i) * nf + t.face[l]] = R[l][i];
+            for (int i = 0; i < D; ++i)
+                o.spart[((size_t(r) * 2 + t.side[l]) * D + i) * nf + t.face[l]] = R[l][i] + cw[l * D + i];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Transient Stokes steps used as a preconditioner (steady problems): the
+// hybridised right-hand side S of a step with no source and the previous
+// level `up` alone (R_K = mu |K|/(d+1) up on the interior faces of K), and the
+// lumped face mass m_sigma = sum_{K ni sigma} |K|/(d+1) that turns a velocity
+// residual v into that previous level, up = v / (mu m).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kElemBlock) k_rhs_previous(MeshView mv, double nu, double mu,
+                                                             const double* __restrict__ up,
+                                                             const double* __restrict__ gdiv,
+                                                             double* __restrict__ spart, int32_t* status) {
+    constexpr int NF = D + 1;
+    const int64_t K = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (K >= mv.ne) return;
+    const int64_t nf = mv.nf;
+    Geom<D> g;
+    simplex_geometry<D>(mv.coords, mv.elems + K * NF, g);
+    Topo<D> t;
+    load_topo<D>(mv, K, t);
+    double e[NF];
+#pragma unroll
+    for (int l = 0; l < NF; ++l) e[l] = 0.0;
+    StokesLocal<D> L;
+    stokes_local<D>(g, t, e, nu, mu, K == mv.k0, L);
+    if (!L.ok) atomicExch(status, CR_ERR_SINGULAR);
+    double R[NF][D];
+    rhs_local<D>(g, t, nullptr, R, up, mu);
+    double vR = 0.0;
+#pragma unroll
+    for (int m = 0; m < NF; ++m)
+#pragma unroll
+        for (int j = 0; j < D; ++j) vR += L.v[m][j] * R[m][j];
+    // a divergence D_K^t U_K = g_K adds Â^{-1} D_K g_K / B_K (invB = 0 on K_0)
+    const double gK = gdiv ? gdiv[K] : 0.0;
+#pragma unroll
+    for (int l = 0; l < NF; ++l) {
+        if (!t.in[l]) continue;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < NF; ++m) s += L.Ti[l][m] * R[m][i];
+            s += L.v[l][i] * (gK - vR) * L.invB;
+            spart[(size_t(t.side[l]) * D + i) * nf + t.face[l]] = t.c[l] * s;
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_merge_rhs(int64_t nf, const double* __restrict__ spart,
+                                                   double* __restrict__ S) {
+    const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+        S[f * D + i] = spart[(size_t(0) * D + i) * nf + f] + spart[(size_t(1) * D + i) * nf + f];
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_face_mass(MeshView mv, double* __restrict__ mass) {
+    const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (f >= mv.nf) return;
+    double m = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int64_t K = __ldg(mv.face_elems + 2 * f + k);
+        Geom<D> g;
+        simplex_geometry<D>(mv.coords, mv.elems + K * (D + 1), g);
+        m += g.vol / double(D + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) mass[f * D + i] = m;
 }
 
 // ---------------------------------------------------------------------------
@@ -698,7 +790,8 @@ __global__ void __launch_bounds__(kBlock) k_recover_stokes(MeshView mv, double n
                                                            const double* __restrict__ fb, const double* __restrict__ W,
                                                            double* __restrict__ U, double* __restrict__ ualt,
                                                            double* __restrict__ P, RedBuf red,
-                                                           double* __restrict__ mean_out) {
+                                                           double* __restrict__ mean_out,
+                                                           const double* __restrict__ gdiv = nullptr) {
     constexpr int NF = D + 1;
     const int64_t K = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     double vals[2] = {0.0, 0.0};
@@ -712,20 +805,21 @@ __global__ void __launch_bounds__(kBlock) k_recover_stokes(MeshView mv, double n
         StokesLocal<D> L;
         stokes_local<D>(g, t, e, nu, mu, K == mv.k0, L);
         double R[NF][D];
-        rhs_local<D>(g, t, fb + size_t(K) * D, R, mv.uprev, mu);
+        rhs_local<D>(g, t, fb ? fb + size_t(K) * D : nullptr, R, mv.uprev, mu);
         double y[NF][D];
 #pragma unroll
         for (int l = 0; l < NF; ++l)
 #pragma unroll
             for (int i = 0; i < D; ++i)
                 y[l][i] = t.in[l] ? R[l][i] - t.c[l] * W[size_t(t.face[l]) * D + i] : 0.0;
-        // P_K = D^t Â^{-1} y / B = v . y / B (Â symmetric)
+        // P_K = (D^t Â^{-1} y - g_K) / B = (v . y - g_K) / B (Â symmetric; g = 0 but in a
+        // preconditioner solve with a divergence residual)
         double vy = 0.0;
 #pragma unroll
         for (int l = 0; l < NF; ++l)
 #pragma unroll
             for (int i = 0; i < D; ++i) vy += L.v[l][i] * y[l][i];
-        const double PK = vy * L.invB;
+        const double PK = (vy - (gdiv ? gdiv[K] : 0.0)) * L.invB;
 #pragma unroll
         for (int l = 0; l < NF; ++l) {
             if (!t.in[l]) continue;
@@ -883,12 +977,60 @@ int launch_assemble_A(cr_system* s, double* val64, int npl, double* dpart, doubl
     mv.uprev = s->uprev_on ? s->uprev : nullptr;
     Outputs o{val64, nullptr, nullptr, nullptr, nullptr, npl, dpart, spart, nullptr};
     const unsigned nbe = blocks_for(m->ne, kElemBlock);
-    if (m->d == 2) k_assemble_A<2><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->fbar, s->nrhs, o, DK);
-    else k_assemble_A<3><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->fbar, s->nrhs, o, DK);
+    if (m->d == 2) k_assemble_A<2><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, s->fbar, s->nrhs, o, DK);
+    else k_assemble_A<3><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, s->conv, s->w, s->fbar, s->nrhs, o, DK);
     CR_CUDA(cudaGetLastError());
     const unsigned nbf = blocks_for(m->nf, 256);
     if (m->d == 2) k_merge<2><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, dpart, spart, o, R, minv64, nullptr);
     else k_merge<3><<<nbf, 256, 0, st>>>(m->nf, s->nrhs, dpart, spart, o, R, minv64, nullptr);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int launch_rhs_previous(cr_hybrid* h, const double* up, const double* gdiv, double* spart, double* S,
+                        cudaStream_t st) {
+    cr_system* s = h->s;
+    cr_mesh* m = h->m;
+    if (s->conv != CR_CONV_NONE || !(s->mu > 0.0))
+        return fail(CR_ERR_ARG, "transient preconditioner: needs a Stokes system with mu > 0");
+    MeshView mv = view(m);
+    const unsigned nbe = blocks_for(m->ne, kElemBlock), nbf = blocks_for(m->nf, 256);
+    if (m->d == 2) {
+        k_rhs_previous<2><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, up, gdiv, spart, h->status);
+        k_merge_rhs<2><<<nbf, 256, 0, st>>>(m->nf, spart, S);
+    } else {
+        k_rhs_previous<3><<<nbe, kElemBlock, 0, st>>>(mv, s->nu, s->mu, up, gdiv, spart, h->status);
+        k_merge_rhs<3><<<nbf, 256, 0, st>>>(m->nf, spart, S);
+    }
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int launch_recover_previous(cr_hybrid* h, const double* up, const double* gdiv, const double* W, double* U,
+                            double* P, cudaStream_t st) {
+    cr_system* s = h->s;
+    cr_mesh* m = h->m;
+    if (s->conv != CR_CONV_NONE || !(s->mu > 0.0))
+        return fail(CR_ERR_ARG, "transient preconditioner: needs a Stokes system with mu > 0");
+    MeshView mv = view(m);
+    mv.uprev = up;
+    const unsigned nb = blocks_for(m->ne, kBlock);
+    if (nb > unsigned(kMaxRedBlocks)) return fail(CR_ERR_ARG, "mesh too large for one reduction pass");
+    if (m->d == 2)
+        k_recover_stokes<2><<<nb, kBlock, 0, st>>>(mv, s->nu, s->mu, nullptr, nullptr, W, U, nullptr, P, h->red, h->pvol,
+                                                   gdiv);
+    else
+        k_recover_stokes<3><<<nb, kBlock, 0, st>>>(mv, s->nu, s->mu, nullptr, nullptr, W, U, nullptr, P, h->red, h->pvol,
+                                                   gdiv);
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+int launch_face_mass(cr_mesh* m, double* mass, cudaStream_t st) {
+    MeshView mv = view(m);
+    const unsigned nbf = blocks_for(m->nf, 256);
+    if (m->d == 2) k_face_mass<2><<<nbf, 256, 0, st>>>(mv, mass);
+    else k_face_mass<3><<<nbf, 256, 0, st>>>(mv, mass);
     CR_CUDA(cudaGetLastError());
     return CR_OK;
 }

@@ -85,6 +85,30 @@ struct RedBuf {
     unsigned int* count;  // completion counter (reset by the last block)
 };
 
+// Workspace of the flexible GMRES of cr_solve_steady, kept with the
+// preconditioning hybrid (so that the steps of a Newton loop share it): Arnoldi vectors V [m+1][n] and preconditioned
+// vectors Z [m][n] over the coupled unknowns (n = nf d + ne), the iterate x,
+// b = [R; 0], a residual r; per face unknown the previous level up, the lumped
+// mass, the inner solve's W and S; the two-sided S scratch [2][d][nf]; the
+// Krylov scalars and a reduction buffer.
+struct SteadyWork {
+    DevArena arena;
+    int m = 0;
+    int64_t n = 0;
+    double *V = nullptr, *Z = nullptr, *x = nullptr, *b = nullptr, *r = nullptr;
+    double *up = nullptr, *mass = nullptr, *W = nullptr, *S = nullptr, *spart = nullptr;
+    void* scal = nullptr;
+    void* h_scal = nullptr;
+    RedBuf red{};
+    void release() {
+        arena.release();
+        if (h_scal) cudaFreeHost(h_scal);
+        h_scal = nullptr;
+        m = 0;
+        n = 0;
+    }
+};
+
 }  // namespace crhyb
 
 struct cr_mesh {
@@ -122,6 +146,7 @@ struct cr_system {
     double* w = nullptr;      // [nf][d] or null
     double* uprev = nullptr;  // [nrhs][nf][d]: previous time level (implicit Euler), used when uprev_on
     bool uprev_on = false;
+    cr_coupled* steady_op = nullptr;   // coupled operator of a steady system (cr_solve_steady), made on first use
 };
 
 struct cr_hybrid {
@@ -172,6 +197,7 @@ struct cr_hybrid {
     int graph_key[kGraphs] = {-1, -1, -1, -1, -1, -1, -1, -1};
     int64_t graph_launches[kGraphs] = {};   // kernels in each captured chunk
     void* pplan[3] = {nullptr, nullptr, nullptr};   // persistent PCG plans (FP64, FF, FF_BF16), solve.cu
+    crhyb::SteadyWork steady;     // cr_solve_steady with this hybrid as preconditioner (first use)
 };
 
 namespace crhyb {
@@ -187,6 +213,23 @@ int launch_assemble_A(cr_system* s, double* val64, int npl, double* dpart, doubl
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st);
 int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* Wdev,
                       cr_solve_stats* st);
+// steady problems: the coupled operator of any system, y = K x or b - K x, b = [R_rhs; 0]
+int coupled_build(cr_system* s, cr_coupled** out, bool minres);
+int launch_coupled_apply(cr_coupled* c, const double* x, const double* b, double* y, cudaStream_t st);
+int launch_coupled_rhs(cr_coupled* c, int rhs, double* b, cudaStream_t st);
+// the transient Stokes step of h as a preconditioner: S from the previous level up alone
+// (no source) and a divergence gdiv per simplex (D_K^t U_K = gdiv_K; NULL: 0), the
+// recovery of U and P (P_{K_0} = 0, not normalised) from W, up and gdiv, the lumped face
+// mass m_sigma per face unknown
+int launch_rhs_previous(cr_hybrid* h, const double* up, const double* gdiv, double* spart, double* S,
+                        cudaStream_t st);
+int launch_recover_previous(cr_hybrid* h, const double* up, const double* gdiv, const double* W, double* U,
+                            double* P, cudaStream_t st);
+int launch_face_mass(cr_mesh* m, double* mass, cudaStream_t st);
+int solve_steady_impl(cr_coupled* c, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_solve_opts* o, double* U,
+                      double* P, cr_solve_stats* st);
+int solve_newton_impl(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin, double ntol,
+                      int maxn, double* U, double* P, cr_newton_stats* st);
 void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 

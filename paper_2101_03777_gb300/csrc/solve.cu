@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -973,6 +974,33 @@ __global__ void __launch_bounds__(kBlock) k_residual_w(int64_t nf, const int32_t
 }
 
 // ---------------------------------------------------------------------------
+// Steady problems: flexible GMRES on the coupled system, preconditioned by
+// transient hybridised solves (cr_solve_steady)
+// ---------------------------------------------------------------------------
+
+// up = v / (mu m): the previous level whose lumped mass term mu m up is the
+// velocity block v of an Arnoldi vector
+__global__ void __launch_bounds__(kBlock) k_prev_from_residual(int64_t N, const double* __restrict__ v,
+                                                             const double* __restrict__ mass, double mu,
+                                                             double* __restrict__ up) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < N; k += int64_t(gridDim.x) * blockDim.x)
+        up[k] = v[k] / (mu * mass[k]);
+}
+
+// sum of squares of r into sc->orr (slot 0) or sc->obb (slot 1)
+__global__ void __launch_bounds__(kBlock) k_sumsq(int64_t n, const double* __restrict__ r, KScal* sc, RedBuf red,
+                                                int slot) {
+    double part[1] = {0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        part[0] += r[k] * r[k];
+    double tot[1];
+    if (grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        if (slot == 0) sc->orr = tot[0];
+        else sc->obb = tot[0];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
 struct Ctx {
@@ -1686,6 +1714,279 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     return status;
 }
 
+// Flexible GMRES(m) (Saad, Algorithm 9.6) on the steady coupled system
+// K_s [U; P] = [R; 0] (Eq. 10 with mu = 0), right-preconditioned by the
+// transient Stokes step of `pre` (mu_pre > 0): z = K_mu^{-1} [v; g] is one
+// hybridised solve (persistent PCG on G_mu to inner_tol, FP64 or float-float)
+// whose right-hand side is the previous level v / (mu m) with no source and
+// the divergence g per simplex, followed by the element-wise recovery.  The Arnoldi vectors, the minimised
+// residual and the update x += Z y are those of K_s, so the result is the
+// steady solution whatever the inner solves return; only the number of
+// steps depends on them (on divergence-free fields K_s K_mu^{-1} has the
+// eigenvalues lambda / (lambda + mu), lambda those of the steady operator).
+template <int D>
+int solve_steady(cr_coupled* cpl, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_solve_opts* o, double* U, double* P,
+                 cr_solve_stats* st, double* res0 = nullptr) {
+    const int64_t N = m->nf * D, ne = m->ne, n = N + ne;
+    const cudaStream_t s = m->stream;
+    const int mr = o->restart > 0 ? o->restart : 30;
+    SteadyWork& w = pre->steady;
+    if (w.m < mr || w.n != n) {
+        w.release();
+        CR_TRY(w.arena.alloc_n(&w.V, size_t(mr + 1) * n));
+        CR_TRY(w.arena.alloc_n(&w.Z, size_t(mr) * n));
+        CR_TRY(w.arena.alloc_n(&w.x, size_t(n)));
+        CR_TRY(w.arena.alloc_n(&w.b, size_t(n)));
+        CR_TRY(w.arena.alloc_n(&w.r, size_t(n)));
+        CR_TRY(w.arena.alloc_n(&w.up, size_t(N)));
+        CR_TRY(w.arena.alloc_n(&w.mass, size_t(N)));
+        CR_TRY(w.arena.alloc_n(&w.W, size_t(N)));
+        CR_TRY(w.arena.alloc_n(&w.S, size_t(N)));
+        CR_TRY(w.arena.alloc_n(&w.spart, size_t(2) * N));
+        CR_TRY(w.arena.alloc(&w.scal, sizeof(KScal)));
+        CR_TRY(w.arena.alloc_n(&w.red.partial, size_t(kRedSlots) * kMaxRedBlocks));
+        CR_TRY(w.arena.alloc_n(&w.red.count, 1));
+        CR_CUDA(cudaMemsetAsync(w.red.count, 0, sizeof(unsigned), s));
+        CR_CUDA(cudaMallocHost(&w.h_scal, sizeof(KScal)));
+        w.m = mr;
+        w.n = n;
+    }
+    Ctx c{pre, s, static_cast<KScal*>(w.scal), static_cast<KScal*>(w.h_scal), m->nf, n, D, false};
+    Ctx cp{pre, s, static_cast<KScal*>(pre->scal), static_cast<KScal*>(pre->h_scal), m->nf, N, D, false};
+    const int g = grid_for(n), gN = grid_for(N);
+    const int mode = persistent_mode(o->prec);
+    const double itol = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : 1e-4;
+    const int gmax = o->max_iter > 0 ? o->max_iter : 1000;
+    const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
+    const double mu = pre->s->mu;
+    std::memset(c.hs, 0, sizeof(KScal));
+    c.hs->max_it = gmax;
+    c.hs->m = mr;
+    CR_CUDA(cudaMemcpyAsync(c.sc, c.hs, sizeof(KScal), cudaMemcpyHostToDevice, s));
+    CR_TRY(launch_face_mass(m, w.mass, s));
+    CR_TRY(launch_coupled_rhs(cpl, rhs, w.b, s));
+    if (o->use_x0) {
+        CR_CUDA(cudaMemcpyAsync(w.x, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        CR_CUDA(cudaMemcpyAsync(w.x + N, P, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CR_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, s));
+    }
+    // tol2 = tol^2 ||[R; 0]||^2
+    k_sumsq<<<g, kBlock, 0, s>>>(n, w.b, c.sc, w.red, 1);
+    ++c.launches;
+    CR_CUDA(cudaGetLastError());
+    CR_TRY(read_scal(c));
+    const double bb = c.hs->obb;
+    c.hs->tol2 = o->tol * o->tol * bb;
+    CR_CUDA(cudaMemcpyAsync(&c.sc->tol2, &c.hs->tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+    int64_t inner_its = 0, prof_it = 0;
+    double prof_ms = 0.0;
+    int status = CR_OK;
+    int first_inner = -1, inner_cap = 200000;
+    bool first_cycle = true;
+    if (res0) *res0 = 0.0;
+    if (bb > 0.0) {
+        for (;;) {
+            CR_TRY(launch_coupled_apply(cpl, w.x, w.b, w.r, s));   // r = b - K x
+            k_gm_norm_start<double><<<g, kBlock, 0, s>>>(n, w.r, c.sc, w.red);
+            k_gm_scale_v0<double><<<g, kBlock, 0, s>>>(n, w.r, w.V, c.sc);
+            c.launches += 3;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            if (res0 && first_cycle) *res0 = std::sqrt(c.hs->rr / bb);
+            first_cycle = false;
+            if (c.hs->done) break;
+            for (int j = 0; j < mr; ++j) {
+                double* z = w.Z + size_t(j) * n;
+                // z_j = K_mu^{-1} [v_j; 0]: previous level, S, inner PCG, recovery
+                k_prev_from_residual<<<gN, kBlock, 0, s>>>(N, w.V + size_t(j) * n, w.mass, mu, w.up);
+                ++c.launches;
+                const double* gdiv = w.V + size_t(j) * n + N;   // the divergence block of v_j
+                CR_TRY(launch_rhs_previous(pre, w.up, gdiv, w.spart, w.S, s));
+                c.launches += 2;
+                PScal Pst{};
+                double kms = 0.0;
+                int64_t kit = 0;
+                // an inner solve that stagnates above inner_tol (its attainable accuracy) stops at
+                // four times the first one's iterations; the flexible outer step takes what it returns
+                CR_TRY(persistent_pcg<D>(cp, w.S, nullptr, w.W, mode, itol, default_delta(mode), inner_cap,
+                                         per_launch, o->profile != 0, &Pst, &kms, &kit));
+                if (first_inner < 0) {
+                    first_inner = Pst.it;
+                    inner_cap = int(std::min<int64_t>(int64_t(4) * std::max(first_inner, 64), 1000000));
+                }
+                inner_its += Pst.it;
+                prof_ms += kms;
+                prof_it += kit;
+                if (Pst.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+                CR_TRY(launch_recover_previous(pre, w.up, gdiv, w.W, z, z + N, s));
+                ++c.launches;
+                // v_{j+1} = K_s z_j, orthogonalised (CGS2) and normalised
+                CR_TRY(launch_coupled_apply(cpl, z, nullptr, w.V + size_t(j + 1) * n, s));
+                ++c.launches;
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int i0 = 0; i0 <= j; i0 += kRedSlots) {
+                        k_gm_dots<double><<<g, kBlock, 0, s>>>(n, w.V, i0, c.sc, w.red);
+                        ++c.launches;
+                    }
+                    k_gm_orth<double><<<g, kBlock, 0, s>>>(n, w.V, c.sc, w.red, pass);
+                    ++c.launches;
+                }
+                k_gm_normalise<double><<<g, kBlock, 0, s>>>(n, w.V, c.sc);
+                ++c.launches;
+                CR_CUDA(cudaGetLastError());
+                CR_TRY(read_scal(c));
+                if (c.hs->done || c.hs->stop) break;
+            }
+            if (status != CR_OK) break;
+            k_gm_solve_y<<<1, 32, 0, s>>>(c.sc);
+            k_fgm_update<<<g, kBlock, 0, s>>>(n, w.x, w.Z, c.sc);
+            c.launches += 2;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            if (c.hs->status != CR_OK) break;
+        }
+    }
+    c.launches += cp.launches;
+    CR_TRY(read_scal(c));
+    if (status == CR_OK) status = c.hs->status;
+    const int steps = c.hs->it;
+    // U, P and the FP64 residual of the coupled system they satisfy
+    CR_CUDA(cudaMemcpyAsync(U, w.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(P, w.x + N, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+    CR_TRY(launch_coupled_apply(cpl, w.x, w.b, w.r, s));
+    k_sumsq<<<g, kBlock, 0, s>>>(n, w.r, c.sc, w.red, 0);
+    c.launches += 2;
+    CR_CUDA(cudaGetLastError());
+    CR_TRY(read_scal(c));
+    const double relres = bb > 0.0 ? std::sqrt(c.hs->orr / bb) : 0.0;
+    if (status == CR_OK && !(relres <= o->tol)) status = CR_ERR_NOT_CONVERGED;
+    if (st) {
+        st->iterations = int32_t(inner_its);
+        st->outer = steps;
+        st->relres = relres;
+        st->status = status;
+        st->spmv_launches = int32_t(prof_it);
+        st->spmv_ms = prof_ms;
+        st->kernel_launches = c.launches;
+    }
+    if (status == CR_ERR_NOT_CONVERGED) return fail(status, "cr_solve_steady: step limit reached before the tolerance");
+    if (status == CR_ERR_BREAKDOWN)
+        return fail(status, "cr_solve_steady: breakdown (zero Arnoldi vector, NaN, or p.Gp <= 0 in an inner PCG)");
+    return status;
+}
+
+// sc->orr = sum (a - b)^2, sc->obb = sum a^2
+__global__ void __launch_bounds__(kBlock) k_diff_sumsq(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, KScal* sc, RedBuf red) {
+    double part[2] = {0.0, 0.0};
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double d = a[k] - b[k];
+        part[0] += d * d;
+        part[1] += a[k] * a[k];
+    }
+    double tot[2];
+    if (grid_sum<2>(part, red, tot) && threadIdx.x == 0) {
+        sc->orr = tot[0];
+        sc->obb = tot[1];
+    }
+}
+
+// Newton's method for the steady Navier-Stokes problem (Section 3.1 with
+// b_h != 0, mu = 0): from U_0 (the caller's U), step k solves the steady
+// coupled system linearised about w = U_k (the Newton Jacobian and its
+// right-hand side R + c_K(w), cr_assemble_coupled with conv = NEWTON) by
+// cr_solve_steady's flexible GMRES from [U_k; P_k], whose first residual is
+// the nonlinear residual at (U_k, P_k); the solution is U_{k+1}.  It stops
+// when ||U_{k+1} - U_k|| <= newton_tol ||U_{k+1}||.
+template <int D>
+int solve_newton(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin, double ntol,
+                 int maxn, double* U, double* P, cr_newton_stats* st) {
+    const int64_t N = m->nf * D, ne = m->ne;
+    const cudaStream_t s = m->stream;
+    DevArena tmp;
+    double *Un = nullptr, *Pn = nullptr;
+    CR_TRY(tmp.alloc_n(&Un, size_t(N)));
+    CR_TRY(tmp.alloc_n(&Pn, size_t(ne)));
+    cr_solve_opts o = *lin;
+    o.use_x0 = 1;
+    int status = CR_ERR_NOT_CONVERGED, k = 0, steps = 0;
+    int64_t inner = 0;
+    double incr = 0.0, res_first = 0.0;
+    for (; k < maxn;) {
+        cr_params p{nu, 0.0, CR_CONV_NEWTON, 0.0};
+        cr_system* sys = nullptr;
+        int rc = cr_assemble_coupled(m, &p, fbar, 1, U, &sys, nullptr);
+        if (rc != CR_OK) { tmp.release(); return rc; }
+        rc = coupled_build(sys, &sys->steady_op, false);
+        cr_solve_stats lst{};
+        double res0 = 0.0;
+        if (rc == CR_OK) {
+            CR_CUDA(cudaMemcpyAsync(Un, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            CR_CUDA(cudaMemcpyAsync(Pn, P, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+            rc = solve_steady<D>(sys->steady_op, m, pre, 0, &o, Un, Pn, &lst, &res0);
+        }
+        cr_destroy_system(sys);
+        ++k;
+        steps += lst.outer;
+        inner += lst.iterations;
+        if (k == 1) res_first = res0;
+        if (rc != CR_OK) { status = rc; break; }
+        // the increment, then U_{k+1}, P_{k+1}
+        SteadyWork& w = pre->steady;
+        Ctx c{pre, s, static_cast<KScal*>(w.scal), static_cast<KScal*>(w.h_scal), m->nf, N, D, false};
+        k_diff_sumsq<<<grid_for(N), kBlock, 0, s>>>(N, Un, U, c.sc, w.red);
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        incr = c.hs->obb > 0.0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
+        CR_CUDA(cudaMemcpyAsync(U, Un, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        CR_CUDA(cudaMemcpyAsync(P, Pn, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+        if (!std::isfinite(incr)) { status = CR_ERR_BREAKDOWN; break; }
+        if (incr <= ntol) { status = CR_OK; break; }
+    }
+    // the nonlinear residual at the returned (U, P): the Newton system linearised about U
+    // evaluated at [U; P] (b_h is quadratic: J(U) U - c(U) = b_h(U, U))
+    double resid = 0.0;
+    {
+        cr_params p{nu, 0.0, CR_CONV_NEWTON, 0.0};
+        cr_system* sys = nullptr;
+        int rc = cr_assemble_coupled(m, &p, fbar, 1, U, &sys, nullptr);
+        if (rc == CR_OK) rc = coupled_build(sys, &sys->steady_op, false);
+        if (rc == CR_OK) {
+            SteadyWork& w = pre->steady;
+            Ctx c{pre, s, static_cast<KScal*>(w.scal), static_cast<KScal*>(w.h_scal), m->nf, N + ne, D, false};
+            CR_CUDA(cudaMemcpyAsync(w.x, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            CR_CUDA(cudaMemcpyAsync(w.x + N, P, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+            rc = launch_coupled_rhs(sys->steady_op, 0, w.b, s);
+            if (rc == CR_OK) rc = launch_coupled_apply(sys->steady_op, w.x, w.b, w.r, s);
+            if (rc == CR_OK) {
+                k_sumsq<<<grid_for(N + ne), kBlock, 0, s>>>(N + ne, w.r, c.sc, w.red, 0);
+                k_sumsq<<<grid_for(N + ne), kBlock, 0, s>>>(N + ne, w.b, c.sc, w.red, 1);
+                CR_CUDA(cudaGetLastError());
+                CR_TRY(read_scal(c));
+                resid = c.hs->obb > 0.0 ? std::sqrt(c.hs->orr / c.hs->obb) : 0.0;
+            }
+        }
+        cr_destroy_system(sys);
+        if (rc != CR_OK) { tmp.release(); return rc; }
+    }
+    CR_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+    if (st) {
+        st->iterations = k;
+        st->linear_steps = steps;
+        st->inner_iterations = inner;
+        st->increment = incr;
+        st->residual = resid;
+        st->first_residual = res_first;
+        st->status = status;
+    }
+    if (status == CR_ERR_NOT_CONVERGED)
+        return fail(status, "cr_solve_newton: Newton iteration limit reached before the increment tolerance");
+    if (status != CR_OK) return status;
+    return CR_OK;
+}
+
 }  // namespace
 
 size_t kscal_bytes() { return sizeof(KScal); }
@@ -1701,6 +2002,17 @@ int launch_spmv64(cr_hybrid* h, const double* x, double* y, cudaStream_t st) {
 int solve_fgmres_impl(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* Wdev,
                       cr_solve_stats* st) {
     return h->m->d == 2 ? solve_fgmres<2>(h, rhs, pre, o, Wdev, st) : solve_fgmres<3>(h, rhs, pre, o, Wdev, st);
+}
+
+int solve_steady_impl(cr_coupled* c, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_solve_opts* o, double* U,
+                      double* P, cr_solve_stats* st) {
+    return m->d == 2 ? solve_steady<2>(c, m, pre, rhs, o, U, P, st) : solve_steady<3>(c, m, pre, rhs, o, U, P, st);
+}
+
+int solve_newton_impl(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin, double ntol,
+                      int maxn, double* U, double* P, cr_newton_stats* st) {
+    return m->d == 2 ? solve_newton<2>(m, nu, fbar, pre, lin, ntol, maxn, U, P, st)
+                     : solve_newton<3>(m, nu, fbar, pre, lin, ntol, maxn, U, P, st);
 }
 
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {

@@ -17,7 +17,7 @@ from paper_2101_03777_gb300 import crhyb
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = [crhyb.cr_mesh_opts, crhyb.cr_params, crhyb.cr_hyb_opts, crhyb.cr_solve_opts, crhyb.cr_solve_stats,
-           crhyb.cr_batch_opts]
+           crhyb.cr_batch_opts, crhyb.cr_newton_stats]
 
 
 def c_layout(tmp_path):

@@ -13,16 +13,18 @@ fit in one pass of every kernel.  These meshes do not:
     rebalanced tiles at the end of the solve;
   * a transient Newton step on 384 x 384 squares (flexible GMRES with inner
     float-float PCG).
-The GPU solves to a relative residual of 1e-12 and recovers U and P (P
+The GPU solves to a relative residual of 1e-11 and recovers U and P (P
 normalised to zero mean, Section 2 item 5); they must match the oracle's
 within 1e-9 relative L2 (FP64, float-float, Chebyshev) or 1e-8 (float-float
 with BF16 low parts), the tolerances of the parity tests.  The oracle's
 truths (fullsize_truth.py) are computed in spawned worker processes while the
-GPU solves run.  1e-12 is near the attainable accuracy at these sizes: the
+GPU solves run.  1e-11 is near the attainable accuracy at these sizes: the
 oracle's own sparse LU of G leaves a relative residual of 1.6e-13 at 384 x 384,
-and FP64 PCG stagnates above 1e-13 there; on the oracle at 128 x 128 a PCG
-solve to 1e-13 recovers U within 1.5e-13 of the direct solve, so the U and P
-errors of a solve to 1e-12 stay orders of magnitude below the tolerances.
+and the GPU's FP64 PCG, whose true residual is evaluated in FP64, stagnates
+between 1e-12 and 1e-11 there; on the oracle at 128 x 128 a PCG solve to 1e-13
+recovers U within 1.5e-13 of the direct solve (the recovered U is far better
+conditioned than W), so the U and P errors of a solve to 1e-11 stay orders of
+magnitude below the tolerances.
 """
 
 import multiprocessing
@@ -110,8 +112,8 @@ def test_2d_384_matches_oracle(truths, solver):
     assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
     opts, tol = SOLVERS[solver]
     opts = dict(opts, **({"poly_ratio": 1000.0} if "chebyshev" in solver else {}))
-    st, U, P = solve_recover(hyb, tol=1e-12, max_iter=400000, **opts)
-    assert st["status"] == 0 and st["relres"] <= 1e-12
+    st, U, P = solve_recover(hyb, tol=1e-11, max_iter=400000, **opts)
+    assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po = truths["2d"].result()[0]
     assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))
 
@@ -124,16 +126,16 @@ def test_newton_384_matches_oracle(truths):
     hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb, conv="newton",
                                                        w=torch.from_numpy(w).cuda()), keep_fp32=False)
     pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb), keep_fp32=False, keep_ff=True)
-    st, U, P = solve_recover(hyb, solver=lambda W: crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-12,
+    st, U, P = solve_recover(hyb, solver=lambda W: crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-11,
                                                                                  prec="ff", max_iter=2000))
-    assert st["status"] == 0 and st["relres"] <= 1e-12
+    assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po = truths["newton"].result()
     assert rel(U, Uo) <= 1e-9 and rel(P, Po) <= 1e-9, (rel(U, Uo), rel(P, Po))
 
 
 def test_full_batch_largest_and_smallest_problems_match_oracle(truths):
     """The batched workload as the bench runs it (float-float, autotuned), every pair to
-    1e-12; the largest problem (n = 234) and the smallest (n = 9) against the oracle."""
+    1e-11; the largest problem (n = 234) and the smallest (n = 9) against the oracle."""
     probs = synth.batch_problems(count=64, nrhs=4, lo=8, hi=256, seed=2)
     hybs = []
     for q in probs:
@@ -143,8 +145,8 @@ def test_full_batch_largest_and_smallest_problems_match_oracle(truths):
                                        keep_ff=True))
     batch = crhyb.cr_batch_create(hybs, prec="ff", autotune=True)
     Ws = [torch.zeros(4 * h.n, dtype=torch.float64, device="cuda") for h in hybs]
-    stats = crhyb.cr_solve_batched(batch, Ws, tol=1e-12, max_iter=400000)
-    assert all(s["status"] == 0 and s["relres"] <= 1e-12 for s in stats)
+    stats = crhyb.cr_solve_batched(batch, Ws, tol=1e-11, max_iter=400000)
+    assert all(s["status"] == 0 and s["relres"] <= 1e-11 for s in stats)
     sizes = [q["n"] for q in probs]
     for key, k in (("batch", _largest_batch_problem()), ("batch_small", int(np.argmin(sizes)))):
         h = hybs[k]
@@ -164,7 +166,7 @@ def test_3d_32cubed_matches_oracle(truths, solver):
     assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
     opts, tol = SOLVERS[solver]
     opts = dict(opts, **({"poly_ratio": 100.0} if "chebyshev" in solver else {}))
-    st, U, P = solve_recover(hyb, tol=1e-12, max_iter=400000, **opts)
-    assert st["status"] == 0 and st["relres"] <= 1e-12
+    st, U, P = solve_recover(hyb, tol=1e-11, max_iter=400000, **opts)
+    assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po, _ = truths["3d"].result()
     assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))

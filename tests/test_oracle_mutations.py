@@ -9,13 +9,14 @@ import warnings
 import numpy as np
 import pytest
 
-from oracle import elements, hybrid, krylov, topology
+from oracle import elements, hybrid, krylov, steady, topology
 import test_oracle_chebyshev as tc
 import test_oracle_deflation as tdf
 import test_oracle_geometry as tg
 import test_oracle_krylov as tk
 import test_oracle_hybrid as th
 import test_oracle_minres as tm
+import test_oracle_steady as ts
 import test_oracle_time as tt
 
 
@@ -147,6 +148,19 @@ CASES = [
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(keep_rho=False), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
+    ("face_mass", steady,
+     _edited(steady, "face_mass", "share = geom[\"vol\"] / (d + 1)", "share = geom[\"vol\"] / d"),   # |K|/d
+     lambda: ts.test_preconditioner_is_the_transient_coupled_solve(2, 6, "none")),
+    ("TransientPreconditioner", steady,
+     _edited(steady, "TransientPreconditioner", "SK = Cv * (np.einsum(\"kab,kb->ka\", M, R_K) + u * (gK * invB)[:, None])",
+             "SK = Cv * np.einsum(\"kab,kb->ka\", M, R_K)"),                                   # divergence dropped from S
+     lambda: ts.test_preconditioner_is_the_transient_coupled_solve(2, 6, "none")),
+    ("fgmres", steady,
+     _edited(steady, "fgmres", "x = x + Z[:k].T @ y", "x = x + V[:k].T @ y"),            # update from V, not Z
+     lambda: ts.test_fgmres_cycle_is_the_minimal_residual_over_span_Z()),
+    ("fgmres", steady,
+     _edited(steady, "fgmres", "x = x + Z[:k].T @ y", "x = x + V[:k].T @ y"),
+     lambda: ts.test_steady_solution_equals_the_direct_solve(2, 10, 1.0, "none", 30.0)),
 ]
 
 
