@@ -111,7 +111,7 @@ def supported_precs(workload, precs):
     """The Chebyshev-preconditioned PCG serves the single transient Stokes solve; the batch
     and the Newton step keep their Jacobi-preconditioned solvers."""
     if workload in ("cfg4", "cfg5"):
-        return ",".join(x for x in precs.split(",") if x and x != "fp64_cheb") or "ff"
+        return ",".join(x for x in precs.split(",") if x and x not in ("fp64_cheb", "ff_cheb")) or "ff"
     return precs
 
 
@@ -144,6 +144,9 @@ PRECS = {
                   "PCG, native FP64, Chebyshev polynomial preconditioner of degree 4 (Jacobi-preconditioned "
                   "Chebyshev steps under the Gershgorin bound; interval ratio 1000 in 2D, 100 in 3D), "
                   "graph-replayed kernels"),
+    "ff_cheb": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01), 8, 8,
+                "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
+                "of degree 4 (interval ratio 1000 in 2D, 100 in 3D), graph-replayed kernels"),
 }
 CHEB_RATIO = {2: 1000.0, 3: 100.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
@@ -152,11 +155,15 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # (k_cheb_step).  Each entry records the SHA-256 of the kernel's source files when it was
 # captured; the bench reports it only while those files are unchanged, else null.
 KERNEL_SOURCES = {
-    "persist": ["persist.cu", "persist.h", "ff.cuh", "device_common.cuh", "internal.h"],
-    "solve": ["solve.cu", "ff.cuh", "device_common.cuh", "internal.h"],
+    "persist": ["persist.cu", "persist.h", "ff.cuh", "device_common.cuh"],
+    "solve": ["solve.cu", "ff.cuh", "device_common.cuh"],
 }
 TRAFFIC = {
     # (workload, solver): {"per": "iteration" | "launch", "bytes": B, "sources": key, "sha256": digest}
+    # the persistent float-float kernel on the 64^3 workload: two launches of 64 iterations,
+    # 164.43 GB and 168.86 GB read + written
+    ("cfg3", "ff"): {"per": "iteration", "bytes": (164.431e9 + 168.859e9) / 2 / 64, "sources": "persist",
+                     "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
 }
 
 
@@ -182,9 +189,10 @@ def measured_traffic(workload, prec):
 
 
 SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
-               "mixed": "k_pcg_spmv<FP32>", "fp64_cheb": "k_cheb_step<FP64> (SpMV + Chebyshev update)"}
+               "mixed": "k_pcg_spmv<FP32>", "fp64_cheb": "k_cheb_step<FP64> (SpMV + Chebyshev update)",
+               "ff_cheb": "kf_cheb_step<float-float> (SpMV + Chebyshev update)"}
 DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
-         "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64"}
+         "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64", "ff_cheb": "f32x2 (float-float)"}
 
 
 def solve_opts(prec, tol, graph, profile, persistent):
@@ -435,8 +443,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             st = crhyb.cr_solve_preconditioned(hyb, pre, Wt, raise_on_error=not args.max_iter, **o)
             crhyb.cr_recover_up(hyb, Wt, Ut, Pt, normalise_p=True)
             return st
-        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_bf16=False, keep_ff=(prec == "ff"),
-                                 keep_ff_bf16=(prec == "ff_bf16"))
+        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_bf16=False,
+                                 keep_ff=(prec in ("ff", "ff_cheb")), keep_ff_bf16=(prec == "ff_bf16"))
         o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
         o["check_every"] = args.check_every
         if o.get("precond") == "chebyshev":
@@ -536,11 +544,11 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         st_main, st_spmv = prof[prec]
         solver = PRECS[prec][3]
         spmv = None
-        if st_spmv is not None and prec == "fp64_cheb":
+        if st_spmv is not None and prec in ("fp64_cheb", "ff_cheb"):
             # the Chebyshev steps: degree - 1 launches per CG iteration, each the SpMV over G fused
             # with the vector update (reads r, d, M^{-1}; writes d and the other z buffer)
             deg = PRECS[prec][0]["poly_degree"]
-            step_bytes = spmv_bytes + 4 * N * xb
+            step_bytes = spmv_bytes + 3 * N * xb + N * (8 if prec == "fp64_cheb" else 4)
             nit = max(st_spmv["spmv_launches"], 1)
             ms = st_spmv["spmv_ms"] / (nit * (deg - 1))
             tb, tnote = measured_traffic(workload, prec)
@@ -576,7 +584,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             else:
                 solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
                           f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
-        elif prec == "fp64_cheb":
+        elif prec in ("fp64_cheb", "ff_cheb"):
             roof = dict(spmv)
         elif args.persistent:
             # the persistent PCG kernel: per iteration the SpMV plus the vector phases (the update

@@ -142,11 +142,13 @@ typedef struct cr_solve_opts {
                            persistent launch (grid barriers with bounded waits between its phases;
                            up to check_every*64 iterations per launch) instead of three launches
                            per iteration; profile and use_graph are ignored then */
-    int32_t precond;    /* enum cr_precond (0: Jacobi).  CHEBYSHEV is implemented for PCG in FP64 on
-                           the multi-kernel path (persistent is ignored): an iteration is the SpMV of CG,
-                           the update, poly_degree - 1 Chebyshev steps (each one SpMV fused with its
-                           vector update) and the direction; profile = 1 times the Chebyshev steps.
-                           cr_solve_preconditioned, cr_solve_coupled and cr_solve_batched take Jacobi only */
+    int32_t precond;    /* enum cr_precond (0: Jacobi).  CHEBYSHEV is implemented for PCG in FP64, FF and
+                           FF_BF16 on the multi-kernel path (persistent is ignored): an iteration is the
+                           SpMV of CG, the update, poly_degree - 1 Chebyshev steps (each one SpMV fused
+                           with its vector update) and the direction; the float-float forms take FP64
+                           reliable updates as their Jacobi forms do; profile = 1 times the Chebyshev
+                           steps.  cr_solve_preconditioned, cr_solve_steady, cr_solve_coupled and
+                           cr_solve_batched take Jacobi only */
     int32_t poly_degree;/* CHEBYSHEV: polynomial degree, 2..CR_MAX_POLY_DEGREE (0 selects 4) */
     double poly_ratio;  /* CHEBYSHEV: lmax / (lower end of the interval), > 1 (<= 0 selects 100) */
 } cr_solve_opts;

@@ -38,15 +38,13 @@ int pointer_place(const void* p, int* owner) {
         cudaGetLastError();   // clear the sticky-free error of an unknown pointer
         return 0;
     }
-    if (a.type == cudaMemoryTypeManaged) return 1;
-    if (a.type != cudaMemoryTypeDevice) return 0;
     int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) {
+    if (a.type == cudaMemoryTypeDevice && cudaGetDevice(&cur) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
-    if (owner) *owner = a.device;
-    return a.device == cur ? 1 : -1;
+    if (owner && a.type == cudaMemoryTypeDevice) *owner = a.device;
+    return place_of(a.type, a.device, cur);
 }
 
 bool is_device_pointer(const void* p) { return pointer_place(p, nullptr) == 1; }
@@ -373,8 +371,10 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
         return fail(CR_ERR_ARG, "cr_solve: bad preconditioner");
     if (o->precond == CR_PRECOND_CHEBYSHEV) {
-        if (o->method != CR_METHOD_PCG || o->prec != CR_PREC_FP64)
-            return fail(CR_ERR_ARG, "cr_solve: the Chebyshev preconditioner is implemented for PCG in FP64");
+        if (o->method != CR_METHOD_PCG ||
+            (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16))
+            return fail(CR_ERR_ARG, "cr_solve: the Chebyshev preconditioner is implemented for PCG in FP64, FF and "
+                                    "FF_BF16");
         const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
         if (deg < 2 || deg > CR_MAX_POLY_DEGREE)
             return fail(CR_ERR_ARG, "cr_solve: poly_degree must be in [2, CR_MAX_POLY_DEGREE]");
@@ -387,6 +387,8 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
     CR_TRY(ensure_workspace(h, o->method == CR_METHOD_GMRES, restart, o->prec));
     if (o->method == CR_METHOD_BICGSTAB) CR_TRY(ensure_workspace(h, false, restart, -1));
     if (o->precond == CR_PRECOND_CHEBYSHEV && !h->cheb) CR_TRY(h->arena.alloc_n(&h->cheb, 3 * n + 1));
+    if (o->precond == CR_PRECOND_CHEBYSHEV && o->prec != CR_PREC_FP64 && !h->chebf)
+        CR_TRY(h->arena.alloc_n(&h->chebf, 3 * n));
     double* Wd = W;
     const bool host = !is_device_pointer(W);
     if (host) {

@@ -59,6 +59,12 @@ int cuda_fail(cudaError_t e, const char* what);
 // Where an array argument lives: 1 device memory of the current GPU (or
 // managed memory), 0 host memory, -1 device memory of another GPU (*owner
 // receives that GPU).  is_device_pointer(p) is pointer_place(p) == 1.
+// place_of is the decision from the attributes the driver reports.
+inline int place_of(cudaMemoryType type, int owner, int current) {
+    if (type == cudaMemoryTypeManaged) return 1;
+    if (type != cudaMemoryTypeDevice) return 0;
+    return owner == current ? 1 : -1;
+}
 int pointer_place(const void* p, int* owner);
 bool is_device_pointer(const void* p);
 // Argument check of an entry point: the handle's mesh (may be NULL) was
@@ -180,6 +186,7 @@ struct cr_hybrid {
     float* Z32 = nullptr;         // GMRES scratch vector
     double* Z64 = nullptr;
     double* cheb = nullptr;       // Chebyshev preconditioner: z (two buffers), d [3][N], lmax slot
+    float2* chebf = nullptr;      // the same vectors in float-float [3][N]
     double cheb_lmax = -1.0;      // Gershgorin bound of M^{-1} G (computed on first use)
     double* fgz = nullptr;        // flexible GMRES: preconditioned vectors FP64 [restart][N]
     int fgz_m = 0;

@@ -379,6 +379,26 @@ __global__ void __launch_bounds__(kBlock) k_residual64(int64_t nf, const int32_t
                 sc->done = 1;
                 sc->status = CR_ERR_BREAKDOWN;
             }
+        } else if (mode == 3) {
+            // reliable update of the Chebyshev float-float PCG: the new scale; r.z of the
+            // last direction moved to the new scale's continuation (beta = r.z(new) /
+            // (r.z(old) sigma_new / sigma_old) gives p = z + beta_true (sigma_new/sigma_old) p)
+            const double rr = tot[0], bb = tot[1];
+            const double target = tol * tol * bb;
+            const double s_old = sc->sigma > 0.0 ? sc->sigma : 1.0;
+            const double s_new = rr > 0.0 && isfinite(rr) ? 1.0 / sqrt(rr) : s_old;
+            sc->bb = bb;
+            sc->rz = sc->rz * (s_new / s_old);
+            sc->rr = rr * s_new * s_new;
+            sc->tol2 = fmax(delta * delta * rr, 0.25 * target) * s_new * s_new;
+            sc->sigma = s_new;
+            sc->conv = (rr <= target) ? 1 : 0;
+            sc->done = sc->conv;
+            sc->status = CR_OK;
+            if (!isfinite(rr)) {
+                sc->done = 1;
+                sc->status = CR_ERR_BREAKDOWN;
+            }
         } else if (mode == 2) {
             const double rr = tot[0], bb = tot[1], rz = tot[2];
             const double target = tol * tol * bb;
@@ -634,6 +654,115 @@ __global__ void __launch_bounds__(kBlock) kf_dir(int64_t n, float2* __restrict__
         const float2 z = ff_mul1(minv[k], r[k]);
         p[k] = first ? z : ff_add(z, ff_mul(beta, p[k]));
     }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev-preconditioned CG in float-float (the FP64 form above with every
+// vector and matrix operation on the FP32 pipes; FP64 reliable updates as for
+// the Jacobi form).  Vectors carry the scale sigma of the last update.
+// ---------------------------------------------------------------------------
+
+// x += alpha p, r -= alpha q, r.r; then the first Chebyshev step z = d = M^{-1} r / theta.
+// Last block: iteration count, the reliable-update target (rr <= tol2), the limit.
+__global__ void __launch_bounds__(kBlock) kf_cpcg_update(int64_t n, float2* __restrict__ x, float2* __restrict__ r,
+                                                        const float2* __restrict__ p, const float2* __restrict__ q,
+                                                        const float* __restrict__ minv, float2* __restrict__ z,
+                                                        float2* __restrict__ d, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const float2 alpha = sc->alpha_ff;
+    const float2 c0 = ff_from_double(sc->cheb[0]);
+    FFAcc rr;
+    rr.zero();
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] = ff_add(x[k], ff_mul(alpha, p[k]));
+        const float2 rn = ff_add(r[k], ff_neg(ff_mul(alpha, q[k])));
+        r[k] = rn;
+        const float2 v = ff_mul(c0, ff_mul1(minv[k], rn));
+        z[k] = v;
+        d[k] = v;
+        rr.mad(rn.x, rn.y, rn.x, rn.y);
+    }
+    float2 part[1] = {rr.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->it += 1;
+        if (!isfinite(tot[0])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[0] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// z = d = M^{-1} r / theta (the first Chebyshev step after a reliable update)
+__global__ void __launch_bounds__(kBlock) kf_cheb_start(int64_t n, const float2* __restrict__ r,
+                                                       const float* __restrict__ minv, float2* __restrict__ z,
+                                                       float2* __restrict__ d, const KScal* sc) {
+    if (sc->done) return;
+    const float2 c0 = ff_from_double(sc->cheb[0]);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float2 v = ff_mul(c0, ff_mul1(minv[k], r[k]));
+        z[k] = v;
+        d[k] = v;
+    }
+}
+
+// Chebyshev step j: zout = zin + d_j, d_j = c1_j d + c2_j M^{-1} (r - G zin); on the
+// last step r.z and, in the last block, beta = r.z / r.z(previous).
+template <int D, typename LT>
+__global__ void __launch_bounds__(kBlock) kf_cheb_step(int64_t nf, const int32_t* __restrict__ cols,
+                                                      const float* __restrict__ vh, const LT* __restrict__ vl,
+                                                      const float* __restrict__ minv, const float2* __restrict__ r,
+                                                      const float2* __restrict__ zin, float2* __restrict__ zout,
+                                                      float2* __restrict__ d, KScal* sc, RedBuf red, int j, int last) {
+    if (sc->done) return;
+    const float2 c1 = ff_from_double(sc->cheb[2 * j - 1]), c2 = ff_from_double(sc->cheb[2 * j]);
+    FFAcc rz;
+    rz.zero();
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        float2 y[D];
+        ff_ell_row<D, LT>(f, cols, vh, vl, zin, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int64_t k = f * D + i;
+            const float2 rk = r[k];
+            const float2 res = ff_add(rk, ff_neg(y[i]));
+            const float2 dn = ff_add(ff_mul(c1, d[k]), ff_mul(c2, ff_mul1(minv[k], res)));
+            const float2 zn = ff_add(zin[k], dn);
+            d[k] = dn;
+            zout[k] = zn;
+            rz.mad(rk.x, rk.y, zn.x, zn.y);
+        }
+    }
+    if (!last) return;
+    float2 part[1] = {rz.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double rzn = tot[0];
+        if (!(rzn > 0.0) || !isfinite(rzn)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->rz_prev = sc->rz;
+            sc->beta = rzn / sc->rz;
+            sc->beta_ff = ff_from_double(sc->beta);
+            sc->rz = rzn;
+        }
+    }
+}
+
+// p = z + beta p   (first: p = z)
+__global__ void __launch_bounds__(kBlock) kf_cpcg_dir(int64_t n, float2* __restrict__ p, const float2* __restrict__ z,
+                                                     const KScal* sc, int first) {
+    if (sc->done) return;
+    const float2 beta = sc->beta_ff;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        p[k] = first ? z[k] : ff_add(z[k], ff_mul(beta, p[k]));
 }
 
 // x64 += x_ff / sigma; x_ff = 0   (the reliable update of the iterate)
@@ -1542,6 +1671,88 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
         c.hs->sigma = 1.0;
         CR_CUDA(cudaMemcpyAsync(&c.sc->sigma, &c.hs->sigma, sizeof(double), cudaMemcpyHostToDevice, c.st));
         CR_CUDA(cudaMemsetAsync(h->xf, 0, sizeof(float2) * c.n, c.st));
+        if (cheb) {
+            // Chebyshev-preconditioned CG in float-float: per iteration the SpMV (+ p.q),
+            // the update with the first Chebyshev step (+ r.r), degree - 1 Chebyshev steps
+            // (SpMV each; the last forms r.z and beta) and the direction.  Reliable updates
+            // as for the Jacobi form: the FP64 true residual, a new scale, and the
+            // direction continued with r.z moved to the new scale.
+            const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+            float2* zb[2] = {h->chebf, h->chebf + c.n};
+            float2* dv = h->chebf + 2 * c.n;
+            auto cheb_steps = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                if (e0) cudaEventRecord(e0, c.st);
+                for (int j = 1; j < deg; ++j) {
+                    if (bf)
+                        kf_cheb_step<D, __nv_bfloat16><<<ggrid, kBlock, 0, c.st>>>(
+                            c.nf, m->cols, h->val32, h->vlo16, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv, c.sc,
+                            h->red, j, j == deg - 1);
+                    else
+                        kf_cheb_step<D, float2><<<ggrid, kBlock, 0, c.st>>>(
+                            c.nf, m->cols, h->val32, h->vff, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv, c.sc,
+                            h->red, j, j == deg - 1);
+                }
+                if (e1) cudaEventRecord(e1, c.st);
+                c.launches += deg - 1;
+            };
+            auto restart_direction = [&](int first) {
+                kf_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zb[0], dv, c.sc);
+                ++c.launches;
+                cheb_steps(nullptr, nullptr);
+                kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
+                ++c.launches;
+            };
+            auto true_residual3 = [&](const double* x) {
+                k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x, h->r64, nullptr, h->minv64,
+                                                            c.sc, h->red, 3, o->tol, delta, h->minv32);
+                k_ff_from64<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->rf, c.sc);
+                c.launches += 2;
+            };
+            true_residual3(x0);
+            restart_direction(1);
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            if (c.hs->status == CR_ERR_BREAKDOWN) status = CR_ERR_BREAKDOWN;
+            double last_rr = c.hs->orr;
+            int it_mark = 0;
+            auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
+                const int g = grid_for(c.nf);
+                if (bf)
+                    kf_spmv<D, __nv_bfloat16><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->vlo16, h->pf, h->qf,
+                                                                      c.sc, h->red);
+                else
+                    kf_spmv<D, float2><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->vff, h->pf, h->qf, c.sc,
+                                                               h->red);
+                kf_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zb[0], dv, c.sc,
+                                                        h->red);
+                cheb_steps(e0, e1);
+                kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, 0);
+                c.launches += 3;
+            };
+            while (status == CR_OK && !c.hs->conv) {
+                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0)));
+                CR_TRY(read_scal(c));
+                const int dev_status = c.hs->status;
+                if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }
+                k_add_ff<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->xf, c.sc);
+                ++c.launches;
+                true_residual3(h->x64);
+                CR_CUDA(cudaGetLastError());
+                CR_TRY(read_scal(c));
+                ++outer;
+                if (trace)
+                    std::fprintf(stderr, "[crhyb] ff chebyshev update %d: it %d, true relres %.3e, status %d\n", outer,
+                                 c.hs->it, std::sqrt(c.hs->orr / c.hs->obb), dev_status);
+                it_mark = c.hs->it;
+                if (c.hs->status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+                if (c.hs->conv) break;
+                if (c.hs->it >= gmax) { status = CR_ERR_NOT_CONVERGED; break; }
+                if (c.hs->orr > 100.0 * last_rr) { status = CR_ERR_BREAKDOWN; break; }   // diverging
+                last_rr = c.hs->orr;
+                restart_direction(dev_status == CR_OK ? 0 : 1);
+                CR_CUDA(cudaGetLastError());
+            }
+        } else {
         // the reliable update: r64 = b - G x64 (FP64), new scale, r_ff = sigma r64
         auto true_residual = [&](const double* x) {
             k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x, h->r64, nullptr, h->minv64,
@@ -1587,6 +1798,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             kf_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, h->rf, h->minv32, c.sc, dev_status == CR_OK ? 0 : 1);
             ++c.launches;
             CR_CUDA(cudaGetLastError());
+        }
         }
     } else if (o->method == CR_METHOD_PCG) {
         // FP32 PCG (FP32 or BF16 matrix values) inside FP64 iterative

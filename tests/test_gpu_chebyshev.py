@@ -1,5 +1,5 @@
-"""The Chebyshev-preconditioned PCG of cr_solve (precond = CHEBYSHEV, FP64)
-against the CPU FP64 oracle.
+"""The Chebyshev-preconditioned PCG of cr_solve (precond = CHEBYSHEV; FP64, and
+float-float with FP64 reliable updates) against the CPU FP64 oracle.
 
 * W reaches the oracle's direct solve of G W = S (1e-9 relative L2 after a
   solve to a relative residual of 1e-12), in 2D and 3D, for several degrees
@@ -41,14 +41,16 @@ def case(name, n):
         G, S = h["G"].tocsr(), h["S"]
         mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
         fb = torch.from_numpy(p["fbar"]).cuda()
-        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False)
+        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
+                                 keep_ff=True, keep_ff_bf16=True)
         _CASES[(name, n)] = (G, S, spla.spsolve(G.tocsc(), S), mesh, hyb)
     return _CASES[(name, n)]
 
 
 def solve(hyb, **opts):
     W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
-    st = crhyb.cr_solve(hyb, W, method="pcg", prec="fp64", precond="chebyshev", **opts)
+    opts.setdefault("prec", "fp64")
+    st = crhyb.cr_solve(hyb, W, method="pcg", precond="chebyshev", **opts)
     return st, W.cpu().numpy()
 
 
@@ -66,6 +68,29 @@ def test_matches_the_oracle(name, n, degree, ratio):
     Wj = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
     stj = crhyb.cr_solve(hyb, Wj, method="pcg", prec="fp64", tol=1e-12)
     assert st["iterations"] < stj["iterations"]
+
+
+@pytest.mark.parametrize("prec,tol", [("ff", 1e-9), ("ff_bf16", 1e-8)])
+@pytest.mark.parametrize("name,n,degree,ratio", [("cfg2", 29, 4, 1000.0), ("cfg2", 29, 8, 300.0),
+                                                 ("cfg3", 4, 4, 100.0)])
+def test_float_float_matches_the_oracle(prec, tol, name, n, degree, ratio):
+    """The same Chebyshev PCG in float-float with FP64 reliable updates: W within the
+    parity tolerance of the direct solve, and about the oracle's CG iteration count
+    (the reliable updates continue the search direction)."""
+    G, S, ref, mesh, hyb = case(name, n)
+    st, W = solve(hyb, prec=prec, tol=1e-12, poly_degree=degree, poly_ratio=ratio, use_graph=True)
+    assert st["status"] == 0 and st["relres"] <= 1e-12 and st["outer"] >= 1
+    assert rel(W, ref) <= tol
+    _, it, _ = krylov.chebyshev_pcg(G, S, krylov.jacobi(G), degree, ratio, rtol=1e-12)
+    assert st["iterations"] <= 1.3 * it + 5, (st["iterations"], it)
+
+
+def test_float_float_graph_and_plain_agree():
+    G, S, ref, mesh, hyb = case("cfg2", 29)
+    st_g, W_g = solve(hyb, prec="ff", tol=1e-11, use_graph=True, check_every=5)
+    st_p, W_p = solve(hyb, prec="ff", tol=1e-11, use_graph=False, profile=True)
+    assert st_g["iterations"] == st_p["iterations"] and np.array_equal(W_g, W_p)
+    assert st_p["spmv_launches"] >= st_p["iterations"] - st_p["outer"] - 1 and st_p["spmv_ms"] > 0.0
 
 
 def test_graph_plain_and_persistent_flag_agree():
@@ -101,7 +126,7 @@ def test_zero_source_and_iteration_limit():
 def test_bad_options_are_refused():
     G, S, ref, mesh, hyb = case("cfg2", 29)
     W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
-    bad = [dict(prec="ff"), dict(method="gmres"), dict(poly_degree=1), dict(poly_degree=17),
+    bad = [dict(prec="mixed"), dict(method="gmres"), dict(poly_degree=1), dict(poly_degree=17),
            dict(poly_ratio=0.5), dict(poly_ratio=1.0)]
     for b in bad:
         o = {"method": "pcg", "prec": "fp64", "precond": "chebyshev", "tol": 1e-10, **b}

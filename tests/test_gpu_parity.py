@@ -460,9 +460,12 @@ def test_tiny_mesh_and_error_paths():
     W = np.zeros(hyb.n)
     st = crhyb.cr_solve(hyb, W, tol=1e-13, max_iter=5, raise_on_error=False)
     assert st["status"] == -4 and st["iterations"] == 5
-    # mu = 0 needs the independent set
-    with pytest.raises(crhyb.CrError):
-        crhyb.cr_assemble_coupled(mesh, 1.0, 0.0, fbar)
+    # the E_K elimination at mu = 0 needs the independent set M_1 (the steady coupled
+    # system itself does not: cr_solve_steady works on any mesh)
+    steady = crhyb.cr_assemble_coupled(mesh, 1.0, 0.0, fbar)
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_hybridise(steady)
+    assert ei.value.name == "CR_ERR_ARG"
 
 
 @pytest.mark.parametrize("prec,persistent", [("mixed", False), ("ff", False), ("ff", True), ("fp64", True)])
