@@ -110,8 +110,12 @@ def test_steady_at_128_and_256_matches_direct_solve(big_truths, conv, nu, mu_pre
 
 
 def test_outer_steps_do_not_grow_with_the_mesh():
-    steps = [gpu_steady(2, n, 1.0, "none", 30.0, tol=1e-10)[0]["outer"] for n in (32, 64, 128)]
-    assert max(steps) - min(steps) <= 3 and max(steps) <= 16, steps
+    """With accurate inner solves (1e-8) the outer count is that of the preconditioned
+    operator, whose eigenvalues lambda/(lambda + mu) do not depend on the mesh (oracle:
+    9 steps at 32, 64 and 128).  The default inner tolerance 1e-4 trades outer steps for
+    inner work (oracle and GPU: 10, 11, 23-24 steps, 40% fewer inner iterations at 128)."""
+    steps = [gpu_steady(2, n, 1.0, "none", 30.0, tol=1e-10, inner_tol=1e-8)[0]["outer"] for n in (32, 64, 128)]
+    assert max(steps) - min(steps) <= 2 and max(steps) <= 12, steps
 
 
 def test_steady_argument_errors():
