@@ -166,6 +166,11 @@ TRAFFIC = {
     # 164.43 GB and 168.86 GB read + written
     ("cfg3", "ff"): {"per": "iteration", "bytes": (164.431e9 + 168.859e9) / 2 / 64, "sources": "persist",
                      "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
+    # the float-float Chebyshev step: three launches each on the 64^3 and 512^2 workloads
+    ("cfg3", "ff_cheb"): {"per": "launch", "bytes": (2061583104 + 2060227584 + 2058483456) / 3, "sources": "solve",
+                          "sha256": "279fe1bfaefcecd8af5d2357e4929b379bc3f58a42bcbaefed53ad86273c56f2"},
+    ("cfg2", "ff_cheb"): {"per": "launch", "bytes": (186525184 + 184703488 + 183807232) / 3, "sources": "solve",
+                          "sha256": "279fe1bfaefcecd8af5d2357e4929b379bc3f58a42bcbaefed53ad86273c56f2"},
 }
 
 
