@@ -305,9 +305,13 @@ int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solv
  *   pre   hybridised on the same mesh handle, conv = NONE, mu > 0 (e.g. mu = 30
  *         for nu = 1, mu = 1 for nu = 0.01); its own S and W are untouched
  *   opts  method GMRES; prec: precision of the inner PCG (FP64, FF, FF_BF16;
- *         FF needs keep_lo_fp32 on pre); restart m (default 30); tol on the
- *         FP64 residual ||[R;0] - K_s [U;P]|| / ||R||; inner_tol: relative
- *         residual of each inner PCG (default 1e-4; an inner solve that
+ *         FF needs keep_lo_fp32 on pre); precond: JACOBI (inner solves by the
+ *         persistent Jacobi-PCG) or CHEBYSHEV (the Chebyshev-preconditioned PCG
+ *         of cr_solve, poly_degree and poly_ratio as there); restart m (default
+ *         30); tol on the FP64 residual ||[R;0] - K_s [U;P]|| / ||R||;
+ *         inner_tol: relative residual of each inner PCG (default 1e-6; looser
+ *         inner solves cost fewer inner iterations on small meshes but let the
+ *         outer steps stall from about 384x384 squares on; an inner solve that
  *         stagnates stops at four times the iterations of the first one);
  *         max_iter caps the GMRES steps (default 1000); use_x0: U, P hold the
  *         start; check_every x 64 inner iterations per persistent launch

@@ -465,8 +465,13 @@ extern "C" int cr_solve_steady(cr_system* sys, cr_hybrid* pre, int rhs, const cr
     if (!(pre->s->mu > 0.0) || pre->s->conv != CR_CONV_NONE)
         return fail(CR_ERR_ARG, "cr_solve_steady: pre needs a transient Stokes system (mu > 0, b_h = 0), whose G is SPD");
     if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_steady: the outer method is (flexible) GMRES");
-    if (o->precond != CR_PRECOND_JACOBI)
-        return fail(CR_ERR_ARG, "cr_solve_steady: the inner PCG is Jacobi-preconditioned");
+    if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
+        return fail(CR_ERR_ARG, "cr_solve_steady: bad preconditioner of the inner PCG");
+    if (o->precond == CR_PRECOND_CHEBYSHEV) {
+        const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+        if (deg < 2 || deg > CR_MAX_POLY_DEGREE || !(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
+            return fail(CR_ERR_ARG, "cr_solve_steady: bad poly_degree or poly_ratio");
+    }
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve_steady: the inner PCG runs in FP64, FF or FF_BF16");
     if ((o->prec == CR_PREC_FF && !pre->vff) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
@@ -480,6 +485,11 @@ extern "C" int cr_solve_steady(cr_system* sys, cr_hybrid* pre, int rhs, const cr
     cr_mesh* m = sys->m;
     StreamScope scope(m);
     CR_TRY(ensure_workspace(pre, false, 0, o->prec));
+    if (o->precond == CR_PRECOND_CHEBYSHEV) {
+        const size_t n = size_t(m->nf) * m->d;
+        if (!pre->cheb) CR_TRY(pre->arena.alloc_n(&pre->cheb, 3 * n + 1));
+        if (o->prec != CR_PREC_FP64 && !pre->chebf) CR_TRY(pre->arena.alloc_n(&pre->chebf, 3 * n));
+    }
     if (!sys->steady_op) CR_TRY(coupled_build(sys, &sys->steady_op, false));
     return solve_steady_impl(sys->steady_op, m, pre, rhs, o, U, P, st);
 }

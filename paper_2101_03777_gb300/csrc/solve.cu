@@ -1544,13 +1544,15 @@ int chebyshev_setup(cr_hybrid* h, const cr_solve_opts* o, cudaStream_t st, KScal
 }
 
 template <int D>
-int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st,
+              const double* b_override = nullptr) {
     cr_mesh* m = h->m;
     Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D,
           o->profile != 0};
     h->prof_ms = 0.0;
     h->prof_n = 0;
-    const double* b = h->S + size_t(rhs) * c.n;
+    // the right-hand side: S of h, or (inner solves of the steady preconditioner) a given vector
+    const double* b = b_override ? b_override : h->S + size_t(rhs) * c.n;
     const int chunk = o->check_every > 0 ? o->check_every : 16;
     const bool graph = o->use_graph != 0;
     const int gmax = o->max_iter > 0 ? o->max_iter : 100000;
@@ -1929,7 +1931,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
 // Flexible GMRES(m) (Saad, Algorithm 9.6) on the steady coupled system
 // K_s [U; P] = [R; 0] (Eq. 10 with mu = 0), right-preconditioned by the
 // transient Stokes step of `pre` (mu_pre > 0): z = K_mu^{-1} [v; g] is one
-// hybridised solve (persistent PCG on G_mu to inner_tol, FP64 or float-float)
+// hybridised solve (PCG on G_mu to inner_tol, FP64 or float-float: the
+// persistent Jacobi-PCG, or the Chebyshev-preconditioned PCG)
 // whose right-hand side is the previous level v / (mu m) with no source and
 // the divergence g per simplex, followed by the element-wise recovery.  The Arnoldi vectors, the minimised
 // residual and the update x += Z y are those of K_s, so the result is the
@@ -1967,7 +1970,8 @@ int solve_steady(cr_coupled* cpl, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_
     Ctx cp{pre, s, static_cast<KScal*>(pre->scal), static_cast<KScal*>(pre->h_scal), m->nf, N, D, false};
     const int g = grid_for(n), gN = grid_for(N);
     const int mode = persistent_mode(o->prec);
-    const double itol = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : 1e-4;
+    const double itol = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : 1e-6;
+    const bool cheb_inner = o->precond == CR_PRECOND_CHEBYSHEV;
     const int gmax = o->max_iter > 0 ? o->max_iter : 1000;
     const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
     const double mu = pre->s->mu;
@@ -2016,21 +2020,44 @@ int solve_steady(cr_coupled* cpl, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_
                 const double* gdiv = w.V + size_t(j) * n + N;   // the divergence block of v_j
                 CR_TRY(launch_rhs_previous(pre, w.up, gdiv, w.spart, w.S, s));
                 c.launches += 2;
-                PScal Pst{};
-                double kms = 0.0;
-                int64_t kit = 0;
                 // an inner solve that stagnates above inner_tol (its attainable accuracy) stops at
                 // four times the first one's iterations; the flexible outer step takes what it returns
-                CR_TRY(persistent_pcg<D>(cp, w.S, nullptr, w.W, mode, itol, default_delta(mode), inner_cap,
-                                         per_launch, o->profile != 0, &Pst, &kms, &kit));
+                int inner_it = 0, inner_status = CR_OK;
+                if (cheb_inner) {
+                    // Chebyshev-preconditioned PCG (multi-kernel, graph-replayed) on G_mu
+                    cr_solve_opts io = *o;
+                    io.method = CR_METHOD_PCG;
+                    io.tol = itol;
+                    io.max_iter = inner_cap;
+                    io.use_x0 = 0;
+                    io.use_graph = o->profile ? 0 : 1;
+                    io.persistent = 0;
+                    io.inner_tol = 0.0;
+                    cr_solve_stats ist{};
+                    const int rc = solve_dim<D>(pre, 0, &io, w.W, &ist, w.S);
+                    if (rc != CR_OK && rc != CR_ERR_NOT_CONVERGED && rc != CR_ERR_BREAKDOWN) return rc;
+                    inner_it = ist.iterations;
+                    inner_status = ist.status;
+                    cp.launches += ist.kernel_launches;
+                    prof_ms += ist.spmv_ms;
+                    prof_it += ist.spmv_launches;
+                } else {
+                    PScal Pst{};
+                    double kms = 0.0;
+                    int64_t kit = 0;
+                    CR_TRY(persistent_pcg<D>(cp, w.S, nullptr, w.W, mode, itol, default_delta(mode), inner_cap,
+                                             per_launch, o->profile != 0, &Pst, &kms, &kit));
+                    inner_it = Pst.it;
+                    inner_status = Pst.status;
+                    prof_ms += kms;
+                    prof_it += kit;
+                }
                 if (first_inner < 0) {
-                    first_inner = Pst.it;
+                    first_inner = inner_it;
                     inner_cap = int(std::min<int64_t>(int64_t(4) * std::max(first_inner, 64), 1000000));
                 }
-                inner_its += Pst.it;
-                prof_ms += kms;
-                prof_it += kit;
-                if (Pst.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+                inner_its += inner_it;
+                if (inner_status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
                 CR_TRY(launch_recover_previous(pre, w.up, gdiv, w.W, z, z + N, s));
                 ++c.launches;
                 // v_{j+1} = K_s z_j, orthogonalised (CGS2) and normalised
