@@ -114,7 +114,7 @@ def supported_precs(workload, precs, steady=False):
     inner solves of a steady step; the batch and the transient Newton step keep their
     Jacobi-preconditioned solvers."""
     if workload == "cfg4" or (workload == "cfg5" and not steady):
-        return ",".join(x for x in precs.split(",") if x and x not in ("fp64_cheb", "ff_cheb")) or "ff"
+        return ",".join(x for x in precs.split(",") if x and x not in CHEB_PRECS) or "ff"
     return precs
 
 
@@ -150,7 +150,21 @@ PRECS = {
     "ff_cheb": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01), 8, 8,
                 "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
                 "of degree 4 (interval ratio 1000 in 2D, 100 in 3D), graph-replayed kernels"),
+    "ff_cheb32": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01,
+                       poly_prec="fp32"), 4, 4,
+                  "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
+                  "of degree 4 whose steps run in FP32 on the FP32 values of G (interval ratio 1000 in 2D, 100 in "
+                  "3D), graph-replayed kernels"),
+    "ff_chebbf": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01,
+                       poly_prec="bf16"), 2, 4,
+                  "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
+                  "of degree 4 whose steps run in FP32 on BF16 values of G (interval ratio 1000 in 2D, 100 in 3D), "
+                  "graph-replayed kernels"),
 }
+CHEB_PRECS = ("fp64_cheb", "ff_cheb", "ff_cheb32", "ff_chebbf")
+# bytes per unknown that a Chebyshev step moves besides its SpMV: r read, d read and written,
+# the Jacobi scale read
+CHEB_EXTRA = {"fp64_cheb": 4 * 8, "ff_cheb": 3 * 8 + 4, "ff_cheb32": 8 + 2 * 4 + 4, "ff_chebbf": 8 + 2 * 4 + 4}
 CHEB_RATIO = {2: 1000.0, 3: 100.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel of a
@@ -198,9 +212,13 @@ def measured_traffic(workload, prec):
 
 SPMV_KERNEL = {"fp64": "k_pcg_spmv<FP64>", "ff": "kf_spmv<float-float>", "ff_bf16": "kf_spmv<float+bf16>",
                "mixed": "k_pcg_spmv<FP32>", "fp64_cheb": "k_cheb_step<FP64> (SpMV + Chebyshev update)",
-               "ff_cheb": "kf_cheb_step<float-float> (SpMV + Chebyshev update)"}
+               "ff_cheb": "kf_cheb_step<float-float> (SpMV + Chebyshev update)",
+               "ff_cheb32": "k32_cheb_step<float> (FP32 SpMV + Chebyshev update)",
+               "ff_chebbf": "k32_cheb_step<bf16> (BF16-value SpMV + Chebyshev update)"}
 DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-float; G low part bf16)",
-         "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64", "ff_cheb": "f32x2 (float-float)"}
+         "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64", "ff_cheb": "f32x2 (float-float)",
+         "ff_cheb32": "f32x2 (float-float CG; f32 preconditioner steps)",
+         "ff_chebbf": "f32x2 (float-float CG; f32 preconditioner steps on bf16 values)"}
 
 
 def solve_opts(prec, tol, graph, profile, persistent):
@@ -426,12 +444,15 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         if newton and p["mu"] == 0.0:
             # the steady Newton step: flexible GMRES on its coupled system, each step
             # preconditioned by a transient Stokes solve (SPD G, persistent PCG)
-            pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], args.mu_pre, fb), keep_fp32=False,
-                                     keep_ff=(prec in ("ff", "ff_cheb")), keep_ff_bf16=(prec == "ff_bf16"))
+            pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], args.mu_pre, fb),
+                                     keep_fp32=(prec == "ff_cheb32"), keep_bf16=(prec == "ff_chebbf"),
+                                     keep_ff=(prec in ("ff", "ff_cheb", "ff_cheb32", "ff_chebbf")),
+                                     keep_ff_bf16=(prec == "ff_bf16"))
             o = dict(tol=args.tol, prec=PRECS[prec][0]["prec"], profile=profile, check_every=args.check_every,
                      restart=60)
-            if prec.endswith("_cheb"):
-                o.update(precond="chebyshev", poly_degree=PRECS[prec][0]["poly_degree"], poly_ratio=CHEB_RATIO[d])
+            if prec in CHEB_PRECS:
+                o.update(precond="chebyshev", poly_degree=PRECS[prec][0]["poly_degree"], poly_ratio=CHEB_RATIO[d],
+                         poly_prec=PRECS[prec][0].get("poly_prec", "same"))
             if args.max_iter:
                 o["max_iter"] = args.max_iter
             # the steady solve writes device arrays: the end-to-end run copies them to its host buffers
@@ -454,8 +475,9 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             st = crhyb.cr_solve_preconditioned(hyb, pre, Wt, raise_on_error=not args.max_iter, **o)
             crhyb.cr_recover_up(hyb, Wt, Ut, Pt, normalise_p=True)
             return st
-        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_bf16=False,
-                                 keep_ff=(prec in ("ff", "ff_cheb")), keep_ff_bf16=(prec == "ff_bf16"))
+        hyb = crhyb.cr_hybridise(system, keep_fp32=(prec in ("mixed", "ff_cheb32")), keep_bf16=(prec == "ff_chebbf"),
+                                 keep_ff=(prec in ("ff", "ff_cheb", "ff_cheb32", "ff_chebbf")),
+                                 keep_ff_bf16=(prec == "ff_bf16"))
         o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
         o["check_every"] = args.check_every
         if o.get("precond") == "chebyshev":
@@ -555,11 +577,11 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         st_main, st_spmv = prof[prec]
         solver = PRECS[prec][3]
         spmv = None
-        if st_spmv is not None and prec in ("fp64_cheb", "ff_cheb"):
+        if st_spmv is not None and prec in CHEB_PRECS:
             # the Chebyshev steps: degree - 1 launches per CG iteration, each the SpMV over G fused
             # with the vector update (reads r, d, M^{-1}; writes d and the other z buffer)
             deg = PRECS[prec][0]["poly_degree"]
-            step_bytes = spmv_bytes + 3 * N * xb + N * (8 if prec == "fp64_cheb" else 4)
+            step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nit = max(st_spmv["spmv_launches"], 1)
             ms = st_spmv["spmv_ms"] / (nit * (deg - 1))
             tb, tnote = measured_traffic(workload, prec)
@@ -577,10 +599,10 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                     "peak": hbm_peak, "unit": "GB/s", "frac": spmv_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
                     "bytes_per_launch": spmv_bytes, "avg_launch_ms": ms, "launches_timed": nl,
                     "peak_note": peak_note}
-        if newton and prec.endswith("_cheb"):
+        if newton and prec in CHEB_PRECS:
             # steady step with Chebyshev inner solves: the Chebyshev steps of the inner PCG dominate
             deg = PRECS[prec][0]["poly_degree"]
-            step_bytes = spmv_bytes + 3 * N * xb + N * (8 if prec == "fp64_cheb" else 4)
+            step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nl = max(st_main["spmv_launches"], 1) * (deg - 1)
             ms = st_main["spmv_ms"] / nl
             roof = {"kernel": SPMV_KERNEL[prec] + " (inner Stokes solves)", "bound": "hbm",
@@ -609,7 +631,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             else:
                 solver = ("flexible GMRES(30) in FP64 on the Newton system, each step preconditioned by an inner "
                           f"{solver} on the transient Stokes G of the same mesh to relative residual 0.1")
-        elif prec in ("fp64_cheb", "ff_cheb"):
+        elif prec in CHEB_PRECS:
             roof = dict(spmv)
         elif args.persistent:
             # the persistent PCG kernel: per iteration the SpMV plus the vector phases (the update

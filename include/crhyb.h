@@ -151,7 +151,17 @@ typedef struct cr_solve_opts {
                            cr_solve_batched take Jacobi only */
     int32_t poly_degree;/* CHEBYSHEV: polynomial degree, 2..CR_MAX_POLY_DEGREE (0 selects 4) */
     double poly_ratio;  /* CHEBYSHEV: lmax / (lower end of the interval), > 1 (<= 0 selects 100) */
+    int32_t poly_prec;  /* CHEBYSHEV with prec FF or FF_BF16: the arithmetic of the Chebyshev steps
+                           (the preconditioner only; the CG keeps its precision and its FP64 reliable
+                           updates).  enum cr_poly_prec: SAME (the CG's), FP32 (FP32 values of G,
+                           kept with keep_fp32 or keep_lo_bf16, FP32 vectors and FMAs), BF16 (BF16
+                           values, kept with keep_bf16, FP32 vectors).  A polynomial in M^{-1} G~
+                           for the rounded, still symmetric G~ is a fixed symmetric positive definite
+                           operator under the same Gershgorin bound, so CG keeps its guarantees up to
+                           the FP32 rounding of the steps, which the reliable updates absorb */
 } cr_solve_opts;
+
+enum cr_poly_prec { CR_POLY_SAME = 0, CR_POLY_FP32 = 1, CR_POLY_BF16 = 2 };
 
 #define CR_MAX_RESTART 64
 

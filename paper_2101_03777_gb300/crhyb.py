@@ -27,6 +27,7 @@ CONV = {"none": 0, "newton": 1, "oseen": 2}
 PREC = {"fp64": 0, "mixed": 1, "mixed_fp32": 1, "mixed_bf16": 2, "ff": 3, "ff_bf16": 4}
 METHOD = {"pcg": 0, "gmres": 1, "bicgstab": 2}
 PRECOND = {"jacobi": 0, "chebyshev": 1}
+POLY_PREC = {"same": 0, "fp32": 1, "bf16": 2}
 CR_MAX_RESTART = 64
 
 
@@ -58,7 +59,8 @@ class cr_solve_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("poly_degree", ctypes.c_int32), ("poly_ratio", ctypes.c_double)]
+                ("precond", ctypes.c_int32), ("poly_degree", ctypes.c_int32), ("poly_ratio", ctypes.c_double),
+                ("poly_prec", ctypes.c_int32)]
 
 
 class cr_batch_opts(ctypes.Structure):
@@ -309,11 +311,11 @@ def cr_hybrid_export(hyb):
 
 def make_solve_opts(method="pcg", prec="fp64", tol=1e-10, max_iter=100000, restart=30, inner_tol=0.0,
                     max_outer=60, use_x0=False, check_every=16, use_graph=False, profile=False, persistent=False,
-                    precond="jacobi", poly_degree=0, poly_ratio=0.0):
+                    precond="jacobi", poly_degree=0, poly_ratio=0.0, poly_prec="same"):
     return cr_solve_opts(METHOD[method], PREC[prec], float(tol), int(max_iter), int(restart), float(inner_tol),
                          int(max_outer), int(bool(use_x0)), int(check_every), int(bool(use_graph)),
                          int(bool(profile)), int(bool(persistent)), PRECOND[precond], int(poly_degree),
-                         float(poly_ratio))
+                         float(poly_ratio), POLY_PREC[poly_prec])
 
 
 def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):

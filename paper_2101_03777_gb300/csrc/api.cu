@@ -380,6 +380,10 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
             return fail(CR_ERR_ARG, "cr_solve: poly_degree must be in [2, CR_MAX_POLY_DEGREE]");
         if (!(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
             return fail(CR_ERR_ARG, "cr_solve: poly_ratio must be > 1 (or <= 0 for the default)");
+        if (o->poly_prec != CR_POLY_SAME && o->poly_prec != CR_POLY_FP32 && o->poly_prec != CR_POLY_BF16)
+            return fail(CR_ERR_ARG, "cr_solve: bad poly_prec");
+        if (o->poly_prec != CR_POLY_SAME && o->prec == CR_PREC_FP64)
+            return fail(CR_ERR_ARG, "cr_solve: poly_prec applies to the float-float Chebyshev PCG");
     }
     cr_mesh* m = h->m;
     const size_t n = size_t(m->nf) * m->d;

@@ -765,6 +765,113 @@ __global__ void __launch_bounds__(kBlock) kf_cpcg_dir(int64_t n, float2* __restr
         p[k] = first ? z[k] : ff_add(z[k], ff_mul(beta, p[k]));
 }
 
+// The same preconditioner with its Chebyshev steps in FP32 (FP32 or BF16 values
+// of G, FP32 z and d): a fixed polynomial in M^{-1} G~ for the rounded G~, which
+// stays positive near 0 and below the Gershgorin bound, so the preconditioner is
+// symmetric positive definite; the CG around it stays in float-float.
+
+// x += alpha p, r -= alpha q, r.r (float-float); z = d = M^{-1} r / theta (FP32).
+__global__ void __launch_bounds__(kBlock) kf_cpcg_update32(int64_t n, float2* __restrict__ x, float2* __restrict__ r,
+                                                          const float2* __restrict__ p, const float2* __restrict__ q,
+                                                          const float* __restrict__ minv, float* __restrict__ z,
+                                                          float* __restrict__ d, KScal* sc, RedBuf red) {
+    if (sc->done) return;
+    const float2 alpha = sc->alpha_ff;
+    const float c0 = float(sc->cheb[0]);
+    FFAcc rr;
+    rr.zero();
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        x[k] = ff_add(x[k], ff_mul(alpha, p[k]));
+        const float2 rn = ff_add(r[k], ff_neg(ff_mul(alpha, q[k])));
+        r[k] = rn;
+        const float v = c0 * minv[k] * (rn.x + rn.y);
+        z[k] = v;
+        d[k] = v;
+        rr.mad(rn.x, rn.y, rn.x, rn.y);
+    }
+    float2 part[1] = {rr.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->it += 1;
+        if (!isfinite(tot[0])) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else if (tot[0] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= sc->max_it) {
+            sc->status = CR_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) kf_cheb_start32(int64_t n, const float2* __restrict__ r,
+                                                         const float* __restrict__ minv, float* __restrict__ z,
+                                                         float* __restrict__ d, const KScal* sc) {
+    if (sc->done) return;
+    const float c0 = float(sc->cheb[0]);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float v = c0 * minv[k] * (r[k].x + r[k].y);
+        z[k] = v;
+        d[k] = v;
+    }
+}
+
+// Chebyshev step j in FP32 on the FP32 (or BF16) values of G; the last step forms
+// r.z in float-float and beta = r.z / r.z(previous).
+template <int D, typename VT>
+__global__ void __launch_bounds__(kBlock) k32_cheb_step(int64_t nf, const int32_t* __restrict__ cols,
+                                                       const VT* __restrict__ vals, const float* __restrict__ minv,
+                                                       const float2* __restrict__ r, const float* __restrict__ zin,
+                                                       float* __restrict__ zout, float* __restrict__ d, KScal* sc,
+                                                       RedBuf red, int j, int last) {
+    if (sc->done) return;
+    const float c1 = float(sc->cheb[2 * j - 1]), c2 = float(sc->cheb[2 * j]);
+    FFAcc rz;
+    rz.zero();
+    for (int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < nf; f += int64_t(gridDim.x) * blockDim.x) {
+        float y[D];
+        ell_row<D, VT, float, float>(f, cols, vals, zin, y);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int64_t k = f * D + i;
+            const float2 rk = r[k];
+            const float dn = fmaf(c1, d[k], c2 * minv[k] * ((rk.x + rk.y) - y[i]));
+            const float zn = zin[k] + dn;
+            d[k] = dn;
+            zout[k] = zn;
+            if (last) rz.mad(rk.x, rk.y, zn, 0.f);
+        }
+    }
+    if (!last) return;
+    float2 part[1] = {rz.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double rzn = tot[0];
+        if (!(rzn > 0.0) || !isfinite(rzn)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->rz_prev = sc->rz;
+            sc->beta = rzn / sc->rz;
+            sc->beta_ff = ff_from_double(sc->beta);
+            sc->rz = rzn;
+        }
+    }
+}
+
+// p = z + beta p (float-float p, FP32 z)
+__global__ void __launch_bounds__(kBlock) kf_cpcg_dir32(int64_t n, float2* __restrict__ p, const float* __restrict__ z,
+                                                       const KScal* sc, int first) {
+    if (sc->done) return;
+    const float2 beta = sc->beta_ff;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float2 zk = make_float2(z[k], 0.f);
+        p[k] = first ? zk : ff_add(zk, ff_mul(beta, p[k]));
+    }
+}
+
 // x64 += x_ff / sigma; x_ff = 0   (the reliable update of the iterate)
 __global__ void __launch_bounds__(kBlock) k_add_ff(int64_t n, double* __restrict__ x, float2* __restrict__ d,
                                                   const KScal* sc) {
@@ -1682,10 +1789,24 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
             float2* zb[2] = {h->chebf, h->chebf + c.n};
             float2* dv = h->chebf + 2 * c.n;
+            // reduced-precision steps (poly_prec): FP32 z (two buffers) and d in the same storage
+            const int pp = o->poly_prec;
+            float* zs[2] = {reinterpret_cast<float*>(h->chebf), reinterpret_cast<float*>(h->chebf) + c.n};
+            float* ds = reinterpret_cast<float*>(h->chebf) + 2 * c.n;
+            if ((pp == CR_POLY_FP32 && !h->val32) || (pp == CR_POLY_BF16 && !h->val16))
+                return fail(CR_ERR_ARG, "cr_solve: the values for poly_prec were not kept by cr_hybridise");
             auto cheb_steps = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 if (e0) cudaEventRecord(e0, c.st);
                 for (int j = 1; j < deg; ++j) {
-                    if (bf)
+                    if (pp == CR_POLY_FP32)
+                        k32_cheb_step<D, float><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->minv32, h->rf,
+                                                                           zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red,
+                                                                           j, j == deg - 1);
+                    else if (pp == CR_POLY_BF16)
+                        k32_cheb_step<D, __nv_bfloat16><<<ggrid, kBlock, 0, c.st>>>(
+                            c.nf, m->cols, h->val16, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red, j,
+                            j == deg - 1);
+                    else if (bf)
                         kf_cheb_step<D, __nv_bfloat16><<<ggrid, kBlock, 0, c.st>>>(
                             c.nf, m->cols, h->val32, h->vlo16, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv, c.sc,
                             h->red, j, j == deg - 1);
@@ -1698,10 +1819,13 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 c.launches += deg - 1;
             };
             auto restart_direction = [&](int first) {
-                kf_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zb[0], dv, c.sc);
+                if (pp != CR_POLY_SAME) kf_cheb_start32<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zs[0], ds, c.sc);
+                else kf_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zb[0], dv, c.sc);
                 ++c.launches;
                 cheb_steps(nullptr, nullptr);
-                kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
+                if (pp != CR_POLY_SAME)
+                    kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, first);
+                else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
                 ++c.launches;
             };
             auto true_residual3 = [&](const double* x) {
@@ -1725,14 +1849,20 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 else
                     kf_spmv<D, float2><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->vff, h->pf, h->qf, c.sc,
                                                                h->red);
-                kf_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zb[0], dv, c.sc,
-                                                        h->red);
+                if (pp != CR_POLY_SAME)
+                    kf_cpcg_update32<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zs[0], ds,
+                                                              c.sc, h->red);
+                else
+                    kf_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zb[0], dv,
+                                                            c.sc, h->red);
                 cheb_steps(e0, e1);
-                kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, 0);
+                if (pp != CR_POLY_SAME)
+                    kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, 0);
+                else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, 0);
                 c.launches += 3;
             };
             while (status == CR_OK && !c.hs->conv) {
-                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0)));
+                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp));
                 CR_TRY(read_scal(c));
                 const int dev_status = c.hs->status;
                 if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }

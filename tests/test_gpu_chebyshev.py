@@ -41,8 +41,8 @@ def case(name, n):
         G, S = h["G"].tocsr(), h["S"]
         mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
         fb = torch.from_numpy(p["fbar"]).cuda()
-        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
-                                 keep_ff=True, keep_ff_bf16=True)
+        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=True,
+                                 keep_bf16=True, keep_ff=True, keep_ff_bf16=True)
         _CASES[(name, n)] = (G, S, spla.spsolve(G.tocsc(), S), mesh, hyb)
     return _CASES[(name, n)]
 
@@ -83,6 +83,21 @@ def test_float_float_matches_the_oracle(prec, tol, name, n, degree, ratio):
     assert rel(W, ref) <= tol
     _, it, _ = krylov.chebyshev_pcg(G, S, krylov.jacobi(G), degree, ratio, rtol=1e-12)
     assert st["iterations"] <= 1.3 * it + 5, (st["iterations"], it)
+
+
+@pytest.mark.parametrize("poly_prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("name,n,ratio", [("cfg2", 29, 1000.0), ("cfg3", 4, 100.0)])
+def test_reduced_precision_preconditioner_steps(poly_prec, name, n, ratio):
+    """The Chebyshev steps in FP32 on FP32 or BF16 values of G (the preconditioner
+    only): W still reaches the direct solve at the float-float tolerance, and the CG
+    iteration count stays near the oracle's FP64 count (the polynomial of the rounded
+    G is still a symmetric positive definite preconditioner)."""
+    G, S, ref, mesh, hyb = case(name, n)
+    st, W = solve(hyb, prec="ff", tol=1e-12, poly_degree=4, poly_ratio=ratio, poly_prec=poly_prec, use_graph=True)
+    assert st["status"] == 0 and st["relres"] <= 1e-12
+    assert rel(W, ref) <= 1e-9
+    _, it, _ = krylov.chebyshev_pcg(G, S, krylov.jacobi(G), 4, ratio, rtol=1e-12)
+    assert st["iterations"] <= 1.5 * it + 5, (st["iterations"], it)
 
 
 def test_float_float_graph_and_plain_agree():
@@ -127,6 +142,7 @@ def test_bad_options_are_refused():
     G, S, ref, mesh, hyb = case("cfg2", 29)
     W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
     bad = [dict(prec="mixed"), dict(method="gmres"), dict(poly_degree=1), dict(poly_degree=17),
+           dict(poly_prec="fp32"),   # reduced-precision steps apply to the float-float PCG only
            dict(poly_ratio=0.5), dict(poly_ratio=1.0)]
     for b in bad:
         o = {"method": "pcg", "prec": "fp64", "precond": "chebyshev", "tol": 1e-10, **b}
