@@ -11,9 +11,10 @@ Metric: time to solution (seconds per step, lower is better), mixed precision
 against FP64.  The default workload is the 3D transient Stokes problem on 64^3
 cubes (1,572,864 Kuhn tetrahedra, 9.4 M unknowns, nu = 1, dt = 1e-3).  `value`
 is the first solver of --precs (by default PCG in float-float with FP64
-reliable updates and the Chebyshev polynomial preconditioner of degree 4);
-every timed solver (that one, float-float Jacobi-PCG, native FP64 Jacobi-PCG,
-float-float with BF16 low parts, Chebyshev-preconditioned FP64 PCG) is reported
+reliable updates and the Chebyshev polynomial preconditioner of degree 4, its
+steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
+and float-float variants, float-float and native FP64 Jacobi-PCG, the FP64
+Chebyshev PCG, float-float with BF16 low parts) is reported
 under "precisions" with its roofline and its speed-up over FP64 Jacobi-PCG,
 and the FP32 PCG inside FP64 refinement is attempted once with a bounded
 iteration budget and its exit reported.  The 2D 512x512 workload follows
@@ -72,8 +73,8 @@ def parse():
     ap.add_argument("--persistent", type=int, default=1, help="PCG in one cooperative persistent launch")
     ap.add_argument("--precs", default=None,
                     help="comma-separated solvers to time, the first is the headline (default: "
-                         "ff_cheb,fp64_cheb,ff,fp64,ff_bf16 in 2D; ff_cheb,ff,fp64,ff_bf16,fp64_cheb for cfg3; "
-                         "ff for cfg4, cfg5)")
+                         "ff_chebbf,ff_cheb32,ff_cheb,fp64_cheb,ff,fp64,ff_bf16 in 2D; "
+                         "ff_chebbf,ff_cheb32,ff_cheb,ff,fp64,fp64_cheb,ff_bf16 for cfg3; ff for cfg4, cfg5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=30)
@@ -102,11 +103,15 @@ def parse():
 
 
 def default_precs(workload):
-    """The fastest measured solver of each workload first: the Chebyshev-preconditioned PCG
-    in float-float (four times fewer CG iterations, every SpMV on the FP32 pipes), then
-    float-float and FP64 Jacobi-PCG in the persistent kernel, the BF16-low-part variant and
-    the FP64 Chebyshev PCG (whose SpMV is bound by the FP64 pipe)."""
-    return "ff_cheb,ff,fp64,ff_bf16,fp64_cheb" if workload == "cfg3" else "ff_cheb,fp64_cheb,ff,fp64,ff_bf16"
+    """The fastest measured solver of each workload first: float-float PCG with the
+    Chebyshev preconditioner whose steps run in FP32 on BF16 values of G (four times fewer
+    CG iterations; the preconditioner's bytes cut to a third), then the same with FP32
+    values and with float-float steps, float-float and FP64 Jacobi-PCG in the persistent
+    kernel, the FP64 Chebyshev PCG (whose SpMV is bound by the FP64 pipe) and the
+    BF16-low-part Jacobi variant."""
+    if workload == "cfg3":
+        return "ff_chebbf,ff_cheb32,ff_cheb,ff,fp64,fp64_cheb,ff_bf16"
+    return "ff_chebbf,ff_cheb32,ff_cheb,fp64_cheb,ff,fp64,ff_bf16"
 
 
 def supported_precs(workload, precs, steady=False):

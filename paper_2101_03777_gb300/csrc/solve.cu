@@ -24,6 +24,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <string>
 
 #include "device_common.cuh"
@@ -68,6 +70,35 @@ int grid_for(int64_t n) {
     }
     const int64_t want = (n + kBlock - 1) / kBlock;
     const int64_t cap = int64_t(g_num_sms) * 8;   // 8 resident 256-thread blocks per SM
+    return int(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// Grid of a grid-stride kernel over n rows: one row per thread, capped at the
+// blocks that all SMs hold at once for this kernel (its occupancy), so that a
+// kernel whose registers allow fewer than 8 resident blocks per SM runs in one
+// wave instead of a full wave and a partial one.
+template <typename K>
+int grid_occ(K kernel, int64_t n) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> per_sm_of;
+    if (g_num_sms == 0) grid_for(1);
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = per_sm_of.find(reinterpret_cast<const void*>(kernel));
+        if (it != per_sm_of.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 0;
+            }
+            if (per_sm <= 0 || per_sm > 8) per_sm = 8;
+            per_sm_of[reinterpret_cast<const void*>(kernel)] = per_sm;
+        }
+    }
+    const int64_t want = (n + kBlock - 1) / kBlock;
+    const int64_t cap = int64_t(g_num_sms) * per_sm;
     return int(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -1724,7 +1755,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             auto cheb_steps = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 if (e0) cudaEventRecord(e0, c.st);
                 for (int j = 1; j < deg; ++j)
-                    k_cheb_step<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->minv64, h->r64,
+                    k_cheb_step<D><<<grid_occ(k_cheb_step<D>, c.nf), kBlock, 0, c.st>>>(c.nf, m->cols, h->val64,
+                                                                                       h->minv64, h->r64,
                                                                zb[(j - 1) & 1], zb[j & 1], dv, c.sc, h->red, j,
                                                                j == deg - 1);
                 if (e1) cudaEventRecord(e1, c.st);
@@ -1738,7 +1770,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 ++c.launches;
             };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
-                k_pcg_spmv<D, double, double><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->p64, h->q64,
+                k_pcg_spmv<D, double, double><<<grid_occ(k_pcg_spmv<D, double, double>, c.nf), kBlock, 0, c.st>>>(
+                    c.nf, m->cols, h->val64, h->p64, h->q64,
                                                                           c.sc, h->red);
                 k_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->p64, h->q64, h->minv64, zb[0], dv,
                                                        c.sc, h->red);
@@ -1799,19 +1832,21 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e0) cudaEventRecord(e0, c.st);
                 for (int j = 1; j < deg; ++j) {
                     if (pp == CR_POLY_FP32)
-                        k32_cheb_step<D, float><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->minv32, h->rf,
-                                                                           zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red,
-                                                                           j, j == deg - 1);
-                    else if (pp == CR_POLY_BF16)
-                        k32_cheb_step<D, __nv_bfloat16><<<ggrid, kBlock, 0, c.st>>>(
-                            c.nf, m->cols, h->val16, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red, j,
+                        k32_cheb_step<D, float><<<grid_occ(k32_cheb_step<D, float>, c.nf), kBlock, 0, c.st>>>(
+                            c.nf, m->cols, h->val32, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red, j,
                             j == deg - 1);
+                    else if (pp == CR_POLY_BF16)
+                        k32_cheb_step<D, __nv_bfloat16>
+                            <<<grid_occ(k32_cheb_step<D, __nv_bfloat16>, c.nf), kBlock, 0, c.st>>>(
+                                c.nf, m->cols, h->val16, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc,
+                                h->red, j, j == deg - 1);
                     else if (bf)
-                        kf_cheb_step<D, __nv_bfloat16><<<ggrid, kBlock, 0, c.st>>>(
-                            c.nf, m->cols, h->val32, h->vlo16, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv, c.sc,
-                            h->red, j, j == deg - 1);
+                        kf_cheb_step<D, __nv_bfloat16>
+                            <<<grid_occ(kf_cheb_step<D, __nv_bfloat16>, c.nf), kBlock, 0, c.st>>>(
+                                c.nf, m->cols, h->val32, h->vlo16, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv,
+                                c.sc, h->red, j, j == deg - 1);
                     else
-                        kf_cheb_step<D, float2><<<ggrid, kBlock, 0, c.st>>>(
+                        kf_cheb_step<D, float2><<<grid_occ(kf_cheb_step<D, float2>, c.nf), kBlock, 0, c.st>>>(
                             c.nf, m->cols, h->val32, h->vff, h->minv32, h->rf, zb[(j - 1) & 1], zb[j & 1], dv, c.sc,
                             h->red, j, j == deg - 1);
                 }
@@ -1842,13 +1877,12 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
             double last_rr = c.hs->orr;
             int it_mark = 0;
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
-                const int g = grid_for(c.nf);
                 if (bf)
-                    kf_spmv<D, __nv_bfloat16><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->vlo16, h->pf, h->qf,
-                                                                      c.sc, h->red);
+                    kf_spmv<D, __nv_bfloat16><<<grid_occ(kf_spmv<D, __nv_bfloat16>, c.nf), kBlock, 0, c.st>>>(
+                        c.nf, m->cols, h->val32, h->vlo16, h->pf, h->qf, c.sc, h->red);
                 else
-                    kf_spmv<D, float2><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val32, h->vff, h->pf, h->qf, c.sc,
-                                                               h->red);
+                    kf_spmv<D, float2><<<grid_occ(kf_spmv<D, float2>, c.nf), kBlock, 0, c.st>>>(
+                        c.nf, m->cols, h->val32, h->vff, h->pf, h->qf, c.sc, h->red);
                 if (pp != CR_POLY_SAME)
                     kf_cpcg_update32<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zs[0], ds,
                                                               c.sc, h->red);

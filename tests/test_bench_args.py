@@ -1,8 +1,8 @@
 """bench.py's choice of solvers per workload (host logic, no GPU).
 
 The headline (first) solver is the fastest measured one of each workload:
-the Chebyshev-preconditioned float-float PCG on the single-system Stokes
-workloads, and the Jacobi-preconditioned solvers of the batch and the
+the Chebyshev-preconditioned float-float PCG (its preconditioner steps in FP32
+on BF16 values) on the single-system Stokes workloads, and the Jacobi-preconditioned solvers of the batch and the
 Newton step, which do not take the Chebyshev preconditioner.  Also the
 host-side rules of a bench line: the default workload, the rejection of a step
 that missed the tolerance, and the DRAM traffic reported only for the kernel
@@ -24,7 +24,7 @@ def parse(monkeypatch, *argv):
     return bench.parse()
 
 
-@pytest.mark.parametrize("workload,head", [("cfg2", "ff_cheb"), ("cfg1", "ff_cheb"), ("cfg3", "ff_cheb"),
+@pytest.mark.parametrize("workload,head", [("cfg2", "ff_chebbf"), ("cfg1", "ff_chebbf"), ("cfg3", "ff_chebbf"),
                                            ("cfg4", "ff"), ("cfg5", "ff")])
 def test_default_headline_per_workload(monkeypatch, workload, head):
     args = parse(monkeypatch, "--workload", workload)
@@ -32,7 +32,7 @@ def test_default_headline_per_workload(monkeypatch, workload, head):
     assert precs[0] == head
     assert all(p in bench.PRECS for p in precs)
     if workload in ("cfg4", "cfg5"):
-        assert "fp64_cheb" not in precs and "ff_cheb" not in precs
+        assert not set(precs) & set(bench.CHEB_PRECS)
 
 
 def test_explicit_list_is_kept_except_where_unsupported(monkeypatch):
@@ -47,7 +47,7 @@ def test_defaults_meet_the_timing_rules(monkeypatch):
     Jacobi-PCG among the timed solvers and the 2D 512^2 workload timed after it."""
     args = parse(monkeypatch)
     assert args.gpus == 1 and args.warmup >= 3 and args.steps >= 1
-    assert args.workload == "cfg3" and args.precs.split(",")[0] == "ff_cheb"
+    assert args.workload == "cfg3" and args.precs.split(",")[0] == "ff_chebbf"
     assert "fp64" in args.precs.split(",") and args.tol == 1e-10
     assert args.also == ["cfg2"] and args.mixed_attempt == 1
     o = bench.PRECS["fp64_cheb"][0]
