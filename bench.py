@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--mixed-attempt", type=int, default=1,
                     help="attempt FP32 PCG inside FP64 refinement once (bounded) and report its exit")
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--poly-degree", type=int, default=0,
+                    help="Chebyshev solvers: degree of the polynomial preconditioner (default 4)")
+    ap.add_argument("--poly-ratio", type=float, default=0.0,
+                    help="Chebyshev solvers: ratio of the interval's ends (default 1000 in 2D, 100 in 3D)")
     ap.add_argument("--graph", type=int, default=1, help="multi-kernel path: replay iteration chunks as graphs")
     ap.add_argument("--persistent", type=int, default=1, help="PCG in one cooperative persistent launch")
     ap.add_argument("--precs", default=None,
@@ -170,44 +174,94 @@ CHEB_PRECS = ("fp64_cheb", "ff_cheb", "ff_cheb32", "ff_chebbf")
 # bytes per unknown that a Chebyshev step moves besides its SpMV: r read, d read and written,
 # the Jacobi scale read
 CHEB_EXTRA = {"fp64_cheb": 4 * 8, "ff_cheb": 3 * 8 + 4, "ff_cheb32": 8 + 2 * 4 + 4, "ff_chebbf": 8 + 2 * 4 + 4}
+
 CHEB_RATIO = {2: 1000.0, 3: 100.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
+
+
+def cheb_degree(args, prec):
+    """Degree of the Chebyshev preconditioner of solver `prec` in this run."""
+    return getattr(args, "poly_degree", 0) or PRECS[prec][0]["poly_degree"]
+
+
+def cheb_ratio(args, d):
+    """Interval ratio of the Chebyshev preconditioner in this run (dimension d)."""
+    return getattr(args, "poly_ratio", 0.0) or CHEB_RATIO[d]
+
+
+def solver_text(args, prec, d):
+    """The solver's description with the degree and ratio of this run."""
+    text = PRECS[prec][3]
+    if prec in CHEB_PRECS:
+        text = text.replace("of degree 4", f"of degree {cheb_degree(args, prec)}")
+        if getattr(args, "poly_ratio", 0.0):
+            text = text.replace("interval ratio 1000 in 2D, 100 in 3D", f"interval ratio {cheb_ratio(args, d):g}")
+    return text
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel of a
 # solver, from one ncu capture: bytes per CG iteration (the persistent kernel) or per launch
-# (k_cheb_step).  Each entry records the SHA-256 of the kernel's source files when it was
-# captured; the bench reports it only while those files are unchanged, else null.
+# (the Chebyshev steps).  Each entry records the SHA-256 of the kernel's source (whole files,
+# or the kernel's own section of a file between two marker lines) when it was captured; the
+# bench reports it only while that source is unchanged, else null.
 KERNEL_SOURCES = {
     "persist": ["persist.cu", "persist.h", "ff.cuh", "device_common.cuh"],
-    "solve": ["solve.cu", "ff.cuh", "device_common.cuh"],
+    "cheb_ff": [("solve.cu", "// Chebyshev step j: zout = zin + d_j, d_j = c1_j d + c2_j M^{-1} (r - G zin); on the",
+                 "// p = z + beta p   (first: p = z)"), "ff.cuh", "device_common.cuh"],
+    "cheb_rows2": [("solve.cu", "// ---- the FP32-step Chebyshev kernel, two rows per thread ----",
+                    "// ---- the FP32-step Chebyshev kernel on slices staged in shared memory ----"),
+                   "ff.cuh", "device_common.cuh"],
+    "cheb_staged": [("solve.cu", "// ---- the FP32-step Chebyshev kernel on slices staged in shared memory ----",
+                     "// Which form of the FP32 Chebyshev step runs"), "ff.cuh", "device_common.cuh"],
 }
 TRAFFIC = {
-    # (workload, solver): {"per": "iteration" | "launch", "bytes": B, "sources": key, "sha256": digest}
+    # (workload, solver, kernel form or None): {"per": "iteration" | "launch", "bytes": B,
+    # "sources": key, "sha256": digest}
     # the persistent float-float kernel on the 64^3 workload: two launches of 64 iterations,
     # 164.43 GB and 168.86 GB read + written
-    ("cfg3", "ff"): {"per": "iteration", "bytes": (164.431e9 + 168.859e9) / 2 / 64, "sources": "persist",
-                     "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
-    # the float-float Chebyshev step: three launches each on the 64^3 and 512^2 workloads
-    ("cfg3", "ff_cheb"): {"per": "launch", "bytes": (2061583104 + 2060227584 + 2058483456) / 3, "sources": "solve",
-                          "sha256": "279fe1bfaefcecd8af5d2357e4929b379bc3f58a42bcbaefed53ad86273c56f2"},
-    ("cfg2", "ff_cheb"): {"per": "launch", "bytes": (186525184 + 184703488 + 183807232) / 3, "sources": "solve",
-                          "sha256": "279fe1bfaefcecd8af5d2357e4929b379bc3f58a42bcbaefed53ad86273c56f2"},
+    ("cfg3", "ff", None): {"per": "iteration", "bytes": (164.431e9 + 168.859e9) / 2 / 64, "sources": "persist",
+                           "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
+    # the FP32 Chebyshev step on BF16 values: three launches each on the 64^3 and 512^2
+    # workloads, read + written
+    ("cfg3", "ff_chebbf", "staged"): {
+        "per": "launch", "bytes": (655519232 + 65823744 + 655515648 + 63299328 + 655502848 + 62904064) / 3,
+        "sources": "cheb_staged", "sha256": "d34bb5e8d04d3b18ed131a58267950ba89cf11291a7f35ae2fbf9d1e046423b6"},
+    ("cfg2", "ff_chebbf", "staged"): {
+        "per": "launch", "bytes": (75429376 + 1369856 + 75426560 + 44032 + 75427584 + 100864) / 3,
+        "sources": "cheb_staged", "sha256": "d34bb5e8d04d3b18ed131a58267950ba89cf11291a7f35ae2fbf9d1e046423b6"},
+    ("cfg3", "ff_chebbf", "rows2"): {
+        "per": "launch", "bytes": (655517184 + 47112448 + 655496704 + 44532736 + 655502592 + 44279296) / 3,
+        "sources": "cheb_rows2", "sha256": "f8ad74ed6aaa33a0b42db85c86ff8cd8f66766b3e52c5d1003ef7c1f609922b5"},
+    ("cfg2", "ff_chebbf", "rows2"): {
+        "per": "launch", "bytes": (75431424 + 1131776 + 75428096 + 68864 + 75427840 + 38144) / 3,
+        "sources": "cheb_rows2", "sha256": "f8ad74ed6aaa33a0b42db85c86ff8cd8f66766b3e52c5d1003ef7c1f609922b5"},
 }
 
 
 def sources_sha(key):
-    """SHA-256 over the named source files of the CUDA library, in order."""
+    """SHA-256 over the named sources of the CUDA library, in order: a file name stands for
+    the whole file, (file, start, end) for its text from the start marker up to the end
+    marker (None if a marker is missing)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[key]:
-        with open(os.path.join(ROOT, "paper_2101_03777_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        name = f if isinstance(f, str) else f[0]
+        with open(os.path.join(ROOT, "paper_2101_03777_gb300", "csrc", name), "rb") as fh:
+            data = fh.read()
+        if not isinstance(f, str):
+            i = data.find(f[1].encode())
+            j = data.find(f[2].encode(), i + 1) if i >= 0 else -1
+            if i < 0 or j < 0:
+                return None
+            data = data[i:j]
+        h.update(data)
     return h.hexdigest()
 
 
-def measured_traffic(workload, prec):
+def measured_traffic(workload, prec, form=None):
     """(bytes, per) from the capture table, or (None, reason) when there is no capture of
-    this kernel build."""
-    t = TRAFFIC.get((workload, prec))
+    this kernel build (form: the Chebyshev step kernel's form, for the FP32-step solvers)."""
+    t = TRAFFIC.get((workload, prec, form))
     if not t:
         return None, "no ncu capture of this kernel on this workload"
     if sources_sha(t["sources"]) != t["sha256"]:
@@ -224,6 +278,25 @@ DTYPE = {"fp64": "f64", "ff": "f32x2 (float-float)", "ff_bf16": "f32x2 (float-fl
          "mixed": "f32 (f64 refinement)", "fp64_cheb": "f64", "ff_cheb": "f32x2 (float-float)",
          "ff_cheb32": "f32x2 (float-float CG; f32 preconditioner steps)",
          "ff_chebbf": "f32x2 (float-float CG; f32 preconditioner steps on bf16 values)"}
+
+
+def cheb_form(d, prec):
+    """Form of the FP32 Chebyshev step kernel (rows1, rows2, staged) the library runs for
+    solver `prec` on a d-dimensional mesh, or None for the other solvers."""
+    pp = PRECS[prec][0].get("poly_prec")
+    if pp not in ("fp32", "bf16"):
+        return None
+    from paper_2101_03777_gb300 import crhyb
+    return crhyb.cr_chebyshev_step_form(d, pp)
+
+
+def kernel_label(d, prec):
+    """Name of the dominant kernel of solver `prec`, with the step kernel's form."""
+    form = cheb_form(d, prec)
+    if not form:
+        return SPMV_KERNEL[prec]
+    name = {"rows1": "k32_cheb_step", "rows2": "k32_cheb_step2", "staged": "k32_cheb_step_staged"}[form]
+    return SPMV_KERNEL[prec].replace("k32_cheb_step", name, 1)
 
 
 def solve_opts(prec, tol, graph, profile, persistent):
@@ -456,7 +529,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             o = dict(tol=args.tol, prec=PRECS[prec][0]["prec"], profile=profile, check_every=args.check_every,
                      restart=60)
             if prec in CHEB_PRECS:
-                o.update(precond="chebyshev", poly_degree=PRECS[prec][0]["poly_degree"], poly_ratio=CHEB_RATIO[d],
+                o.update(precond="chebyshev", poly_degree=cheb_degree(args, prec), poly_ratio=cheb_ratio(args, d),
                          poly_prec=PRECS[prec][0].get("poly_prec", "same"))
             if args.max_iter:
                 o["max_iter"] = args.max_iter
@@ -486,7 +559,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
         o["check_every"] = args.check_every
         if o.get("precond") == "chebyshev":
-            o["poly_ratio"] = CHEB_RATIO[d]
+            o["poly_ratio"] = cheb_ratio(args, d)
+            o["poly_degree"] = cheb_degree(args, prec)
         if args.max_iter:
             o["max_iter"] = args.max_iter
         if extra:
@@ -580,20 +654,23 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         vb, xb = PRECS[prec][1], PRECS[prec][2]
         spmv_bytes, blocks, nnz = algorithmic_spmv_bytes(fe, nf, d, vb, xb)
         st_main, st_spmv = prof[prec]
-        solver = PRECS[prec][3]
+        solver = solver_text(args, prec, d)
         spmv = None
         if st_spmv is not None and prec in CHEB_PRECS:
             # the Chebyshev steps: degree - 1 launches per CG iteration, each the SpMV over G fused
             # with the vector update (reads r, d, M^{-1}; writes d and the other z buffer)
-            deg = PRECS[prec][0]["poly_degree"]
+            deg = cheb_degree(args, prec)
             step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nit = max(st_spmv["spmv_launches"], 1)
             ms = st_spmv["spmv_ms"] / (nit * (deg - 1))
-            tb, tnote = measured_traffic(workload, prec)
-            spmv = {"kernel": SPMV_KERNEL[prec], "bound": "hbm", "achieved": step_bytes / (ms * 1e-3) / 1e9,
+            form = cheb_form(d, prec)
+            tb, tnote = measured_traffic(workload, prec, form)
+            spmv = {"kernel": kernel_label(d, prec), "bound": "hbm", "achieved": step_bytes / (ms * 1e-3) / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
                     "traffic": tb, "bytes_per_launch": step_bytes, "avg_launch_ms": ms,
                     "launches_timed": nit * (deg - 1), "peak_note": peak_note}
+            if form:
+                spmv["form"] = form
             if tb is None:
                 spmv["traffic_note"] = tnote
         elif st_spmv is not None:
@@ -606,11 +683,11 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                     "peak_note": peak_note}
         if newton and prec in CHEB_PRECS:
             # steady step with Chebyshev inner solves: the Chebyshev steps of the inner PCG dominate
-            deg = PRECS[prec][0]["poly_degree"]
+            deg = cheb_degree(args, prec)
             step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nl = max(st_main["spmv_launches"], 1) * (deg - 1)
             ms = st_main["spmv_ms"] / nl
-            roof = {"kernel": SPMV_KERNEL[prec] + " (inner Stokes solves)", "bound": "hbm",
+            roof = {"kernel": kernel_label(d, prec) + " (inner Stokes solves)", "bound": "hbm",
                     "achieved": step_bytes / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
                     "bytes_per_launch": step_bytes, "avg_launch_ms": ms, "launches_timed": nl,

@@ -268,6 +268,21 @@ int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S)
  * CR_ERR_CUDA. */
 int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st);
 
+/* Which form of the reduced-precision Chebyshev step kernel (poly_prec FP32 or
+ * BF16) cr_solve runs on a dim-dimensional mesh.  An introspection call of the
+ * library; the paper has no counterpart.  Every form computes the same step
+ * (the SpMV of G on z fused with d <- c1 d + c2 M^{-1}(r - G z), z <- z + d), each
+ * face row's sums in the same order:
+ *   0  one face row per thread;
+ *   1  two adjacent face rows per thread (paired value and column loads);
+ *   2  one slice of the sliced ELL per block, its values and columns copied into
+ *      shared memory by TMA bulk copies (cp.async.bulk) while the rows' own
+ *      vector entries load.
+ * The default depends on dim and poly_prec; the environment variable
+ * CRHYB_CHEB_KERNEL (rows1, rows2, staged), read once per process, overrides it.
+ * Returns the form, or CR_ERR_ARG (dim not 2 or 3, poly_prec not FP32 or BF16). */
+int cr_chebyshev_step_form(int dim, int poly_prec);
+
 /* Solve G W = S (right-hand side `rhs` of h) by flexible GMRES(m) in FP64
  * (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.6), right-
  * preconditioned by an inner Jacobi-PCG solve with the SPD matrix G_pre of

@@ -116,6 +116,7 @@ _SIGS = {
     "cr_destroy_batch": (None, [_vp]),
     "cr_residual_noalloc": (_i32, [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cr_residual_noalloc_max_rows": (_i64, []),
+    "cr_chebyshev_step_form": (_i32, [ctypes.c_int, ctypes.c_int]),
     "cr_last_error": (ctypes.c_char_p, []),
 }
 EXPORTED = tuple(_SIGS)
@@ -492,6 +493,18 @@ def cr_solve_batched(batch, Ws, raise_on_error=True, **opts):
     if rc != CR_OK and raise_on_error:
         _check(rc)
     return out
+
+
+CHEB_STEP_FORMS = ("rows1", "rows2", "staged")
+
+
+def cr_chebyshev_step_form(dim, poly_prec):
+    """Name of the Chebyshev step kernel form cr_solve runs for FP32/BF16 steps:
+    'rows1' (one face row per thread), 'rows2' (two) or 'staged' (slices staged in
+    shared memory by TMA bulk copies)."""
+    rc = load_library().cr_chebyshev_step_form(int(dim), POLY_PREC[poly_prec])
+    _check(rc if rc < 0 else 0)
+    return CHEB_STEP_FORMS[rc]
 
 
 def cr_residual_noalloc_max_rows():

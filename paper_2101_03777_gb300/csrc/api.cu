@@ -157,6 +157,12 @@ using namespace crhyb;
 
 extern "C" const char* cr_last_error(void) { return g_last_error.c_str(); }
 
+extern "C" int cr_chebyshev_step_form(int dim, int poly_prec) {
+    if ((dim != 2 && dim != 3) || (poly_prec != CR_POLY_FP32 && poly_prec != CR_POLY_BF16))
+        return fail(CR_ERR_ARG, "cr_chebyshev_step_form: dim must be 2 or 3 and poly_prec FP32 or BF16");
+    return cheb_step_form_impl(dim, poly_prec);
+}
+
 // ---------------------------------------------------------------------------
 extern "C" int cr_assemble_coupled(cr_mesh* m, const cr_params* p, const double* fbar, int nrhs, const double* w,
                                    cr_system** out, double* blocks_out) {

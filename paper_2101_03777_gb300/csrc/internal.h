@@ -237,6 +237,7 @@ int solve_steady_impl(cr_coupled* c, cr_mesh* m, cr_hybrid* pre, int rhs, const 
                       double* P, cr_solve_stats* st);
 int solve_newton_impl(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin, double ntol,
                       int maxn, double* U, double* P, cr_newton_stats* st);
+int cheb_step_form_impl(int d, int poly_prec);
 void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 

@@ -892,6 +892,311 @@ __global__ void __launch_bounds__(kBlock) k32_cheb_step(int64_t nf, const int32_
     }
 }
 
+// ---- the FP32-step Chebyshev kernel, two rows per thread ----
+//
+// Every thread takes two adjacent rows: two independent gather chains, and one
+// load instruction for the values (and for the columns) of both rows, which are
+// adjacent in every plane of the sliced ELL.
+
+// values of rows f and f+1 (f even) of one plane, as FP32
+__device__ __forceinline__ float2 ld_val2(const float* p) { return __ldcs(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 ld_val2(const __nv_bfloat16* p) {
+    const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(p));
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// The Chebyshev step of k32_cheb_step on rows (2t, 2t+1) per thread.  The rows
+// of the last slice beyond nf hold zero values and column 0 (in bounds); their
+// vectors are neither read nor written.
+template <int D, typename VT>
+__global__ void __launch_bounds__(kBlock) k32_cheb_step2(int64_t nf, const int32_t* __restrict__ cols,
+                                                        const VT* __restrict__ vals, const float* __restrict__ minv,
+                                                        const float2* __restrict__ r, const float* __restrict__ zin,
+                                                        float* __restrict__ zout, float* __restrict__ d, KScal* sc,
+                                                        RedBuf red, int j, int last) {
+    if (sc->done) return;
+    constexpr int NS = 2 * D + 1, NPL = NS * D * D;
+    const float c1 = float(sc->cheb[2 * j - 1]), c2 = float(sc->cheb[2 * j]);
+    FFAcc rz;
+    rz.zero();
+    const int64_t npair = (nf + 1) / 2;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < npair; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t f0 = 2 * t;
+        const bool two = f0 + 1 < nf;
+        float y0[D], y1[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) y0[i] = y1[i] = 0.f;
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+            int64_t c0 = f0, cb = f0 + 1;
+            if (sl > 0) {
+                const int2 cc = __ldcs(reinterpret_cast<const int2*>(cols + sell(f0, sl - 1, 2 * D)));
+                c0 = cc.x;
+                cb = cc.y;
+            }
+            if (!two) cb = c0;   // the padding row: any in-bounds column, its values are 0
+            float x0[D], x1[D];
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) {
+                x0[jj] = __ldg(zin + c0 * D + jj);
+                x1[jj] = __ldg(zin + cb * D + jj);
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) {
+                    const float2 v = ld_val2(vals + sell(f0, (sl * D + i) * D + jj, NPL));
+                    y0[i] = fmaf(v.x, x0[jj], y0[i]);
+                    y1[i] = fmaf(v.y, x1[jj], y1[i]);
+                }
+        }
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
+            if (row == 1 && !two) break;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int64_t k = (f0 + row) * D + i;
+                const float2 rk = r[k];
+                const float yi = row == 0 ? y0[i] : y1[i];
+                const float dn = fmaf(c1, d[k], c2 * minv[k] * ((rk.x + rk.y) - yi));
+                const float zn = zin[k] + dn;
+                d[k] = dn;
+                zout[k] = zn;
+                if (last) rz.mad(rk.x, rk.y, zn, 0.f);
+            }
+        }
+    }
+    if (!last) return;
+    float2 part[1] = {rz.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double rzn = tot[0];
+        if (!(rzn > 0.0) || !isfinite(rzn)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->rz_prev = sc->rz;
+            sc->beta = rzn / sc->rz;
+            sc->beta_ff = ff_from_double(sc->beta);
+            sc->rz = rzn;
+        }
+    }
+}
+
+// ---- the FP32-step Chebyshev kernel on slices staged in shared memory ----
+//
+// Every block takes whole slices of the sliced ELL (256 rows, one row per
+// thread) and has the TMA engine copy the slice's values and
+// columns (one contiguous run each) into shared memory with cp.async.bulk,
+// completion counted in bytes on one mbarrier.  The rows' own vector entries
+// are loaded while the copy runs; only the gathers of z at the neighbours stay
+// per-thread global loads.  A slice of an array starts at a multiple of 256 rows
+// times 2-8 bytes per entry, so both copies are 16-byte aligned and a multiple of
+// 16 bytes long; the last slice is copied whole (its rows beyond nf are zero).
+constexpr long long kStageWaitLimit = 1ll << 22;   // bounded mbarrier waits
+
+template <int D, typename VT>
+struct ChebStage {
+    static constexpr int NPL = (2 * D + 1) * D * D, NC = 2 * D;
+    static constexpr uint32_t VB = uint32_t(NPL) * kSlice * sizeof(VT);   // bytes of a slice's values
+    static constexpr uint32_t CB = uint32_t(NC) * kSlice * 4;             // bytes of its columns
+    static constexpr uint32_t SMEM = VB + CB + 16;                        // + the mbarrier
+    static_assert(VB % 16 == 0 && CB % 16 == 0, "bulk copies are whole 16-byte units");
+};
+
+__device__ __forceinline__ uint32_t cta_smem(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool stage_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(cta_smem(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool stage_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (long long n = 0; n < kStageWaitLimit; ++n)
+        if (stage_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ float smem_val(const float* p) { return *p; }
+__device__ __forceinline__ float smem_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <int D, typename VT>
+__global__ void __launch_bounds__(kBlock) k32_cheb_step_staged(int64_t nf, const int32_t* __restrict__ cols,
+                                                              const VT* __restrict__ vals,
+                                                              const float* __restrict__ minv,
+                                                              const float2* __restrict__ r,
+                                                              const float* __restrict__ zin, float* __restrict__ zout,
+                                                              float* __restrict__ d, KScal* sc, RedBuf red, int j,
+                                                              int last) {
+    static_assert(kBlock == kSlice, "one row of the slice per thread");
+    if (sc->done) return;
+    using G = ChebStage<D, VT>;
+    constexpr int NS = 2 * D + 1;
+    extern __shared__ __align__(128) unsigned char stage[];
+    const VT* sv = reinterpret_cast<const VT*>(stage);
+    const int32_t* scol = reinterpret_cast<const int32_t*>(stage + G::VB);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(stage + G::VB + G::CB);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cta_smem(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const float c1 = float(sc->cheb[2 * j - 1]), c2 = float(sc->cheb[2 * j]);
+    FFAcc rz;
+    rz.zero();
+    const int64_t nsl = (nf + kSlice - 1) / kSlice;
+    uint32_t parity = 0;
+    for (int64_t sl = blockIdx.x; sl < nsl; sl += gridDim.x) {
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cta_smem(bar)),
+                         "r"(G::VB + G::CB)
+                         : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads before the new writes
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                             "r"(cta_smem(stage)),
+                         "l"(vals + size_t(sl) * G::NPL * kSlice), "r"(G::VB), "r"(cta_smem(bar))
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                             "r"(cta_smem(stage + G::VB)),
+                         "l"(cols + size_t(sl) * G::NC * kSlice), "r"(G::CB), "r"(cta_smem(bar))
+                         : "memory");
+        }
+        const int64_t f = sl * kSlice + tid;
+        const bool act = f < nf;
+        float2 rk[D];
+        float mk[D], dk[D], zk[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int64_t k = act ? f * D + i : 0;
+            rk[i] = r[k];
+            mk[i] = minv[k];
+            dk[i] = d[k];
+            zk[i] = zin[k];
+        }
+        const bool ok = stage_wait_bounded(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // the copies never completed: wait (bounded) once more so that none is
+            // left in flight, report the time-out and leave the sweep
+            if (tid == 0) {
+                stage_wait_bounded(bar, parity ^ 1u);
+                sc->status = CR_ERR_TIMEOUT;
+                sc->done = 1;
+            }
+            break;
+        }
+        if (act) {
+            float y[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int64_t c = s == 0 ? f : int64_t(scol[(s - 1) * kSlice + tid]);
+                float xv[D];
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) xv[jj] = __ldg(zin + c * D + jj);
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < D; ++jj)
+                        y[i] = fmaf(smem_val(sv + ((s * D + i) * D + jj) * kSlice + tid), xv[jj], y[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int64_t k = f * D + i;
+                const float dn = fmaf(c1, dk[i], c2 * mk[i] * ((rk[i].x + rk[i].y) - y[i]));
+                const float zn = zk[i] + dn;
+                d[k] = dn;
+                zout[k] = zn;
+                if (last) rz.mad(rk[i].x, rk[i].y, zn, 0.f);
+            }
+        }
+        __syncthreads();   // every read of this slice ends before the next copy overwrites it
+    }
+    if (!last) return;
+    float2 part[1] = {rz.result()};
+    double tot[1];
+    if (ff_grid_sum<1>(part, red, tot) && threadIdx.x == 0) {
+        const double rzn = tot[0];
+        if (sc->status == CR_ERR_TIMEOUT) return;
+        if (!(rzn > 0.0) || !isfinite(rzn)) {
+            sc->status = CR_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->rz_prev = sc->rz;
+            sc->beta = rzn / sc->rz;
+            sc->beta_ff = ff_from_double(sc->beta);
+            sc->rz = rzn;
+        }
+    }
+}
+
+// Grid of the staged kernel: resident blocks per SM (shared memory and registers)
+// x SMs, at most one block per slice; the first call per instantiation raises the
+// kernel's dynamic shared-memory limit (it runs before any graph capture).
+template <int D, typename VT>
+int staged_grid(int64_t nf) {
+    static std::once_flag once;
+    static int per_sm = 1;
+    std::call_once(once, [] {
+        auto kern = k32_cheb_step_staged<D, VT>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ChebStage<D, VT>::SMEM)) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, ChebStage<D, VT>::SMEM) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        if (per_sm <= 0) per_sm = 1;
+        if (per_sm > 8) per_sm = 8;
+    });
+    if (g_num_sms == 0) grid_for(1);
+    const int64_t want = (nf + kSlice - 1) / kSlice, cap = int64_t(g_num_sms) * per_sm;
+    return int(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// Which form of the FP32 Chebyshev step runs: 2 staged, 1 two rows per thread,
+// 0 one row per thread.  Defaults, from timing each form on GB300 (2D 512^2 and
+// 3D 64^3 meshes): staged for BF16 values (its slice, 32 KB in 3D, leaves five
+// blocks per SM); for FP32 values, whose slice leaves three, two rows per thread
+// in 3D and one in 2D.  The environment variable CRHYB_CHEB_KERNEL (staged,
+// rows2, rows1) overrides the default for a process.
+int cheb32_form(int d, bool bf16) {
+    static const int forced = [] {
+        const char* e = std::getenv("CRHYB_CHEB_KERNEL");
+        if (e && !std::strcmp(e, "staged")) return 2;
+        if (e && !std::strcmp(e, "rows2")) return 1;
+        if (e && !std::strcmp(e, "rows1")) return 0;
+        return -1;
+    }();
+    if (forced >= 0) return forced;
+    return bf16 ? 2 : (d == 3 ? 1 : 0);
+}
+
+// One FP32 Chebyshev step on FP32 or BF16 values, in the form cheb32_form() names.
+template <int D, typename VT>
+void launch_cheb32(int64_t nf, const int32_t* cols, const VT* vals, const float* minv, const float2* r,
+                   const float* zin, float* zout, float* d, KScal* sc, RedBuf red, int j, int last, cudaStream_t st) {
+    const int form = cheb32_form(D, std::is_same<VT, __nv_bfloat16>::value);
+    if (form == 2)
+        k32_cheb_step_staged<D, VT><<<staged_grid<D, VT>(nf), kBlock, ChebStage<D, VT>::SMEM, st>>>(
+            nf, cols, vals, minv, r, zin, zout, d, sc, red, j, last);
+    else if (form == 1)
+        k32_cheb_step2<D, VT><<<grid_occ(k32_cheb_step2<D, VT>, (nf + 1) / 2), kBlock, 0, st>>>(
+            nf, cols, vals, minv, r, zin, zout, d, sc, red, j, last);
+    else
+        k32_cheb_step<D, VT><<<grid_occ(k32_cheb_step<D, VT>, nf), kBlock, 0, st>>>(nf, cols, vals, minv, r, zin, zout,
+                                                                                   d, sc, red, j, last);
+}
+
 // p = z + beta p (float-float p, FP32 z)
 __global__ void __launch_bounds__(kBlock) kf_cpcg_dir32(int64_t n, float2* __restrict__ p, const float* __restrict__ z,
                                                        const KScal* sc, int first) {
@@ -1832,14 +2137,11 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e0) cudaEventRecord(e0, c.st);
                 for (int j = 1; j < deg; ++j) {
                     if (pp == CR_POLY_FP32)
-                        k32_cheb_step<D, float><<<grid_occ(k32_cheb_step<D, float>, c.nf), kBlock, 0, c.st>>>(
-                            c.nf, m->cols, h->val32, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc, h->red, j,
-                            j == deg - 1);
+                        launch_cheb32<D, float>(c.nf, m->cols, h->val32, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1],
+                                                ds, c.sc, h->red, j, j == deg - 1, c.st);
                     else if (pp == CR_POLY_BF16)
-                        k32_cheb_step<D, __nv_bfloat16>
-                            <<<grid_occ(k32_cheb_step<D, __nv_bfloat16>, c.nf), kBlock, 0, c.st>>>(
-                                c.nf, m->cols, h->val16, h->minv32, h->rf, zs[(j - 1) & 1], zs[j & 1], ds, c.sc,
-                                h->red, j, j == deg - 1);
+                        launch_cheb32<D, __nv_bfloat16>(c.nf, m->cols, h->val16, h->minv32, h->rf, zs[(j - 1) & 1],
+                                                        zs[j & 1], ds, c.sc, h->red, j, j == deg - 1, c.st);
                     else if (bf)
                         kf_cheb_step<D, __nv_bfloat16>
                             <<<grid_occ(kf_cheb_step<D, __nv_bfloat16>, c.nf), kBlock, 0, c.st>>>(
@@ -1899,6 +2201,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp));
                 CR_TRY(read_scal(c));
                 const int dev_status = c.hs->status;
+                if (dev_status == CR_ERR_TIMEOUT) { status = CR_ERR_TIMEOUT; break; }
                 if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }
                 k_add_ff<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->xf, c.sc);
                 ++c.launches;
@@ -2424,6 +2727,8 @@ int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_s
         return h->m->d == 2 ? solve_persistent<2>(h, rhs, o, Wdev, st) : solve_persistent<3>(h, rhs, o, Wdev, st);
     return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);
 }
+
+int cheb_step_form_impl(int d, int poly_prec) { return cheb32_form(d, poly_prec == CR_POLY_BF16); }
 
 void destroy_persistent_plans(cr_hybrid* h) {
     for (void*& p : h->pplan) {

@@ -65,14 +65,40 @@ def test_also_rejects_workloads_it_cannot_time(monkeypatch):
 def test_traffic_is_reported_only_for_the_captured_kernel_build(monkeypatch):
     sha = bench.sources_sha("persist")
     assert len(sha) == 64 and sha == bench.sources_sha("persist")
-    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff"): {"per": "iteration", "bytes": 123.0,
-                                                            "sources": "persist", "sha256": sha}})
+    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff", None): {"per": "iteration", "bytes": 123.0,
+                                                                  "sources": "persist", "sha256": sha}})
     assert bench.measured_traffic("cfgX", "ff") == (123.0, "iteration")
-    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff"): {"per": "iteration", "bytes": 123.0,
-                                                            "sources": "persist", "sha256": "0" * 64}})
+    monkeypatch.setattr(bench, "TRAFFIC", {("cfgX", "ff", None): {"per": "iteration", "bytes": 123.0,
+                                                                  "sources": "persist", "sha256": "0" * 64}})
     tb, why = bench.measured_traffic("cfgX", "ff")
     assert tb is None and "changed" in why
     assert bench.measured_traffic("cfgY", "ff")[0] is None
+
+
+def test_kernel_sections_are_hashed_alone(tmp_path, monkeypatch):
+    """A (file, start, end) source hashes the text between its markers: an edit
+    outside the section leaves the digest, an edit inside changes it, and a missing
+    marker gives None (no capture applies)."""
+    csrc = tmp_path / "paper_2101_03777_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    f = csrc / "k.cu"
+    f.write_text("head\n// <a>\nbody\n// <b>\ntail\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", {"k": [("k.cu", "// <a>", "// <b>")]})
+    sha = bench.sources_sha("k")
+    f.write_text("HEAD\n// <a>\nbody\n// <b>\nTAIL\n")
+    assert bench.sources_sha("k") == sha
+    f.write_text("head\n// <a>\nbody2\n// <b>\ntail\n")
+    assert bench.sources_sha("k") != sha
+    f.write_text("head\nbody\n// <b>\n")
+    assert bench.sources_sha("k") is None
+
+
+def test_every_recorded_kernel_section_exists():
+    for key in bench.KERNEL_SOURCES:
+        assert bench.sources_sha(key) is not None, key
+    for key, t in bench.TRAFFIC.items():
+        assert len(key) == 3 and t["sources"] in bench.KERNEL_SOURCES and t["per"] in ("iteration", "launch")
 
 
 def test_a_step_above_the_tolerance_is_rejected():

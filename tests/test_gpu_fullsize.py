@@ -19,7 +19,9 @@ checked on properties that the oracle computes from the paper at any size:
     perturbed 512x512 mesh have condition numbers near 3e3, so the two FP64
     evaluation orders differ by about 1e-12 of max|G|).
 The solves run as bench.py times them: persistent float-float and FP64
-Jacobi-PCG and FP64 Chebyshev-preconditioned PCG for transient Stokes; for the Newton step, flexible GMRES
+Jacobi-PCG, FP64 Chebyshev-preconditioned PCG and the float-float Chebyshev PCG
+with its steps in FP32 on BF16 values (the bench headline, on both the 3D and
+the 2D workload) for transient Stokes; for the Newton step, flexible GMRES
 preconditioned by inner float-float PCG solves with the transient Stokes G of
 the same mesh (Jacobi-GMRES(30) does not reach 1e-10 on it: 28,538 iterations
 at 64x64, no convergence within 60,000 at 128x128; Jacobi-BiCGStab converges up
@@ -73,12 +75,17 @@ CASES = [
                   use_graph=True), True),
     ("cfg3", dict(method="pcg", prec="fp64", persistent=True), False),
     ("cfg3", dict(method="pcg", prec="ff", persistent=True), False),
+    ("cfg3", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, poly_ratio=100.0, use_graph=True,
+                  poly_prec="bf16"), False),
+    ("cfg2", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, poly_ratio=1000.0, use_graph=True,
+                  poly_prec="bf16"), True),
     ("cfg5", dict(method="stokes-fgmres", prec="ff"), True),
 ]
 
 
 @pytest.mark.parametrize("name,opts,with_g", CASES,
-                         ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}-{c[1].get('precond', 'jacobi')}" for c in CASES])
+                         ids=[f"{c[0]}-{c[1]['method']}-{c[1]['prec']}-{c[1].get('precond', 'jacobi')}-"
+                              f"{c[1].get('poly_prec', 'same')}" for c in CASES])
 def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
     p, w = problem(name)
     o = oracle(name, with_g)
@@ -86,7 +93,8 @@ def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
     fb = torch.from_numpy(p["fbar"]).cuda()
     wt = torch.from_numpy(w).cuda() if w is not None else None
     hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb, conv=p["conv"], w=wt),
-                             keep_fp32=False, keep_ff=(opts["prec"] == "ff" and opts["method"] == "pcg"))
+                             keep_fp32=False, keep_bf16=opts.get("poly_prec") == "bf16",
+                             keep_ff=(opts["prec"] == "ff" and opts["method"] == "pcg"))
     n, ne, d = hyb.n, mesh.ne, mesh.dim
     W = torch.zeros(n, dtype=torch.float64, device="cuda")
     if opts["method"] == "stokes-fgmres":

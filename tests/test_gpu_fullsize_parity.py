@@ -12,7 +12,12 @@ fit in one pass of every kernel.  These meshes do not:
     each, float-float, autotuned), whose largest problem runs alone on
     rebalanced tiles at the end of the solve;
   * a transient Newton step on 384 x 384 squares (flexible GMRES with inner
-    float-float PCG).
+    float-float PCG);
+  * the three forms of the FP32 Chebyshev step kernel (one row per thread,
+    two rows per thread, slices staged in shared memory by bulk copies), each
+    in a child process (CRHYB_CHEB_KERNEL fixes the form per process), on
+    both meshes: more slices than resident blocks, so every block of the
+    staged form sweeps several slices and flips its mbarrier phase.
 The GPU solves to a relative residual of 1e-11 and recovers U and P (P
 normalised to zero mean, Section 2 item 5); they must match the oracle's
 within 1e-9 relative L2 (FP64, float-float, Chebyshev) or 1e-8 (float-float
@@ -28,6 +33,9 @@ magnitude below the tolerances.
 """
 
 import multiprocessing
+import os
+import subprocess
+import sys
 from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
@@ -78,8 +86,8 @@ def gpu_problem(name):
         p = synth.config_problem("cfg2" if name == "2d" else "cfg3", n=N2D if name == "2d" else N3D)
         mesh = crhyb.cr_mesh_load(p["coords"], p["elems"])
         fb = torch.from_numpy(p["fbar"]).cuda()
-        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
-                                 keep_ff=True, keep_ff_bf16=True)
+        hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=True,
+                                 keep_bf16=True, keep_ff=True, keep_ff_bf16=True)
         _GPU[name] = (mesh, hyb)
     return _GPU[name]
 
@@ -101,9 +109,15 @@ SOLVERS = {
     "fp64-three-kernel-graph": (dict(method="pcg", prec="fp64", use_graph=True), 1e-9),
     "ff-three-kernel": (dict(method="pcg", prec="ff"), 1e-9),
     "fp64-chebyshev": (dict(method="pcg", prec="fp64", precond="chebyshev", poly_degree=4, use_graph=True), 1e-9),
+    "ff-chebyshev": (dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, use_graph=True), 1e-9),
+    "ff-chebyshev-fp32-steps": (dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, use_graph=True,
+                                     poly_prec="fp32"), 1e-9),
+    "ff-chebyshev-bf16-steps": (dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, use_graph=True,
+                                     poly_prec="bf16"), 1e-9),
 }
 CASES_2D = list(SOLVERS)
-CASES_3D = ["fp64-persistent", "ff-persistent", "ff-three-kernel", "fp64-chebyshev"]
+CASES_3D = ["fp64-persistent", "ff-persistent", "ff-three-kernel", "fp64-chebyshev", "ff-chebyshev",
+            "ff-chebyshev-fp32-steps", "ff-chebyshev-bf16-steps"]
 
 
 @pytest.mark.parametrize("solver", CASES_2D)
@@ -170,3 +184,44 @@ def test_3d_32cubed_matches_oracle(truths, solver):
     assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po, _ = truths["3d"].result()
     assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))
+
+
+FORMS = ["rows1", "rows2", "staged"]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_chebyshev_step_forms_match_oracle(truths, tmp_path, form):
+    out = str(tmp_path / f"{form}.npz")
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.pathsep.join([os.path.dirname(here), here] + [q for q in [os.environ.get("PYTHONPATH")] if q])
+    env = dict(os.environ, CRHYB_CHEB_KERNEL=form, PYTHONPATH=path)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), form, out], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    got = np.load(out)
+    for name, key in (("2d", "2d"), ("3d", "3d")):
+        ref = truths[key].result()
+        Uo, Po = (ref[0] if name == "2d" else ref[:2])
+        for pp in ("fp32", "bf16"):
+            U, P = got[f"{name}_{pp}_U"], got[f"{name}_{pp}_P"]
+            assert got[f"{name}_{pp}_status"] == 0 and got[f"{name}_{pp}_relres"] <= 1e-11, (name, pp)
+            assert rel(U, Uo) <= 1e-9 and rel(P, Po) <= 1e-9, (form, name, pp, rel(U, Uo), rel(P, Po))
+
+
+def _child(form, out):
+    """Solve the 2D and 3D cases with FP32 and BF16 Chebyshev steps in this process's form."""
+    assert os.environ.get("CRHYB_CHEB_KERNEL") == form
+    res = {}
+    for name in ("2d", "3d"):
+        mesh, hyb = gpu_problem(name)
+        assert (mesh.nf + 255) // 256 > 5 * 152
+        for pp in ("fp32", "bf16"):
+            opts = dict(SOLVERS[f"ff-chebyshev-{pp}-steps"][0], poly_ratio=1000.0 if name == "2d" else 100.0)
+            st, U, P = solve_recover(hyb, tol=1e-11, max_iter=400000, **opts)
+            res.update({f"{name}_{pp}_U": U, f"{name}_{pp}_P": P, f"{name}_{pp}_status": st["status"],
+                        f"{name}_{pp}_relres": st["relres"]})
+    np.savez(out, **res)
+
+
+if __name__ == "__main__":
+    _child(sys.argv[1], sys.argv[2])

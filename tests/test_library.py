@@ -69,3 +69,24 @@ def test_bad_arguments_are_rejected(lib):
     assert lib.cr_solve_batched(None, None, None, None) == -1
     rc = lib.cr_solve(None, 0, None, None, None)
     assert rc == -1 and b"NULL" in lib.cr_last_error()
+
+
+def test_chebyshev_step_form_query(lib):
+    """cr_chebyshev_step_form: the defaults (staged for BF16 values; two rows per
+    thread for FP32 values in 3D, one in 2D), CR_ERR_ARG for other arguments, and the
+    CRHYB_CHEB_KERNEL override (read once per process, so in a child process)."""
+    import subprocess
+    import sys
+    if os.environ.get("CRHYB_CHEB_KERNEL"):
+        pytest.skip("the form is overridden in this environment")
+    assert [crhyb.cr_chebyshev_step_form(d, pp) for d in (2, 3) for pp in ("fp32", "bf16")] == \
+        ["rows1", "staged", "rows2", "staged"]
+    for d, pp in ((1, 1), (4, 2), (2, 0), (3, 3)):
+        assert crhyb.CR_ERR[lib.cr_chebyshev_step_form(d, pp)] == "CR_ERR_ARG"
+    code = ("from paper_2101_03777_gb300 import crhyb; "
+            "print(crhyb.cr_chebyshev_step_form(2, 'fp32'), crhyb.cr_chebyshev_step_form(3, 'bf16'))")
+    for form in ("rows1", "rows2", "staged"):
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120,
+                             env=dict(os.environ, CRHYB_CHEB_KERNEL=form))
+        assert out.returncode == 0, out.stderr
+        assert out.stdout.split() == [form, form]
