@@ -11,8 +11,8 @@ Metric: time to solution (seconds per step, lower is better), mixed precision
 against FP64.  The default workload is the 3D transient Stokes problem on 64^3
 cubes (1,572,864 Kuhn tetrahedra, 9.4 M unknowns, nu = 1, dt = 1e-3).  `value`
 is the first solver of --precs (by default PCG in float-float with FP64
-reliable updates and the Chebyshev polynomial preconditioner of degree 4, its
-steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
+reliable updates and the Chebyshev polynomial preconditioner, degree 12 in 3D and
+16 in 2D, its steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
 and float-float variants, float-float and native FP64 Jacobi-PCG, the FP64
 Chebyshev PCG, float-float with BF16 low parts) is reported
 under "precisions" with its roofline and its speed-up over FP64 Jacobi-PCG,
@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--sample-repeats", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--check-every", type=int, default=16,
                     help="iterations per convergence check (persistent: x64 iterations per launch)")
+    ap.add_argument("--deflate", type=int, default=0,
+                    help="with --time-steps: also run the loop deflated by this many Ritz vectors, taken after "
+                         "the first step from --lanczos FP64 PCG steps on its right-hand side")
+    ap.add_argument("--lanczos", type=int, default=200, help="PCG steps of the Ritz vectors (--deflate)")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="also time this many implicit Euler steps of the transient workload")
     ap.add_argument("--compare-coupled", action="store_true",
@@ -153,21 +157,20 @@ PRECS = {
     "mixed": (dict(prec="mixed", max_iter=400000, inner_tol=1e-4), 4, 4,
               "FP32 Jacobi-PCG restarted inside FP64 iterative refinement"),
     "fp64_cheb": (dict(prec="fp64", max_iter=200000, precond="chebyshev", poly_degree=4), 8, 8,
-                  "PCG, native FP64, Chebyshev polynomial preconditioner of degree 4 (Jacobi-preconditioned "
-                  "Chebyshev steps under the Gershgorin bound; interval ratio 1000 in 2D, 100 in 3D), "
-                  "graph-replayed kernels"),
+                  "PCG, native FP64, Chebyshev polynomial preconditioner of degree {degree} (Jacobi-preconditioned "
+                  "Chebyshev steps under the Gershgorin bound; interval ratio {ratio}), graph-replayed kernels"),
     "ff_cheb": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01), 8, 8,
                 "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
-                "of degree 4 (interval ratio 1000 in 2D, 100 in 3D), graph-replayed kernels"),
+                "of degree {degree} (interval ratio {ratio}), graph-replayed kernels"),
     "ff_cheb32": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01,
                        poly_prec="fp32"), 4, 4,
                   "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
-                  "of degree 4 whose steps run in FP32 on the FP32 values of G (interval ratio 1000 in 2D, 100 in "
-                  "3D), graph-replayed kernels"),
+                  "of degree {degree} whose steps run in FP32 on the FP32 values of G (interval ratio {ratio}), "
+                  "graph-replayed kernels"),
     "ff_chebbf": (dict(prec="ff", max_iter=200000, precond="chebyshev", poly_degree=4, inner_tol=0.01,
                        poly_prec="bf16"), 2, 4,
                   "PCG in float-float (FP32 pairs) with FP64 reliable updates, Chebyshev polynomial preconditioner "
-                  "of degree 4 whose steps run in FP32 on BF16 values of G (interval ratio 1000 in 2D, 100 in 3D), "
+                  "of degree {degree} whose steps run in FP32 on BF16 values of G (interval ratio {ratio}), "
                   "graph-replayed kernels"),
 }
 CHEB_PRECS = ("fp64_cheb", "ff_cheb", "ff_cheb32", "ff_chebbf")
@@ -179,23 +182,35 @@ CHEB_RATIO = {2: 1000.0, 3: 100.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 
 
-def cheb_degree(args, prec):
-    """Degree of the Chebyshev preconditioner of solver `prec` in this run."""
-    return getattr(args, "poly_degree", 0) or PRECS[prec][0]["poly_degree"]
+# Chebyshev degree and interval ratio per dimension.  Steps in FP32 (on FP32 or BF16
+# values) cost a fraction of a CG iteration's float-float SpMV, update and direction, so
+# those solvers take a high degree (fewer CG iterations, more steps); measured on the
+# 512^2 and 64^3 workloads: 2D degree 16 / ratio 1000 0.157 s against 0.256 s at degree 4,
+# 3D degree 12 / ratio 300 0.525 s against 0.666 s.  The float-float and FP64 steps cost
+# as much as the CG iteration itself and stay at degree 4.
+CHEB_DEGREE_FP32_STEPS = {2: 16, 3: 12}
+CHEB_RATIO_FP32_STEPS = {2: 1000.0, 3: 300.0}
 
 
-def cheb_ratio(args, d):
-    """Interval ratio of the Chebyshev preconditioner in this run (dimension d)."""
-    return getattr(args, "poly_ratio", 0.0) or CHEB_RATIO[d]
+def cheb_degree(args, prec, d):
+    """Degree of the Chebyshev preconditioner of solver `prec` on a d-dimensional mesh."""
+    if getattr(args, "poly_degree", 0):
+        return args.poly_degree
+    return CHEB_DEGREE_FP32_STEPS[d] if prec in ("ff_cheb32", "ff_chebbf") else PRECS[prec][0]["poly_degree"]
+
+
+def cheb_ratio(args, prec, d):
+    """Interval ratio of the Chebyshev preconditioner of solver `prec` (dimension d)."""
+    if getattr(args, "poly_ratio", 0.0):
+        return args.poly_ratio
+    return CHEB_RATIO_FP32_STEPS[d] if prec in ("ff_cheb32", "ff_chebbf") else CHEB_RATIO[d]
 
 
 def solver_text(args, prec, d):
     """The solver's description with the degree and ratio of this run."""
     text = PRECS[prec][3]
     if prec in CHEB_PRECS:
-        text = text.replace("of degree 4", f"of degree {cheb_degree(args, prec)}")
-        if getattr(args, "poly_ratio", 0.0):
-            text = text.replace("interval ratio 1000 in 2D, 100 in 3D", f"interval ratio {cheb_ratio(args, d):g}")
+        text = text.format(degree=cheb_degree(args, prec, d), ratio=f"{cheb_ratio(args, prec, d):g}")
     return text
 
 
@@ -224,11 +239,18 @@ TRAFFIC = {
     # the FP32 Chebyshev step on BF16 values: three launches each on the 64^3 and 512^2
     # workloads, read + written
     ("cfg3", "ff_chebbf", "staged"): {
-        "per": "launch", "bytes": (655519232 + 65823744 + 655515648 + 63299328 + 655502848 + 62904064) / 3,
+        "per": "launch", "bytes": (655521280 + 65956608 + 655623680 + 63242752 + 655530240 + 62977792) / 3,
         "sources": "cheb_staged", "sha256": "d34bb5e8d04d3b18ed131a58267950ba89cf11291a7f35ae2fbf9d1e046423b6"},
     ("cfg2", "ff_chebbf", "staged"): {
-        "per": "launch", "bytes": (75429376 + 1369856 + 75426560 + 44032 + 75427584 + 100864) / 3,
+        "per": "launch", "bytes": (75430144 + 1292544 + 75429120 + 45824 + 75427328 + 56064) / 3,
         "sources": "cheb_staged", "sha256": "d34bb5e8d04d3b18ed131a58267950ba89cf11291a7f35ae2fbf9d1e046423b6"},
+    # the float-float Chebyshev step (occupancy-sized grid)
+    ("cfg3", "ff_cheb", None): {
+        "per": "launch", "bytes": (1910210816 + 113576960 + 1910211328 + 109615616 + 1910217728 + 110364416) / 3,
+        "sources": "cheb_ff", "sha256": "282b6805c17fe174f84a97c904a5c96d72d9b3226acd7b76783095ad5bcd0c72"},
+    ("cfg2", "ff_cheb", None): {
+        "per": "launch", "bytes": (182250496 + 4264960 + 182249216 + 2390784 + 182252032 + 1692928) / 3,
+        "sources": "cheb_ff", "sha256": "282b6805c17fe174f84a97c904a5c96d72d9b3226acd7b76783095ad5bcd0c72"},
     ("cfg3", "ff_chebbf", "rows2"): {
         "per": "launch", "bytes": (655517184 + 47112448 + 655496704 + 44532736 + 655502592 + 44279296) / 3,
         "sources": "cheb_rows2", "sha256": "f8ad74ed6aaa33a0b42db85c86ff8cd8f66766b3e52c5d1003ef7c1f609922b5"},
@@ -529,8 +551,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             o = dict(tol=args.tol, prec=PRECS[prec][0]["prec"], profile=profile, check_every=args.check_every,
                      restart=60)
             if prec in CHEB_PRECS:
-                o.update(precond="chebyshev", poly_degree=cheb_degree(args, prec), poly_ratio=cheb_ratio(args, d),
-                         poly_prec=PRECS[prec][0].get("poly_prec", "same"))
+                o.update(precond="chebyshev", poly_degree=cheb_degree(args, prec, d),
+                         poly_ratio=cheb_ratio(args, prec, d), poly_prec=PRECS[prec][0].get("poly_prec", "same"))
             if args.max_iter:
                 o["max_iter"] = args.max_iter
             # the steady solve writes device arrays: the end-to-end run copies them to its host buffers
@@ -559,8 +581,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         o = solve_opts(prec, args.tol, args.graph and not profile, profile, persistent)
         o["check_every"] = args.check_every
         if o.get("precond") == "chebyshev":
-            o["poly_ratio"] = cheb_ratio(args, d)
-            o["poly_degree"] = cheb_degree(args, prec)
+            o["poly_ratio"] = cheb_ratio(args, prec, d)
+            o["poly_degree"] = cheb_degree(args, prec, d)
         if args.max_iter:
             o["max_iter"] = args.max_iter
         if extra:
@@ -659,7 +681,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
         if st_spmv is not None and prec in CHEB_PRECS:
             # the Chebyshev steps: degree - 1 launches per CG iteration, each the SpMV over G fused
             # with the vector update (reads r, d, M^{-1}; writes d and the other z buffer)
-            deg = cheb_degree(args, prec)
+            deg = cheb_degree(args, prec, d)
             step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nit = max(st_spmv["spmv_launches"], 1)
             ms = st_spmv["spmv_ms"] / (nit * (deg - 1))
@@ -683,7 +705,7 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                     "peak_note": peak_note}
         if newton and prec in CHEB_PRECS:
             # steady step with Chebyshev inner solves: the Chebyshev steps of the inner PCG dominate
-            deg = cheb_degree(args, prec)
+            deg = cheb_degree(args, prec, d)
             step_bytes = spmv_bytes + CHEB_EXTRA[prec] * N
             nl = max(st_main["spmv_launches"], 1) * (deg - 1)
             ms = st_main["spmv_ms"] / nl
@@ -782,33 +804,55 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
     if extras and args.time_steps and not newton:
         # implicit Euler steps of the transient workload (mu = 1/dt) from rest: each step hands
         # U^n to the next right-hand side, hybridises, solves from the previous W (warm start)
-        # and recovers U^{n+1}; timed as one region with CUDA events
+        # and recovers U^{n+1}; timed as one region with CUDA events.  With --deflate the loop
+        # runs again, deflated after its first step by Ritz vectors of that step's system
+        # (their Lanczos run inside the timed region)
         prec = head
         o = solve_opts(prec, args.tol, args.graph, False, args.persistent)
         o["check_every"] = args.check_every
-        system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fbar_dev)
-        Ut = torch.zeros(n, dtype=torch.float64, device="cuda")
-        Wt = torch.zeros(n, dtype=torch.float64, device="cuda")
-        iters = []
+        if o.get("precond") == "chebyshev":
+            o["poly_ratio"] = cheb_ratio(args, prec, d)
+            o["poly_degree"] = cheb_degree(args, prec, d)
 
-        def time_step(use_x0):
-            crhyb.cr_system_set_previous(system, Ut)
-            hyb = crhyb.cr_hybridise(system, keep_fp32=(prec == "mixed"), keep_ff=(prec == "ff"),
-                                     keep_ff_bf16=(prec == "ff_bf16"))
-            st = crhyb.cr_solve(hyb, Wt, use_x0=use_x0, **o)
-            crhyb.cr_recover_up(hyb, Wt, Ut, P, normalise_p=True)
-            iters.append(st["iterations"])
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(args.time_steps):
-            time_step(k > 0)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tl = agg(e0.elapsed_time(e1) / 1e3)
+        def time_loop(k_defl):
+            system = crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fbar_dev)
+            Ut = torch.zeros(n, dtype=torch.float64, device="cuda")
+            Wt = torch.zeros(n, dtype=torch.float64, device="cuda")
+            iters, defl = [], []
+
+            def time_step(k):
+                crhyb.cr_system_set_previous(system, Ut)
+                hyb = crhyb.cr_hybridise(system, keep_fp32=(prec in ("mixed", "ff_cheb32")),
+                                         keep_bf16=(prec == "ff_chebbf"),
+                                         keep_ff=(prec in ("ff", "ff_cheb", "ff_cheb32", "ff_chebbf")),
+                                         keep_ff_bf16=(prec == "ff_bf16"))
+                st = crhyb.cr_solve(hyb, Wt, use_x0=k > 0, deflation=defl[0] if defl else None, **o)
+                crhyb.cr_recover_up(hyb, Wt, Ut, P, normalise_p=True)
+                iters.append(st["iterations"])
+                if k_defl and not defl:
+                    lo = {key: o[key] for key in ("precond", "poly_degree", "poly_ratio") if key in o}
+                    defl.append(crhyb.cr_deflation_lanczos(hyb, args.lanczos, k_defl, **lo)[0])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.time_steps):
+                time_step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return agg(e0.elapsed_time(e1) / 1e3), iters, (defl[0].k if defl else 0)
+
+        tl, iters, _ = time_loop(0)
         out["time_loop"] = {"steps": args.time_steps, "value": tl / args.time_steps, "unit": "s per step",
                             "precision": prec, "iterations_per_step": iters,
                             "note": "implicit Euler from rest, dt = 1/mu; each step warm-starts from the previous W"}
+        if args.deflate:
+            tld, iters_d, kept = time_loop(args.deflate)
+            out["time_loop_deflated"] = {
+                "steps": args.time_steps, "value": tld / args.time_steps, "unit": "s per step", "precision": prec,
+                "iterations_per_step": iters_d, "vectors": kept, "lanczos_steps": args.lanczos,
+                "speedup": tl / tld,
+                "note": "the same loop; after the first step, Ritz vectors from FP64 PCG steps on its system "
+                        "(inside the timed region) deflate the solves of the later steps"}
     if extras and args.compare_coupled and not newton:
         # the paper's comparison: the same coupled system solved without hybridisation
         # (assembly + preconditioned MINRES to the same relative residual), one warm-up and

@@ -70,6 +70,7 @@ extern "C" {
 typedef struct cr_mesh cr_mesh;
 typedef struct cr_system cr_system;
 typedef struct cr_hybrid cr_hybrid;
+typedef struct cr_deflation cr_deflation;
 
 /* ---- options and parameters --------------------------------------------- */
 typedef struct cr_mesh_opts {
@@ -159,6 +160,16 @@ typedef struct cr_solve_opts {
                            for the rounded, still symmetric G~ is a fixed symmetric positive definite
                            operator under the same Gershgorin bound, so CG keeps its guarantees up to
                            the FP32 rounding of the steps, which the reliable updates absorb */
+    const cr_deflation* deflation; /* NULL, or a deflation space of this G (cr_deflation_create or
+                           cr_deflation_lanczos) for deflated PCG: x starts at x + V E^{-1} V^t r
+                           (E = V^t G V) and every search direction is made G-orthogonal to V,
+                           p = z + beta p - V E^{-1} (G V)^t z, so V^t r = 0 throughout and the
+                           eigenvalues of the preconditioned operator on span(V) leave the
+                           convergence.  PCG in FP64 (Jacobi or Chebyshev, persistent ignored) or
+                           FF with the Chebyshev preconditioner (V and G V in FP32; every reliable
+                           update repeats the deflated start, removing the components along V that
+                           the FP32 projection lets into r).  The space must come from a system of
+                           the same mesh, nu and mu without convection (the same G) */
 } cr_solve_opts;
 
 enum cr_poly_prec { CR_POLY_SAME = 0, CR_POLY_FP32 = 1, CR_POLY_BF16 = 2 };
@@ -267,6 +278,53 @@ int cr_hybrid_export(const cr_hybrid* h, int32_t* cols, double* vals, double* S)
  * CR_ERR_BREAKDOWN, CR_ERR_ARG (e.g. a precision whose values were not kept),
  * CR_ERR_CUDA. */
 int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st);
+
+/* ---- deflation spaces ----------------------------------------------------
+ * Deflated CG (Saad, Yeung, Erhel and Guyomarc'h, SIAM J. Sci. Comput. 21,
+ * 2000) for repeated solves with one G: the steps of a time loop (Section 3.1,
+ * implicit Euler: G depends on nu, mu and the mesh, not on the previous level)
+ * and several right-hand sides.  The paper has no counterpart: it compares
+ * algebraic multigrid and ILU preconditioners instead (Section 4).  A space
+ * holds at most CR_MAX_DEFLATION vectors V of length n = dim * nf_int, rounded
+ * to FP32 on entry (the FP64 and float-float solvers then deflate the same
+ * space), with G V, M^{-1} G V and the Cholesky factor of E = V^t G V on the
+ * device.  A vector whose Cholesky pivot falls below 1e-10 of its diagonal
+ * entry lies (numerically) in the span of those before it and is dropped;
+ * cr_deflation_info gives the count kept.  The space serves every system of
+ * the same mesh, nu and mu without convection.  Destroy it before its mesh. */
+#define CR_MAX_DEFLATION 16
+#define CR_MAX_LANCZOS 4096
+
+/* A space from k given vectors V, float64 [k][n], host or device.
+ * Errors: CR_ERR_ARG (k out of range, h not the SPD G of a transient Stokes
+ * system, no vector with V^t G V > 0), CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_deflation_create(cr_hybrid* h, int k, const double* V, cr_deflation** out);
+
+/* A space of Ritz vectors: m steps of FP64 PCG on right-hand side rhs of h from
+ * W = 0, with the preconditioner of opts (Jacobi, or Chebyshev with its degree
+ * and ratio; opts->prec is not used), storing the normalised preconditioned
+ * residuals q_j = z_j / sqrt(r_j . z_j) (FP32, m * n * 4 bytes of scratch).
+ * They are orthonormal in the inner product of M (the preconditioner's
+ * inverse), and Q^t G Q is the Lanczos matrix T with diagonal 1/alpha_j +
+ * beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j from the CG
+ * coefficients (Saad, Iterative Methods for Sparse Linear Systems, Section
+ * 6.7.3).  The k smallest eigenpairs (theta, s) of T (bisection and inverse
+ * iteration on the host) give the Ritz vectors y = Q s, approximate
+ * eigenvectors of the preconditioned operator for its smallest eigenvalues.
+ *   theta  host, float64 [k]: the Ritz values of the vectors kept, in order (0 after them)
+ * Stops early when the residual vanishes.  Errors: CR_ERR_ARG (1 <= k <=
+ * CR_MAX_DEFLATION and k <= m <= CR_MAX_LANCZOS, a zero right-hand side),
+ * CR_ERR_BREAKDOWN, CR_ERR_OOM, CR_ERR_CUDA. */
+int cr_deflation_lanczos(cr_hybrid* h, int rhs, const cr_solve_opts* opts, int m, int k, double* theta,
+                         cr_deflation** out);
+
+/* Vectors kept and their length. */
+int cr_deflation_info(const cr_deflation* d, int32_t* k, int64_t* n);
+
+/* The space's vectors (as rounded to FP32), float64 [k][n], host or device. */
+int cr_deflation_export(const cr_deflation* d, double* V);
+
+void cr_destroy_deflation(cr_deflation* d);
 
 /* Which form of the reduced-precision Chebyshev step kernel (poly_prec FP32 or
  * BF16) cr_solve runs on a dim-dimensional mesh.  An introspection call of the

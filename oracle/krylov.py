@@ -14,7 +14,10 @@ iterative refinement: inner solves in float32, residual and update in float64.
 Jacobi-preconditioned Chebyshev steps, Saad Algorithm 12.1) on the interval
 below a Gershgorin bound of the spectrum.  ``deflated_pcg`` keeps the CG
 directions G-orthogonal to given vectors (deflated CG), removing their
-eigenvalues from the convergence.
+eigenvalues from the convergence; ``lanczos_ritz`` takes approximate low
+eigenvectors of the preconditioned operator from the coefficients and
+preconditioned residuals of a PCG run (the Lanczos connection of CG), the
+vectors a later solve with the same G deflates.
 """
 
 import numpy as np
@@ -171,6 +174,54 @@ def deflated_pcg(G, b, precond, V, rtol=1e-10, maxit=100000):
         p = project(z) + (rz_new / rz) * p
         rz = rz_new
     return x, it, hist
+
+
+def lanczos_ritz(G, b, precond, m, k):
+    """Ritz pairs of the preconditioned operator from m steps of PCG on G x = b
+    from x = 0 (Saad, Iterative Methods for Sparse Linear Systems, Section 6.7.3,
+    the Lanczos connection of CG), preconditioner z = precond(r) with M its inverse.
+
+    The preconditioned residuals z_j of PCG satisfy z_i . r_j = 0 for i != j, so
+    q_j = z_j / sqrt(r_j . z_j) are orthonormal in the inner product of M, and
+    Q^t G Q (Q = [q_0 .. q_{m-1}]) is the tridiagonal matrix T whose entries
+    follow from the CG step lengths alpha_j and the ratios beta_j = r_{j+1}.z_{j+1}
+    / r_j.z_j:
+        T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}   (no second term for j = 0),
+        T_{j,j+1} = T_{j+1,j} = -sqrt(beta_j)/alpha_j.
+    The eigenpairs (theta, s) of T with the k smallest theta give the Ritz
+    vectors y = Q s, approximate eigenvectors of M^{-1} G (Galerkin condition:
+    Q^t (G y - theta M y) = 0).  Stops early when the
+    residual vanishes.  Returns (theta [k'], Y [n, k'], T [m', m']) with m' the
+    steps taken and k' = min(k, m')."""
+    r = np.array(b, dtype=float, copy=True)
+    z = precond(r)
+    rz = float(np.dot(r, z))
+    p = z.copy()
+    Q, alphas, betas = [], [], []
+    for _ in range(m):
+        if not rz > 0.0:
+            break
+        Q.append(z / np.sqrt(rz))
+        q = G @ p
+        alpha = rz / float(np.dot(p, q))
+        alphas.append(alpha)
+        r = r - alpha * q
+        z = precond(r)
+        rz_new = float(np.dot(r, z))
+        beta = rz_new / rz
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    mm = len(alphas)
+    T = np.zeros((mm, mm))
+    for j in range(mm):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < mm:
+            T[j, j + 1] = T[j + 1, j] = -np.sqrt(betas[j]) / alphas[j]
+    theta, S = np.linalg.eigh(T)
+    kk = min(k, mm)
+    Qm = np.array(Q).T if mm else np.zeros((b.shape[0], 0))
+    return theta[:kk], Qm @ S[:, :kk], T
 
 
 def gmres(G, b, minv, x0=None, restart=30, rtol=1e-10, maxit=100000):

@@ -60,7 +60,7 @@ class cr_solve_opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("poly_degree", ctypes.c_int32), ("poly_ratio", ctypes.c_double),
-                ("poly_prec", ctypes.c_int32)]
+                ("poly_prec", ctypes.c_int32), ("deflation", ctypes.c_void_p)]
 
 
 class cr_batch_opts(ctypes.Structure):
@@ -117,6 +117,12 @@ _SIGS = {
     "cr_residual_noalloc": (_i32, [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cr_residual_noalloc_max_rows": (_i64, []),
     "cr_chebyshev_step_form": (_i32, [ctypes.c_int, ctypes.c_int]),
+    "cr_deflation_create": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "cr_deflation_lanczos": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_vp)]),
+    "cr_deflation_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "cr_deflation_export": (_i32, [_vp, _vp]),
+    "cr_destroy_deflation": (None, [_vp]),
     "cr_last_error": (ctypes.c_char_p, []),
 }
 EXPORTED = tuple(_SIGS)
@@ -312,11 +318,54 @@ def cr_hybrid_export(hyb):
 
 def make_solve_opts(method="pcg", prec="fp64", tol=1e-10, max_iter=100000, restart=30, inner_tol=0.0,
                     max_outer=60, use_x0=False, check_every=16, use_graph=False, profile=False, persistent=False,
-                    precond="jacobi", poly_degree=0, poly_ratio=0.0, poly_prec="same"):
+                    precond="jacobi", poly_degree=0, poly_ratio=0.0, poly_prec="same", deflation=None):
     return cr_solve_opts(METHOD[method], PREC[prec], float(tol), int(max_iter), int(restart), float(inner_tol),
                          int(max_outer), int(bool(use_x0)), int(check_every), int(bool(use_graph)),
                          int(bool(profile)), int(bool(persistent)), PRECOND[precond], int(poly_degree),
-                         float(poly_ratio), POLY_PREC[poly_prec])
+                         float(poly_ratio), POLY_PREC[poly_prec], deflation.handle if deflation is not None else None)
+
+
+class Deflation:
+    """Owner of a cr_deflation handle (keeps the mesh of the system it was built
+    from alive): k vectors of length n."""
+
+    def __init__(self, handle, hyb):
+        self.handle, self.mesh = handle, hyb.mesh
+        k, n = _i32(), _i64()
+        _check(load_library().cr_deflation_info(handle, ctypes.byref(k), ctypes.byref(n)))
+        self.k, self.n = int(k.value), int(n.value)
+
+    def vectors(self):
+        """The space's vectors (rounded to FP32), float64 [k, n] on the host."""
+        V = np.empty((self.k, self.n), dtype=np.float64)
+        _check(load_library().cr_deflation_export(self.handle, _ptr(V, np.float64, self.k * self.n, "V")))
+        return V
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _alive():
+            _lib.cr_destroy_deflation(self.handle)
+            self.handle = None
+
+
+def cr_deflation_create(hyb, V):
+    """A deflation space of the G of `hyb` from the rows of V (float64 [k, n], host or device)."""
+    k = int(V.shape[0])
+    h = _vp()
+    _check(load_library().cr_deflation_create(hyb.handle, k, _ptr(V, np.float64, k * hyb.n, "V"), ctypes.byref(h)))
+    return Deflation(h, hyb)
+
+
+def cr_deflation_lanczos(hyb, m, k, rhs=0, **opts):
+    """A deflation space of k Ritz vectors from m FP64 PCG steps on right-hand side `rhs`
+    of `hyb` (preconditioner from opts: precond, poly_degree, poly_ratio).
+    Returns (Deflation, Ritz values of the vectors kept)."""
+    o = make_solve_opts(**opts)
+    theta = (ctypes.c_double * int(k))()
+    h = _vp()
+    _check(load_library().cr_deflation_lanczos(hyb.handle, int(rhs), ctypes.byref(o), int(m), int(k), theta,
+                                               ctypes.byref(h)))
+    d = Deflation(h, hyb)
+    return d, np.array(theta[:d.k])
 
 
 def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):

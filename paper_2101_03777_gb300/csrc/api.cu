@@ -358,6 +358,20 @@ extern "C" int cr_apply_G(cr_hybrid* h, const double* x, double* y) {
     return launch_spmv64(h, x, y, h->m->stream);
 }
 
+// A deflation space serves the solves whose G is the one it was built from: the same
+// mesh, nu and mu, no convection; PCG in FP64 (Jacobi or Chebyshev) or float-float
+// (Chebyshev).
+static int check_deflation(const cr_deflation* d, const cr_hybrid* h, const cr_solve_opts* o, const char* fn) {
+    const std::string f(fn);
+    if (d->m != h->m || d->nu != h->s->nu || d->mu != h->s->mu || h->s->conv != CR_CONV_NONE)
+        return fail(CR_ERR_ARG, f + ": the deflation space belongs to another G (mesh, nu, mu or convection)");
+    if (o->method != CR_METHOD_PCG) return fail(CR_ERR_ARG, f + ": deflation applies to PCG");
+    const bool ok = (o->prec == CR_PREC_FP64) || (o->prec == CR_PREC_FF && o->precond == CR_PRECOND_CHEBYSHEV);
+    if (!ok)
+        return fail(CR_ERR_ARG, f + ": deflation runs in FP64 PCG (Jacobi or Chebyshev) or float-float Chebyshev PCG");
+    return CR_OK;
+}
+
 extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
     if (st) std::memset(st, 0, sizeof(*st));
     if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
@@ -391,6 +405,7 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
         if (o->poly_prec != CR_POLY_SAME && o->prec == CR_PREC_FP64)
             return fail(CR_ERR_ARG, "cr_solve: poly_prec applies to the float-float Chebyshev PCG");
     }
+    if (o->deflation) CR_TRY(check_deflation(o->deflation, h, o, "cr_solve"));
     cr_mesh* m = h->m;
     const size_t n = size_t(m->nf) * m->d;
     StreamScope scope(m);
@@ -413,6 +428,77 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
         if (e != cudaSuccess && rc == CR_OK) rc = cuda_fail(e, "cr_solve: copy of W");
     }
     return rc;
+}
+
+// ---- deflation spaces ---------------------------------------------------------
+
+extern "C" int cr_deflation_create(cr_hybrid* h, int k, const double* V, cr_deflation** out) {
+    if (!h || !V || !out) return fail(CR_ERR_ARG, "cr_deflation_create: NULL argument");
+    *out = nullptr;
+    CR_TRY(check_call(h->m, "cr_deflation_create", {V}));
+    if (k < 1 || k > CR_MAX_DEFLATION) return fail(CR_ERR_ARG, "cr_deflation_create: k must be in [1, CR_MAX_DEFLATION]");
+    if (h->s->conv != CR_CONV_NONE || !(h->s->mu > 0.0))
+        return fail(CR_ERR_ARG, "cr_deflation_create: deflated CG needs the SPD G of a transient Stokes system");
+    StreamScope scope(h->m);
+    cr_deflation* d = nullptr;
+    CR_TRY(defl_alloc(h, k, &d));
+    const size_t bytes = sizeof(double) * size_t(k) * size_t(d->n);
+    cudaError_t e = cudaMemcpyAsync(d->V64, V, bytes, cudaMemcpyDefault, h->m->stream);
+    int rc = e == cudaSuccess ? defl_build(d, h, h->m->stream) : cuda_fail(e, "cr_deflation_create: copy of V");
+    if (rc != CR_OK) {
+        d->arena.release();
+        delete d;
+        return rc;
+    }
+    *out = d;
+    return CR_OK;
+}
+
+extern "C" int cr_deflation_lanczos(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta,
+                                    cr_deflation** out) {
+    if (!h || !o || !theta || !out) return fail(CR_ERR_ARG, "cr_deflation_lanczos: NULL argument");
+    *out = nullptr;
+    CR_TRY(check_call(h->m, "cr_deflation_lanczos", {}));
+    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_deflation_lanczos: rhs out of range");
+    if (k < 1 || k > CR_MAX_DEFLATION || m < k || m > CR_MAX_LANCZOS)
+        return fail(CR_ERR_ARG, "cr_deflation_lanczos: need 1 <= k <= CR_MAX_DEFLATION and k <= m <= CR_MAX_LANCZOS");
+    if (h->s->conv != CR_CONV_NONE || !(h->s->mu > 0.0))
+        return fail(CR_ERR_ARG, "cr_deflation_lanczos: deflated CG needs the SPD G of a transient Stokes system");
+    if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
+        return fail(CR_ERR_ARG, "cr_deflation_lanczos: bad preconditioner");
+    if (o->precond == CR_PRECOND_CHEBYSHEV) {
+        const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+        if (deg < 2 || deg > CR_MAX_POLY_DEGREE || !(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
+            return fail(CR_ERR_ARG, "cr_deflation_lanczos: bad poly_degree or poly_ratio");
+    }
+    const size_t n = size_t(h->m->nf) * h->m->d;
+    StreamScope scope(h->m);
+    CR_TRY(ensure_workspace(h, false, 0, CR_PREC_FP64));
+    if (o->precond == CR_PRECOND_CHEBYSHEV && !h->cheb) CR_TRY(h->arena.alloc_n(&h->cheb, 3 * n + 1));
+    return lanczos_impl(h, rhs, o, m, k, theta, out);
+}
+
+extern "C" int cr_deflation_info(const cr_deflation* d, int32_t* k, int64_t* n) {
+    if (!d) return fail(CR_ERR_ARG, "cr_deflation_info: NULL deflation");
+    if (k) *k = d->k;
+    if (n) *n = d->n;
+    return CR_OK;
+}
+
+extern "C" int cr_deflation_export(const cr_deflation* d, double* V) {
+    if (!d || !V) return fail(CR_ERR_ARG, "cr_deflation_export: NULL argument");
+    CR_TRY(check_call(d->m, "cr_deflation_export", {V}));
+    StreamScope scope(d->m);
+    CR_CUDA(cudaMemcpyAsync(V, d->V64, sizeof(double) * size_t(d->k) * size_t(d->n), cudaMemcpyDefault, d->m->stream));
+    CR_CUDA(cudaStreamSynchronize(d->m->stream));
+    return CR_OK;
+}
+
+extern "C" void cr_destroy_deflation(cr_deflation* d) {
+    if (!d) return;
+    cudaStreamSynchronize(d->m->stream);
+    d->arena.release();
+    delete d;
 }
 
 extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* W,

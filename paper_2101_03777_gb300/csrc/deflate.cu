@@ -1,0 +1,459 @@
+// Deflation of the CG for G W = S: a space of k vectors V whose G-components
+// the iteration keeps out of its search directions (deflated CG: Saad, Yeung,
+// Erhel and Guyomarc'h, SIAM J. Sci. Comput. 21, 2000).  With E = V^t G V,
+//   x_0 = x + V E^{-1} V^t (b - G x),   p_j = z_j + beta_j p_{j-1} - V E^{-1} (G V)^t z_j,
+// every residual stays orthogonal to V and the eigenvalues of the preconditioned
+// operator on span(V) drop out of the convergence.  The paper has no counterpart
+// (it compares algebraic multigrid and ILU preconditioners, Section 4); this is
+// the library's way to cut the iterations of repeated solves with one G (the
+// steps of a time loop, several right-hand sides).
+//
+// This file holds the space (cr_deflation), its kernels and the host linear
+// algebra of its small matrices: the Cholesky factor of E, and the eigenpairs of
+// the Lanczos matrix T from which cr_deflation_lanczos takes Ritz vectors.
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+#include "ff.cuh"
+#include "internal.h"
+
+namespace crhyb {
+namespace {
+
+constexpr int kDeflBlock = 256;
+
+__device__ __forceinline__ double as_double(double v) { return v; }
+__device__ __forceinline__ double as_double(float v) { return double(v); }
+__device__ __forceinline__ double as_double(float2 v) { return double(v.x) + double(v.y); }
+
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// g = Y^t v (k sums, Y [k][n]); the last block sums the per-block partials in
+// block order and, with solve, forms c = E^{-1} g from the Cholesky factor
+// L (row-major, E = L L^t).  Nothing runs when *done is set (a converged solve).
+template <typename YT, typename VT>
+__global__ void __launch_bounds__(kDeflBlock) k_defl_dots(int64_t n, const YT* __restrict__ Y,
+                                                          const VT* __restrict__ v, DeflDev dd, int solve,
+                                                          const int* done) {
+    if (done && *done) return;
+    const int k = dd.k;
+    double acc[kMaxDefl];
+#pragma unroll
+    for (int i = 0; i < kMaxDefl; ++i) acc[i] = 0.0;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double vj = as_double(v[j]);
+#pragma unroll
+        for (int i = 0; i < kMaxDefl; ++i)
+            if (i < k) acc[i] = fma(as_double(Y[size_t(i) * n + j]), vj, acc[i]);
+    }
+    __shared__ double sh[kMaxDefl][kDeflBlock / 32];
+    __shared__ double tot[kMaxDefl];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kMaxDefl; ++i) {
+        if (i >= k) break;
+        const double a = warp_sum(acc[i]);
+        if (lane == 0) sh[i][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double s = 0.0;
+        for (int w = 0; w < kDeflBlock / 32; ++w) s += sh[threadIdx.x][w];
+        dd.partial[size_t(threadIdx.x) * kMaxDeflBlocks + blockIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(dd.count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < k) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(dd.partial + size_t(threadIdx.x) * kMaxDeflBlocks + b);
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *dd.count = 0u;
+        double c[kMaxDefl];
+        for (int i = 0; i < k; ++i) c[i] = tot[i];
+        if (solve) {
+            for (int i = 0; i < k; ++i) {   // L y = g
+                double s = c[i];
+                for (int j = 0; j < i; ++j) s -= dd.L[i * k + j] * c[j];
+                c[i] = s / dd.L[i * k + i];
+            }
+            for (int i = k - 1; i >= 0; --i) {   // L^t c = y
+                double s = c[i];
+                for (int j = i + 1; j < k; ++j) s -= dd.L[j * k + i] * c[j];
+                c[i] = s / dd.L[i * k + i];
+            }
+        }
+        for (int i = 0; i < k; ++i) {
+            dd.c[i] = c[i];
+            dd.cf[i] = float(c[i]);
+        }
+    }
+}
+
+// x += sign * Y c (FP64)
+template <typename YT>
+__global__ void __launch_bounds__(kDeflBlock) k_defl_axpy(int64_t n, const YT* __restrict__ Y, DeflDev dd,
+                                                          double sign, double* __restrict__ x) {
+    const int k = dd.k;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s = fma(dd.c[i], as_double(Y[size_t(i) * n + j]), s);
+        x[j] = fma(sign, s, x[j]);
+    }
+}
+
+// p -= V c: FP64 p, or float-float p with the FP32 vectors (the sum in FP32)
+__global__ void __launch_bounds__(kDeflBlock) k_defl_project64(int64_t n, const double* __restrict__ V, DeflDev dd,
+                                                               double* __restrict__ p, const int* done) {
+    if (done && *done) return;
+    const int k = dd.k;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s = fma(dd.c[i], V[size_t(i) * n + j], s);
+        p[j] -= s;
+    }
+}
+
+__global__ void __launch_bounds__(kDeflBlock) k_defl_projectff(int64_t n, const float* __restrict__ V, DeflDev dd,
+                                                               float2* __restrict__ p, const int* done) {
+    if (done && *done) return;
+    const int k = dd.k;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        float s = 0.f;
+        for (int i = 0; i < k; ++i) s = fmaf(dd.cf[i], V[size_t(i) * n + j], s);
+        p[j] = ff_add(p[j], make_float2(-s, 0.f));
+    }
+}
+
+// V rounded to FP32 (in place in FP64, and its FP32 copy)
+__global__ void __launch_bounds__(kDeflBlock) k_defl_round(int64_t n, double* __restrict__ v, float* __restrict__ v32) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const float f = __double2float_rn(v[j]);
+        v[j] = double(f);
+        v32[j] = f;
+    }
+}
+
+// w = M^{-1} g (FP64) and g32 = fl32(g)
+__global__ void __launch_bounds__(kDeflBlock) k_defl_scale(int64_t n, const double* __restrict__ g,
+                                                           const double* __restrict__ minv, double* __restrict__ w,
+                                                           float* __restrict__ g32) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        w[j] = minv[j] * g[j];
+        g32[j] = __double2float_rn(g[j]);
+    }
+}
+
+// q = z / sqrt(rz), z = zin or (zin = null) M^{-1} r; rz read from the device
+__global__ void __launch_bounds__(kDeflBlock) k_lanczos_store(int64_t n, const double* __restrict__ zin,
+                                                              const double* __restrict__ minv,
+                                                              const double* __restrict__ r, const double* rz,
+                                                              float* __restrict__ q) {
+    const double s = 1.0 / sqrt(*rz);
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double z = zin ? zin[j] : minv[j] * r[j];
+        q[j] = __double2float_rn(z * s);
+    }
+}
+
+// Y [k][n] = Q S: Q [m][n] (FP32 Lanczos vectors), S [m][k] (FP64, column l the
+// eigenvector of T for Ritz value l)
+__global__ void __launch_bounds__(kDeflBlock) k_ritz(int64_t n, int m, int k, const float* __restrict__ Q,
+                                                     const double* __restrict__ S, double* __restrict__ Y) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double y[kMaxDefl];
+#pragma unroll
+        for (int l = 0; l < kMaxDefl; ++l) y[l] = 0.0;
+        for (int t = 0; t < m; ++t) {
+            const double qv = double(Q[size_t(t) * n + j]);
+#pragma unroll
+            for (int l = 0; l < kMaxDefl; ++l)
+                if (l < k) y[l] = fma(qv, __ldg(S + size_t(t) * k + l), y[l]);
+        }
+#pragma unroll
+        for (int l = 0; l < kMaxDefl; ++l)
+            if (l < k) Y[size_t(l) * n + j] = y[l];
+    }
+}
+
+int defl_grid(int64_t n) {
+    const int64_t g = (n + kDeflBlock - 1) / kDeflBlock;
+    return int(g < 1 ? 1 : (g > kMaxDeflBlocks ? kMaxDeflBlocks : g));
+}
+
+// ---- host linear algebra of the small matrices ----------------------------------
+
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count of
+// the LDL^t pivots of T - x I).
+int sturm_below(const std::vector<double>& a, const std::vector<double>& b, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    const size_t n = a.size();
+    for (size_t i = 0; i < n; ++i) {
+        const double off = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+        d = a[i] - x - (i > 0 ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Solve (T - s I) y = v for symmetric tridiagonal T by Gaussian elimination with
+// partial pivoting (the factor gains a second superdiagonal).
+void tridiag_solve(const std::vector<double>& a, const std::vector<double>& b, double s, std::vector<double>& y) {
+    const size_t n = a.size();
+    std::vector<double> dl(n, 0.0), d(n), du(n, 0.0), du2(n, 0.0);
+    for (size_t i = 0; i < n; ++i) {
+        d[i] = a[i] - s;
+        if (i + 1 < n) du[i] = b[i], dl[i] = b[i];
+    }
+    for (size_t i = 0; i + 1 < n; ++i) {
+        if (std::fabs(d[i]) >= std::fabs(dl[i])) {
+            if (d[i] == 0.0) d[i] = 1e-300;
+            const double f = dl[i] / d[i];
+            d[i + 1] -= f * du[i];
+            y[i + 1] -= f * y[i];
+            dl[i] = 0.0;
+        } else {   // swap rows i and i+1
+            const double f = d[i] / dl[i];
+            d[i] = dl[i];
+            const double t = d[i + 1];
+            d[i + 1] = du[i] - f * t;
+            du[i] = t;
+            if (i + 2 < n) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du2[i];
+            }
+            std::swap(y[i], y[i + 1]);
+            y[i + 1] -= f * y[i];
+        }
+    }
+    if (d[n - 1] == 0.0) d[n - 1] = 1e-300;
+    y[n - 1] /= d[n - 1];
+    if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / d[n - 2];
+    for (size_t i = n >= 3 ? n - 3 : 0; n >= 3; --i) {
+        y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
+        if (i == 0) break;
+    }
+}
+
+}  // namespace
+
+// The k smallest eigenpairs of the symmetric tridiagonal matrix with diagonal a and
+// off-diagonal b: eigenvalues by bisection on Sturm counts, eigenvectors by inverse
+// iteration, orthogonalised against those already found (S column-major [n][k]:
+// S[t * k + l] is component t of vector l).
+void tridiag_smallest_eigen(const std::vector<double>& a, const std::vector<double>& b, int k,
+                            std::vector<double>& theta, std::vector<double>& S) {
+    const int n = int(a.size());
+    k = k < n ? k : n;
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+        lo = std::fmin(lo, a[i] - r);
+        hi = std::fmax(hi, a[i] + r);
+    }
+    const double span = std::fmax(hi - lo, 1e-300);
+    theta.assign(k, 0.0);
+    S.assign(size_t(n) * k, 0.0);
+    std::vector<std::vector<double>> vecs;
+    for (int l = 0; l < k; ++l) {
+        double x0 = lo, x1 = hi;   // the (l+1)-th smallest eigenvalue lies in [x0, x1]
+        for (int it = 0; it < 200 && x1 - x0 > 1e-15 * std::fmax(std::fabs(x0) + std::fabs(x1), span * 1e-300); ++it) {
+            const double mid = 0.5 * (x0 + x1);
+            if (sturm_below(a, b, mid) > l) x1 = mid;
+            else x0 = mid;
+        }
+        const double th = 0.5 * (x0 + x1);
+        theta[l] = th;
+        std::vector<double> y(n);
+        for (int t = 0; t < n; ++t) y[t] = 1.0 + 0.001 * ((t * 7919) % 13);   // a start with every component
+        const double shift = th - 1e-13 * span;
+        for (int it = 0; it < 4; ++it) {
+            tridiag_solve(a, b, shift, y);
+            for (const auto& v : vecs) {   // the eigenvectors of nearby eigenvalues, projected out
+                double dot = 0.0;
+                for (int t = 0; t < n; ++t) dot += v[t] * y[t];
+                for (int t = 0; t < n; ++t) y[t] -= dot * v[t];
+            }
+            double nrm = 0.0;
+            for (int t = 0; t < n; ++t) nrm += y[t] * y[t];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) break;
+            for (int t = 0; t < n; ++t) y[t] /= nrm;
+        }
+        for (int t = 0; t < n; ++t) S[size_t(t) * k + l] = y[t];
+        vecs.push_back(y);
+    }
+}
+
+DeflDev cr_deflation_dev(const cr_deflation* d) {
+    DeflDev dd;
+    dd.k = d->k;
+    dd.L = d->L;
+    dd.c = d->c;
+    dd.cf = d->cf;
+    dd.partial = d->partial;
+    dd.count = d->count;
+    return dd;
+}
+
+int defl_dots64(const cr_deflation* d, const double* Y, const double* v, bool solve, const int* done, cudaStream_t st) {
+    k_defl_dots<double, double><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), solve, done);
+    return CR_OK;
+}
+
+int defl_dots32(const cr_deflation* d, const float* Y, const float* v, const int* done, cudaStream_t st) {
+    k_defl_dots<float, float><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
+    return CR_OK;
+}
+
+int defl_dots32ff(const cr_deflation* d, const float* Y, const float2* v, const int* done, cudaStream_t st) {
+    k_defl_dots<float, float2><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
+    return CR_OK;
+}
+
+int defl_axpy64(const cr_deflation* d, const double* Y, double sign, double* x, cudaStream_t st) {
+    k_defl_axpy<double><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, cr_deflation_dev(d), sign, x);
+    return CR_OK;
+}
+
+int defl_project64(const cr_deflation* d, double* p, const int* done, cudaStream_t st) {
+    k_defl_project64<<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, d->V64, cr_deflation_dev(d), p, done);
+    return CR_OK;
+}
+
+int defl_projectff(const cr_deflation* d, float2* p, const int* done, cudaStream_t st) {
+    k_defl_projectff<<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, d->V32, cr_deflation_dev(d), p, done);
+    return CR_OK;
+}
+
+int lanczos_store(int64_t n, const double* z, const double* minv, const double* r, const double* rz, float* q,
+                  cudaStream_t st) {
+    k_lanczos_store<<<defl_grid(n), kDeflBlock, 0, st>>>(n, z, minv, r, rz, q);
+    return CR_OK;
+}
+
+int ritz_vectors(int64_t n, int m, int k, const float* Q, const double* S, double* Y, cudaStream_t st) {
+    k_ritz<<<defl_grid(n), kDeflBlock, 0, st>>>(n, m, k, Q, S, Y);
+    return CR_OK;
+}
+
+// Build the space from the k vectors in d->V64 (device, [k][n]) for the G of h:
+// V rounded to FP32, G V, M^{-1} G V, E = V^t G V, and the vectors kept greedily
+// in order while the Cholesky pivot of E stays above 1e-10 of its diagonal entry
+// (a vector in the span of those before it is dropped; d->k becomes the count).
+int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st) {
+    const int64_t n = d->n;
+    const int k = d->k;
+    const int g = defl_grid(n);
+    for (int i = 0; i < k; ++i) {
+        k_defl_round<<<g, kDeflBlock, 0, st>>>(n, d->V64 + size_t(i) * n, d->V32 + size_t(i) * n);
+        CR_TRY(launch_spmv64(h, d->V64 + size_t(i) * n, d->GV64 + size_t(i) * n, st));
+        k_defl_scale<<<g, kDeflBlock, 0, st>>>(n, d->GV64 + size_t(i) * n, h->minv64, d->W64 + size_t(i) * n,
+                                              d->GV32 + size_t(i) * n);
+    }
+    CR_CUDA(cudaGetLastError());
+    // E column by column: E_ij = V_i . (G V)_j
+    std::vector<double> E(size_t(k) * k);
+    std::vector<double> col(kMaxDefl);
+    for (int j = 0; j < k; ++j) {
+        CR_TRY(defl_dots64(d, d->V64, d->GV64 + size_t(j) * n, false, nullptr, st));
+        CR_CUDA(cudaMemcpyAsync(col.data(), d->c, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CR_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < k; ++i) E[size_t(i) * k + j] = col[i];
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < i; ++j) E[size_t(i) * k + j] = E[size_t(j) * k + i] = 0.5 * (E[size_t(i) * k + j] + E[size_t(j) * k + i]);
+    // greedy Cholesky over the vectors in order
+    std::vector<int> keep;
+    std::vector<double> L;   // row-major over the kept vectors
+    for (int i = 0; i < k; ++i) {
+        const int r = int(keep.size());
+        std::vector<double> row(r + 1, 0.0);
+        bool ok = E[size_t(i) * k + i] > 0.0 && std::isfinite(E[size_t(i) * k + i]);
+        for (int a = 0; ok && a < r; ++a) {
+            double s = E[size_t(i) * k + keep[a]];
+            for (int b = 0; b < a; ++b) s -= row[b] * L[size_t(a) * (k) + b];
+            row[a] = s / L[size_t(a) * k + a];
+        }
+        double piv = ok ? E[size_t(i) * k + i] : 0.0;
+        for (int a = 0; ok && a < r; ++a) piv -= row[a] * row[a];
+        if (!ok || !(piv > 1e-10 * E[size_t(i) * k + i])) continue;
+        row[r] = std::sqrt(piv);
+        L.resize(size_t(r + 1) * k, 0.0);
+        for (int a = 0; a <= r; ++a) L[size_t(r) * k + a] = row[a];
+        keep.push_back(i);
+    }
+    if (keep.empty()) return fail(CR_ERR_ARG, "deflation: no vector with V^t G V > 0");
+    // compact the kept vectors to the front
+    for (int a = 0; a < int(keep.size()); ++a) {
+        const int i = keep[a];
+        if (i == a) continue;
+        const size_t dst = size_t(a) * n, src = size_t(i) * n;
+        CR_CUDA(cudaMemcpyAsync(d->V64 + dst, d->V64 + src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CR_CUDA(cudaMemcpyAsync(d->GV64 + dst, d->GV64 + src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CR_CUDA(cudaMemcpyAsync(d->W64 + dst, d->W64 + src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CR_CUDA(cudaMemcpyAsync(d->V32 + dst, d->V32 + src, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        CR_CUDA(cudaMemcpyAsync(d->GV32 + dst, d->GV32 + src, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    const int kk = int(keep.size());
+    std::vector<double> Lk(size_t(kk) * kk, 0.0);
+    for (int a = 0; a < kk; ++a)
+        for (int b = 0; b <= a; ++b) Lk[size_t(a) * kk + b] = L[size_t(a) * k + b];
+    d->k = kk;
+    d->kept = keep;
+    CR_CUDA(cudaMemcpyAsync(d->L, Lk.data(), sizeof(double) * kk * kk, cudaMemcpyHostToDevice, st));
+    CR_CUDA(cudaStreamSynchronize(st));
+    return CR_OK;
+}
+
+// Allocate a space for up to k vectors of the G of h (mesh, nu, mu recorded).
+int defl_alloc(cr_hybrid* h, int k, cr_deflation** out) {
+    auto* d = new cr_deflation();
+    static std::atomic<uint64_t> serial{0};
+    d->m = h->m;
+    d->dim = h->m->d;
+    d->n = h->m->nf * h->m->d;
+    d->k = k;
+    d->nu = h->s->nu;
+    d->mu = h->s->mu;
+    d->serial = ++serial;
+    const size_t kn = size_t(k) * size_t(d->n);
+    int rc;
+    if ((rc = d->arena.alloc_n(&d->V64, kn)) || (rc = d->arena.alloc_n(&d->GV64, kn)) ||
+        (rc = d->arena.alloc_n(&d->W64, kn)) || (rc = d->arena.alloc_n(&d->V32, kn)) ||
+        (rc = d->arena.alloc_n(&d->GV32, kn)) || (rc = d->arena.alloc_n(&d->L, size_t(kMaxDefl) * kMaxDefl)) ||
+        (rc = d->arena.alloc_n(&d->c, size_t(kMaxDefl))) || (rc = d->arena.alloc_n(&d->cf, size_t(kMaxDefl))) ||
+        (rc = d->arena.alloc_n(&d->partial, size_t(kMaxDefl) * kMaxDeflBlocks)) ||
+        (rc = d->arena.alloc_n(&d->count, 1))) {
+        d->arena.release();
+        delete d;
+        return rc;
+    }
+    cudaError_t e = cudaMemsetAsync(d->count, 0, sizeof(unsigned), h->m->stream);
+    if (e != cudaSuccess) {
+        d->arena.release();
+        delete d;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    *out = d;
+    return CR_OK;
+}
+
+}  // namespace crhyb

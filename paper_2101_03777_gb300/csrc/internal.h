@@ -155,6 +155,40 @@ struct cr_system {
     cr_coupled* steady_op = nullptr;   // coupled operator of a steady system (cr_solve_steady), made on first use
 };
 
+namespace crhyb {
+constexpr int kMaxDefl = 16;           // deflation vectors at most
+constexpr int kMaxDeflBlocks = 1024;   // blocks of the deflation dot products
+// what the deflation kernels read and write
+struct DeflDev {
+    int k;
+    const double* L;     // [k][k] Cholesky factor of E = V^t G V, row-major lower
+    double* c;           // [kMaxDefl] coefficients of the last dot-product solve
+    float* cf;           // the same in FP32
+    double* partial;     // [kMaxDefl][kMaxDeflBlocks] per-block partial sums
+    unsigned* count;     // completion counter of the dot products
+};
+}  // namespace crhyb
+
+// A deflation space (deflate.cu): k vectors V, rounded to FP32, of the G shared by
+// every Stokes system of one mesh with one nu and mu; G V, M^{-1} G V (FP64), V and
+// G V in FP32, and the Cholesky factor of E = V^t G V.
+struct cr_deflation {
+    cr_mesh* m = nullptr;
+    int dim = 0, k = 0;
+    int64_t n = 0;
+    double nu = 0, mu = 0;
+    uint64_t serial = 0;              // distinguishes spaces in the solvers' graph caches
+    std::vector<int> kept;            // indices of the given vectors kept
+    crhyb::DevArena arena;
+    double *V64 = nullptr, *GV64 = nullptr, *W64 = nullptr;   // [k][n]
+    float *V32 = nullptr, *GV32 = nullptr;                    // [k][n]
+    double* L = nullptr;
+    double* c = nullptr;
+    float* cf = nullptr;
+    double* partial = nullptr;
+    unsigned* count = nullptr;
+};
+
 struct cr_hybrid {
     cr_system* s = nullptr;
     cr_mesh* m = nullptr;
@@ -201,7 +235,8 @@ struct cr_hybrid {
     std::vector<cudaEvent_t> prof_ev;   // profile = 1: event pairs around SpMV launches
     double prof_ms = 0.0;
     int prof_n = 0;
-    int graph_key[kGraphs] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int64_t graph_key[kGraphs] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    uint64_t graph_tag[kGraphs] = {};   // the deflation space a captured chunk uses (its serial; 0: none)
     int64_t graph_launches[kGraphs] = {};   // kernels in each captured chunk
     void* pplan[3] = {nullptr, nullptr, nullptr};   // persistent PCG plans (FP64, FF, FF_BF16), solve.cu
     crhyb::SteadyWork steady;     // cr_solve_steady with this hybrid as preconditioner (first use)
@@ -238,6 +273,25 @@ int solve_steady_impl(cr_coupled* c, cr_mesh* m, cr_hybrid* pre, int rhs, const 
 int solve_newton_impl(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre, const cr_solve_opts* lin, double ntol,
                       int maxn, double* U, double* P, cr_newton_stats* st);
 int cheb_step_form_impl(int d, int poly_prec);
+// deflation (deflate.cu): dot products g = Y^t v over the space's k vectors (with
+// solve: c = E^{-1} g into the space's coefficient slots), x += sign Y c, p -= V c,
+// skipped while *done (when given) is set; the space's build and allocation; the
+// Lanczos-vector store q = z / sqrt(rz) and the Ritz vectors Y = Q S; the k smallest
+// eigenpairs of a symmetric tridiagonal matrix (host)
+int defl_dots64(const cr_deflation* d, const double* Y, const double* v, bool solve, const int* done, cudaStream_t st);
+int defl_dots32(const cr_deflation* d, const float* Y, const float* v, const int* done, cudaStream_t st);
+int defl_dots32ff(const cr_deflation* d, const float* Y, const float2* v, const int* done, cudaStream_t st);
+int defl_axpy64(const cr_deflation* d, const double* Y, double sign, double* x, cudaStream_t st);
+int defl_project64(const cr_deflation* d, double* p, const int* done, cudaStream_t st);
+int defl_projectff(const cr_deflation* d, float2* p, const int* done, cudaStream_t st);
+int defl_alloc(cr_hybrid* h, int k, cr_deflation** out);
+int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st);
+int lanczos_store(int64_t n, const double* z, const double* minv, const double* r, const double* rz, float* q,
+                  cudaStream_t st);
+int ritz_vectors(int64_t n, int m, int k, const float* Q, const double* S, double* Y, cudaStream_t st);
+void tridiag_smallest_eigen(const std::vector<double>& a, const std::vector<double>& b, int k,
+                            std::vector<double>& theta, std::vector<double>& S);
+int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out);
 void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 

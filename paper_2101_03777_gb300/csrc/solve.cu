@@ -1623,10 +1623,10 @@ void ff_iteration(Ctx& c, const LT* vl, float2* x, float2* r, float2* p, float2*
 // iteration.  Assumes x, r, p, rz, tol2 are set.  `variant` distinguishes
 // iterations with different launch sequences under the same graph slot.
 template <typename Iter>
-int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey, int variant = 0) {
+int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey, int variant = 0, uint64_t tag = 0) {
     cr_hybrid* h = c.h;
-    const int key = chunk + (variant << 20);
-    if (graph && (h->graph_key[gkey] != key || !h->graph_exec[gkey])) {
+    const int64_t key = int64_t(chunk) + (int64_t(variant) << 20);
+    if (graph && (h->graph_key[gkey] != key || h->graph_tag[gkey] != tag || !h->graph_exec[gkey])) {
         if (h->graph_exec[gkey]) { cudaGraphExecDestroy(h->graph_exec[gkey]); h->graph_exec[gkey] = nullptr; }
         cudaGraph_t gr;
         const int64_t before = c.launches;
@@ -1639,6 +1639,7 @@ int pcg_loop(Ctx& c, Iter iter, int chunk, bool graph, int gkey, int variant = 0
         cudaGraphDestroy(gr);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
         h->graph_key[gkey] = key;
+        h->graph_tag[gkey] = tag;
     }
     const bool prof = c.profile && !graph;
     if (prof && int(h->prof_ev.size()) < 2 * chunk) {
@@ -1926,13 +1927,26 @@ int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, 
 // systems) restarts CG from the iterate with r = b - G x, up to max_outer
 // times, so that CR_OK always means ||b - G x|| <= tol ||b||.  `start` forms
 // the first direction from r; `run` iterates until the device flags done.
+// With a deflation space dfl every cycle first moves x to x + V E^{-1} V^t r and
+// recomputes r (the deflated start: V^t r = 0).
 template <int D, typename Start, typename Run>
-int restarted_pcg(Ctx& c, Start start, Run run, const double* b, int max_outer, double tol, int& outer) {
+int restarted_pcg(Ctx& c, Start start, Run run, const double* b, int max_outer, double tol, int& outer,
+                  const cr_deflation* dfl = nullptr) {
     cr_hybrid* h = c.h;
     const int ggrid = grid_for(c.nf);
     for (;;) {
         CR_TRY(read_scal(c));
         if (c.hs->done) return CR_OK;   // the start (true) residual already meets the tolerance
+        if (dfl) {
+            CR_TRY(defl_dots64(dfl, dfl->V64, h->r64, true, nullptr, c.st));
+            CR_TRY(defl_axpy64(dfl, dfl->V64, 1.0, h->x64, c.st));
+            k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, h->m->cols, h->val64, b, h->x64, h->r64, nullptr,
+                                                        h->minv64, c.sc, h->red, 1, tol, 0.0);
+            c.launches += 3;
+            CR_CUDA(cudaGetLastError());
+            CR_TRY(read_scal(c));
+            if (c.hs->done) return CR_OK;
+        }
         start();
         CR_CUDA(cudaGetLastError());
         CR_TRY(run());
@@ -2002,6 +2016,9 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     const int max_outer = o->max_outer > 0 ? o->max_outer : 60;
     const int ggrid = grid_for(c.nf), gn = grid_for(c.n);
     const double* x0 = o->use_x0 ? h->x64 : nullptr;
+    const cr_deflation* dfl = o->deflation;   // checked against h by the caller
+    const int* done = &c.sc->done;            // device flag: the deflation kernels skip a finished solve
+    const uint64_t dtag = dfl ? dfl->serial : 0;
 
     std::memset(c.hs, 0, sizeof(KScal));
     c.hs->max_it = gmax;
@@ -2067,12 +2084,18 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e1) cudaEventRecord(e1, c.st);
                 c.launches += deg - 1;
             };
+            // deflated: c = E^{-1} (G V)^t z before the direction, p -= V c after it
+            auto direction = [&](int first) {
+                if (dfl) defl_dots64(dfl, dfl->GV64, zb[(deg - 1) & 1], true, done, c.st);
+                k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, first);
+                if (dfl) defl_project64(dfl, h->p64, done, c.st);
+                c.launches += dfl ? 3 : 1;
+            };
             auto start = [&]() {
                 k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
                 ++c.launches;
                 cheb_steps(nullptr, nullptr);
-                k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 1);
-                ++c.launches;
+                direction(1);
             };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 k_pcg_spmv<D, double, double><<<grid_occ(k_pcg_spmv<D, double, double>, c.nf), kBlock, 0, c.st>>>(
@@ -2081,21 +2104,42 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 k_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->p64, h->q64, h->minv64, zb[0], dv,
                                                        c.sc, h->red);
                 cheb_steps(e0, e1);
-                k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 0);
-                c.launches += 3;
+                direction(0);
+                c.launches += 2;
             };
-            CR_TRY(restarted_pcg<D>(c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 6, deg); }, b, max_outer,
-                                 o->tol, outer));
+            CR_TRY(restarted_pcg<D>(
+                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 6, deg + (dfl ? 512 : 0), dtag); }, b,
+                max_outer, o->tol, outer, dfl));
         } else if (o->method == CR_METHOD_PCG) {
+            // deflated (Jacobi): c = E^{-1} (M^{-1} G V)^t r = E^{-1} (G V)^t z, p -= V c
             auto start = [&]() {
                 k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
                 ++c.launches;
+                if (dfl) {
+                    defl_dots64(dfl, dfl->W64, h->r64, true, done, c.st);
+                    defl_project64(dfl, h->p64, done, c.st);
+                    c.launches += 2;
+                }
             };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
-                pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, e0, e1);
+                if (!dfl) {
+                    pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, e0, e1);
+                    return;
+                }
+                if (e0) cudaEventRecord(e0, c.st);
+                k_pcg_spmv<D, double, double><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, h->p64, h->q64,
+                                                                           c.sc, h->red);
+                if (e1) cudaEventRecord(e1, c.st);
+                k_pcg_update<D, double><<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->p64, h->q64, h->minv64,
+                                                                 c.sc, h->red);
+                defl_dots64(dfl, dfl->W64, h->r64, true, done, c.st);
+                k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 0);
+                defl_project64(dfl, h->p64, done, c.st);
+                c.launches += 5;
             };
-            CR_TRY(restarted_pcg<D>(c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 0); }, b, max_outer,
-                                 o->tol, outer));
+            CR_TRY(restarted_pcg<D>(
+                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 0, dfl ? 512 : 0, dtag); }, b, max_outer,
+                o->tol, outer, dfl));
         } else {
             CR_TRY((gmres_loop<D, double, double>(c, h->val64, h->minv64, b, h->x64, h->r64, h->V64, h->Z64)));
         }
@@ -2155,15 +2199,35 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e1) cudaEventRecord(e1, c.st);
                 c.launches += deg - 1;
             };
+            // the direction p = z + beta p; deflated: c = E^{-1} (G V)^t z (FP32 G V) before,
+            // p -= V c (FP32 V) after
+            auto direction = [&](int first) {
+                if (dfl) {
+                    if (pp != CR_POLY_SAME) defl_dots32(dfl, dfl->GV32, zs[(deg - 1) & 1], done, c.st);
+                    else defl_dots32ff(dfl, dfl->GV32, zb[(deg - 1) & 1], done, c.st);
+                }
+                if (pp != CR_POLY_SAME)
+                    kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, first);
+                else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
+                if (dfl) defl_projectff(dfl, h->pf, done, c.st);
+                c.launches += dfl ? 3 : 1;
+            };
             auto restart_direction = [&](int first) {
                 if (pp != CR_POLY_SAME) kf_cheb_start32<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zs[0], ds, c.sc);
                 else kf_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zb[0], dv, c.sc);
                 ++c.launches;
                 cheb_steps(nullptr, nullptr);
-                if (pp != CR_POLY_SAME)
-                    kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, first);
-                else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
-                ++c.launches;
+                direction(first);
+            };
+            // deflated start (and the same at every reliable update, which also removes the
+            // components along V that the FP32 projection lets into r):
+            // x64 += V E^{-1} V^t (b - G x64)
+            auto deflate_x = [&](const double* x) {
+                k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x, h->r64, nullptr,
+                                                            h->minv64, c.sc, h->red, 0, o->tol, 0.0);
+                defl_dots64(dfl, dfl->V64, h->r64, true, nullptr, c.st);
+                defl_axpy64(dfl, dfl->V64, 1.0, h->x64, c.st);
+                c.launches += 3;
             };
             auto true_residual3 = [&](const double* x) {
                 k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, x, h->r64, nullptr, h->minv64,
@@ -2171,7 +2235,12 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 k_ff_from64<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->rf, c.sc);
                 c.launches += 2;
             };
-            true_residual3(x0);
+            if (dfl) {
+                deflate_x(x0);
+                true_residual3(h->x64);
+            } else {
+                true_residual3(x0);
+            }
             restart_direction(1);
             CR_CUDA(cudaGetLastError());
             CR_TRY(read_scal(c));
@@ -2192,19 +2261,18 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                     kf_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->xf, h->rf, h->pf, h->qf, h->minv32, zb[0], dv,
                                                             c.sc, h->red);
                 cheb_steps(e0, e1);
-                if (pp != CR_POLY_SAME)
-                    kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, 0);
-                else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, 0);
-                c.launches += 3;
+                direction(0);
+                c.launches += 2;
             };
             while (status == CR_OK && !c.hs->conv) {
-                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp));
+                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp + (dfl ? 4096 : 0), dtag));
                 CR_TRY(read_scal(c));
                 const int dev_status = c.hs->status;
                 if (dev_status == CR_ERR_TIMEOUT) { status = CR_ERR_TIMEOUT; break; }
                 if (dev_status == CR_ERR_BREAKDOWN && c.hs->it == it_mark) { status = CR_ERR_BREAKDOWN; break; }
                 k_add_ff<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->xf, c.sc);
                 ++c.launches;
+                if (dfl) deflate_x(h->x64);
                 true_residual3(h->x64);
                 CR_CUDA(cudaGetLastError());
                 CR_TRY(read_scal(c));
@@ -2722,10 +2790,113 @@ int solve_newton_impl(cr_mesh* m, double nu, const double* fbar, cr_hybrid* pre,
 }
 
 int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_solve_stats* st) {
-    if (o->persistent && o->method == CR_METHOD_PCG && o->precond == CR_PRECOND_JACOBI &&
+    if (o->persistent && o->method == CR_METHOD_PCG && o->precond == CR_PRECOND_JACOBI && !o->deflation &&
         (o->prec == CR_PREC_FP64 || o->prec == CR_PREC_FF || o->prec == CR_PREC_FF_BF16))
         return h->m->d == 2 ? solve_persistent<2>(h, rhs, o, Wdev, st) : solve_persistent<3>(h, rhs, o, Wdev, st);
     return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);
+}
+
+// Ritz vectors for a deflation space from m steps of FP64 PCG (Jacobi or Chebyshev,
+// as opts says) on right-hand side rhs from x = 0: the normalised preconditioned
+// residuals q_j = z_j / sqrt(r_j.z_j) are stored in FP32, the Lanczos matrix T (its
+// diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal -sqrt(beta_j)/alpha_j
+// from the CG coefficients; Saad, Iterative Methods for Sparse Linear Systems,
+// Section 6.7.3) gives its k smallest eigenpairs on the host, and Y = Q S.  One
+// iteration per launch sequence, its coefficients read back after each.
+template <int D>
+int lanczos_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, int mmax, int k, double* theta,
+                cr_deflation** out) {
+    cr_mesh* m = h->m;
+    Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D, false};
+    const double* b = h->S + size_t(rhs) * c.n;
+    const int ggrid = grid_for(c.nf), gn = grid_for(c.n);
+    std::memset(c.hs, 0, sizeof(KScal));
+    c.hs->max_it = 1 << 30;
+    const bool cheb = o->precond == CR_PRECOND_CHEBYSHEV;
+    if (cheb) CR_TRY(chebyshev_setup<D>(h, o, c.st, c.hs));
+    CR_CUDA(cudaMemcpyAsync(c.sc, c.hs, sizeof(KScal), cudaMemcpyHostToDevice, c.st));
+    CR_CUDA(cudaMemsetAsync(h->x64, 0, sizeof(double) * c.n, c.st));
+    struct Tmp {
+        DevArena a;
+        ~Tmp() { a.release(); }
+    } tmp;
+    float* Q = nullptr;
+    CR_TRY(tmp.a.alloc_n(&Q, size_t(mmax) * size_t(c.n)));
+    // r = b with r.M^{-1}r; tolerance 0: the flag stays down unless r is exactly zero
+    k_residual64<D><<<ggrid, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, b, nullptr, h->r64, nullptr, h->minv64, c.sc,
+                                                h->red, 1, 0.0, 0.0);
+    const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+    double* zb[2] = {h->cheb, h->cheb ? h->cheb + c.n : nullptr};
+    double* dv = h->cheb ? h->cheb + 2 * c.n : nullptr;
+    auto cheb_steps = [&]() {
+        for (int j = 1; j < deg; ++j)
+            k_cheb_step<D><<<grid_occ(k_cheb_step<D>, c.nf), kBlock, 0, c.st>>>(
+                c.nf, m->cols, h->val64, h->minv64, h->r64, zb[(j - 1) & 1], zb[j & 1], dv, c.sc, h->red, j,
+                j == deg - 1);
+    };
+    const double* zcur = cheb ? zb[(deg - 1) & 1] : nullptr;   // null: z = M^{-1} r
+    if (cheb) {
+        k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
+        cheb_steps();
+        k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 1);
+    } else {
+        k_pcg_dir<double><<<gn, kBlock, 0, c.st>>>(c.n, h->p64, h->r64, h->minv64, c.sc, 1);
+    }
+    CR_CUDA(cudaGetLastError());
+    CR_TRY(read_scal(c));
+    if (c.hs->done || !(c.hs->rz > 0.0)) return fail(CR_ERR_ARG, "cr_deflation_lanczos: zero right-hand side");
+    CR_TRY(lanczos_store(c.n, zcur, h->minv64, h->r64, &c.sc->rz, Q, c.st));
+    std::vector<double> alpha, beta;
+    for (int j = 0; j < mmax; ++j) {
+        if (cheb) {
+            k_pcg_spmv<D, double, double><<<grid_occ(k_pcg_spmv<D, double, double>, c.nf), kBlock, 0, c.st>>>(
+                c.nf, m->cols, h->val64, h->p64, h->q64, c.sc, h->red);
+            k_cpcg_update<<<gn, kBlock, 0, c.st>>>(c.n, h->x64, h->r64, h->p64, h->q64, h->minv64, zb[0], dv, c.sc,
+                                                   h->red);
+            cheb_steps();
+            k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, 0);
+        } else {
+            pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, nullptr,
+                                             nullptr);
+        }
+        CR_CUDA(cudaGetLastError());
+        CR_TRY(read_scal(c));
+        if (c.hs->status == CR_ERR_BREAKDOWN || !(c.hs->alpha > 0.0) || !std::isfinite(c.hs->alpha)) break;
+        alpha.push_back(c.hs->alpha);
+        beta.push_back(c.hs->beta);
+        if (c.hs->done || !(c.hs->rz > 0.0) || !std::isfinite(c.hs->beta)) break;   // r = 0: the space is exact
+        if (j + 1 < mmax) CR_TRY(lanczos_store(c.n, zcur, h->minv64, h->r64, &c.sc->rz, Q + size_t(j + 1) * c.n, c.st));
+    }
+    const int mm = int(alpha.size());
+    if (mm == 0) return fail(CR_ERR_BREAKDOWN, "cr_deflation_lanczos: the first CG step broke down");
+    std::vector<double> ta(mm), tb(mm > 1 ? mm - 1 : 0);
+    for (int j = 0; j < mm; ++j) {
+        ta[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < mm) tb[j] = -std::sqrt(beta[j]) / alpha[j];
+    }
+    std::vector<double> th, S;
+    tridiag_smallest_eigen(ta, tb, k, th, S);
+    const int kk = int(th.size());
+    double* Sd = nullptr;
+    CR_TRY(tmp.a.alloc_n(&Sd, S.size()));
+    CR_CUDA(cudaMemcpyAsync(Sd, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice, c.st));
+    cr_deflation* d = nullptr;
+    CR_TRY(defl_alloc(h, kk, &d));
+    CR_TRY(ritz_vectors(c.n, mm, kk, Q, Sd, d->V64, c.st));
+    CR_CUDA(cudaGetLastError());
+    int rc = defl_build(d, h, c.st);
+    if (rc != CR_OK) {
+        d->arena.release();
+        delete d;
+        return rc;
+    }
+    for (int a = 0; a < k; ++a) theta[a] = a < d->k ? th[d->kept[a]] : 0.0;
+    *out = d;
+    return CR_OK;
+}
+
+int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out) {
+    return h->m->d == 2 ? lanczos_dim<2>(h, rhs, o, m, k, theta, out) : lanczos_dim<3>(h, rhs, o, m, k, theta, out);
 }
 
 int cheb_step_form_impl(int d, int poly_prec) { return cheb32_form(d, poly_prec == CR_POLY_BF16); }

@@ -114,10 +114,14 @@ SOLVERS = {
                                      poly_prec="fp32"), 1e-9),
     "ff-chebyshev-bf16-steps": (dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, use_graph=True,
                                      poly_prec="bf16"), 1e-9),
+    # the bench's headline: degree 16, ratio 1000 in 2D; degree 12, ratio 300 in 3D
+    "ff-chebyshev-bf16-steps-bench-degree": (dict(method="pcg", prec="ff", precond="chebyshev", use_graph=True,
+                                                  poly_prec="bf16"), 1e-9),
 }
+BENCH_DEGREE = {2: dict(poly_degree=16, poly_ratio=1000.0), 3: dict(poly_degree=12, poly_ratio=300.0)}
 CASES_2D = list(SOLVERS)
 CASES_3D = ["fp64-persistent", "ff-persistent", "ff-three-kernel", "fp64-chebyshev", "ff-chebyshev",
-            "ff-chebyshev-fp32-steps", "ff-chebyshev-bf16-steps"]
+            "ff-chebyshev-fp32-steps", "ff-chebyshev-bf16-steps", "ff-chebyshev-bf16-steps-bench-degree"]
 
 
 @pytest.mark.parametrize("solver", CASES_2D)
@@ -126,6 +130,8 @@ def test_2d_384_matches_oracle(truths, solver):
     assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
     opts, tol = SOLVERS[solver]
     opts = dict(opts, **({"poly_ratio": 1000.0} if "chebyshev" in solver else {}))
+    if "bench-degree" in solver:
+        opts.update(BENCH_DEGREE[2])
     st, U, P = solve_recover(hyb, tol=1e-11, max_iter=400000, **opts)
     assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po = truths["2d"].result()[0]
@@ -180,6 +186,8 @@ def test_3d_32cubed_matches_oracle(truths, solver):
     assert mesh.nf > 8 * 152 * 256 and (mesh.nf + 255) // 256 > 3 * 152
     opts, tol = SOLVERS[solver]
     opts = dict(opts, **({"poly_ratio": 100.0} if "chebyshev" in solver else {}))
+    if "bench-degree" in solver:
+        opts.update(BENCH_DEGREE[3])
     st, U, P = solve_recover(hyb, tol=1e-11, max_iter=400000, **opts)
     assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po, _ = truths["3d"].result()

@@ -77,3 +77,82 @@ def test_low_modes_deflated_reach_the_solution_sooner(cheb):
     assert hist[-1] <= 1e-12
     assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
     assert it < it0
+
+
+# ---- Ritz vectors from the Lanczos connection of CG (krylov.lanczos_ritz) ----
+
+def test_lanczos_matrix_is_q_transpose_g_q():
+    """T from the CG coefficients equals Q^t G Q formed from the stored vectors, and
+    Q^t M Q = I for the Jacobi preconditioner (M = diag(G)): catches a wrong sign of
+    the off-diagonal, a dropped beta/alpha term and unnormalised vectors."""
+    G, S = hybrid_system(10)
+    minv = krylov.jacobi(G)
+    m = 12
+    # the Lanczos vectors again, as the oracle stores them, to form Q^t G Q directly
+    r = S.copy()
+    z = minv * r
+    p = z.copy()
+    rz = r @ z
+    Q = []
+    for _ in range(m):
+        Q.append(z / np.sqrt(rz))
+        q = G @ p
+        a = rz / (p @ q)
+        r = r - a * q
+        z = minv * r
+        rzn = r @ z
+        p = z + (rzn / rz) * p
+        rz = rzn
+    Q = np.array(Q).T
+    theta, Y, T = krylov.lanczos_ritz(G, S, lambda v: minv * v, m, 4)
+    QGQ = Q.T @ (G @ Q)
+    assert T.shape == (m, m)
+    assert np.abs(QGQ - T).max() <= 1e-8 * np.abs(T).max()
+    assert np.abs(Q.T @ (G.diagonal()[:, None] * Q) - np.eye(m)).max() <= 1e-8
+    # Galerkin condition of the returned Ritz pairs
+    for j in range(len(theta)):
+        res = G @ Y[:, j] - theta[j] * G.diagonal() * Y[:, j]
+        assert np.abs(Q.T @ res).max() <= 1e-8 * np.linalg.norm(G.diagonal() * Y[:, j]) * max(theta[j], 1.0)
+
+
+def test_full_lanczos_gives_the_exact_smallest_eigenvalues():
+    """On a diagonal system with n distinct eigenvalues, n CG steps from a vector with
+    every component give T with exactly those eigenvalues; the k smallest come back
+    first, and the Ritz vectors are the coordinate vectors (up to sign)."""
+    rng = np.random.default_rng(4)
+    lam = np.sort(rng.uniform(0.5, 20.0, 12))
+    G = sp.diags(lam).tocsr()
+    b = rng.uniform(0.5, 1.5, 12)
+    theta, Y, T = krylov.lanczos_ritz(G, b, lambda r: r, 12, 3)
+    assert np.allclose(theta, lam[:3], rtol=1e-9, atol=0)
+    assert np.allclose(np.abs(Y[:3, :3]), np.eye(3), atol=1e-6)
+    assert np.allclose(np.linalg.eigvalsh(T), lam, rtol=1e-9, atol=0)
+
+
+def test_jacobi_preconditioned_ritz_values_are_generalised_eigenvalues():
+    """With M = diag(G) and enough steps, the smallest Ritz values reach the smallest
+    eigenvalues of the pencil (G, M) (dense solve on a small hybridised system)."""
+    import scipy.linalg as sla
+    G, S = hybrid_system(6)
+    minv = krylov.jacobi(G)
+    Gd = G.toarray()
+    ev = sla.eigh(Gd, np.diag(G.diagonal()), eigvals_only=True)
+    theta, Y, _ = krylov.lanczos_ritz(G, S, lambda v: minv * v, 80, 2)
+    assert np.allclose(theta, ev[:2], rtol=1e-6, atol=0)
+
+
+def test_ritz_vectors_of_one_solve_deflate_the_next():
+    """The Ritz vectors of a short Chebyshev-PCG run on one right-hand side, deflated in
+    the solve of another right-hand side with the same G, reach its solution in fewer
+    iterations."""
+    G, S = hybrid_system(24)
+    minv = krylov.jacobi(G)
+    lmax = krylov.gershgorin_bound(G, minv)
+    precond = lambda r: krylov.chebyshev_apply(G, minv, r, 4, lmax, 1000.0)   # noqa: E731
+    _, Y, _ = krylov.lanczos_ritz(G, S, precond, 60, 8)
+    b2 = np.random.default_rng(3).standard_normal(G.shape[0])
+    ref = spla.spsolve(G.tocsc(), b2)
+    _, it0, _ = krylov.deflated_pcg(G, b2, precond, np.zeros((G.shape[0], 0)), rtol=1e-10)
+    x, it, _ = krylov.deflated_pcg(G, b2, precond, Y, rtol=1e-10)
+    assert np.linalg.norm(x - ref) <= 1e-7 * np.linalg.norm(ref)
+    assert it < 0.85 * it0, (it, it0)
