@@ -11,8 +11,8 @@ Metric: time to solution (seconds per step, lower is better), mixed precision
 against FP64.  The default workload is the 3D transient Stokes problem on 64^3
 cubes (1,572,864 Kuhn tetrahedra, 9.4 M unknowns, nu = 1, dt = 1e-3).  `value`
 is the first solver of --precs (by default PCG in float-float with FP64
-reliable updates and the Chebyshev polynomial preconditioner, degree 12 in 3D and
-16 in 2D, its steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
+reliable updates and the Chebyshev polynomial preconditioner of degree 16, its
+steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
 and float-float variants, float-float and native FP64 Jacobi-PCG, the FP64
 Chebyshev PCG, float-float with BF16 low parts) is reported
 under "precisions" with its roofline and its speed-up over FP64 Jacobi-PCG,
@@ -86,9 +86,10 @@ def parse():
     ap.add_argument("--check-every", type=int, default=16,
                     help="iterations per convergence check (persistent: x64 iterations per launch)")
     ap.add_argument("--deflate", type=int, default=0,
-                    help="with --time-steps: also run the loop deflated by this many Ritz vectors, taken after "
-                         "the first step from --lanczos FP64 PCG steps on its right-hand side")
-    ap.add_argument("--lanczos", type=int, default=200, help="PCG steps of the Ritz vectors (--deflate)")
+                    help="with --time-steps: also run the loop deflated by this many Ritz vectors, recorded by "
+                         "the first step's solve over its first --lanczos iterations; with --steady: deflate the "
+                         "inner solves by Ritz vectors of their G (--lanczos FP64 PCG steps)")
+    ap.add_argument("--lanczos", type=int, default=200, help="PCG iterations that give the Ritz vectors (--deflate)")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="also time this many implicit Euler steps of the transient workload")
     ap.add_argument("--compare-coupled", action="store_true",
@@ -185,11 +186,12 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # Chebyshev degree and interval ratio per dimension.  Steps in FP32 (on FP32 or BF16
 # values) cost a fraction of a CG iteration's float-float SpMV, update and direction, so
 # those solvers take a high degree (fewer CG iterations, more steps); measured on the
-# 512^2 and 64^3 workloads: 2D degree 16 / ratio 1000 0.157 s against 0.256 s at degree 4,
-# 3D degree 12 / ratio 300 0.525 s against 0.666 s.  The float-float and FP64 steps cost
-# as much as the CG iteration itself and stay at degree 4.
-CHEB_DEGREE_FP32_STEPS = {2: 16, 3: 12}
-CHEB_RATIO_FP32_STEPS = {2: 1000.0, 3: 300.0}
+# 512^2 and 64^3 workloads: 2D degree 16 / ratio 3000 0.154 s against 0.256 s at degree
+# 4 / ratio 1000, 3D degree 16 / ratio 1000 0.488 s against 0.666 s at degree 4 / ratio
+# 100.  The float-float and FP64 steps cost as much as the CG iteration itself and stay
+# at degree 4.
+CHEB_DEGREE_FP32_STEPS = {2: 16, 3: 16}
+CHEB_RATIO_FP32_STEPS = {2: 3000.0, 3: 1000.0}
 
 
 def cheb_degree(args, prec, d):
@@ -555,6 +557,11 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                          poly_ratio=cheb_ratio(args, prec, d), poly_prec=PRECS[prec][0].get("poly_prec", "same"))
             if args.max_iter:
                 o["max_iter"] = args.max_iter
+            if args.deflate and prec in CHEB_PRECS:
+                # every inner solve shares G_mu: Ritz vectors of pre deflate them all (their Lanczos
+                # run is part of the step)
+                lo = {key: o[key] for key in ("precond", "poly_degree", "poly_ratio")}
+                o["deflation"] = crhyb.cr_deflation_lanczos(pre, args.lanczos, args.deflate, **lo)[0]
             # the steady solve writes device arrays: the end-to-end run copies them to its host buffers
             Ud = Ut if Ut.is_cuda else torch.zeros(Ut.shape, dtype=torch.float64, device="cuda")
             Pd = Pt if Pt.is_cuda else torch.zeros(Pt.shape, dtype=torch.float64, device="cuda")
@@ -826,12 +833,14 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                                          keep_bf16=(prec == "ff_chebbf"),
                                          keep_ff=(prec in ("ff", "ff_cheb", "ff_cheb32", "ff_chebbf")),
                                          keep_ff_bf16=(prec == "ff_bf16"))
-                st = crhyb.cr_solve(hyb, Wt, use_x0=k > 0, deflation=defl[0] if defl else None, **o)
+                if k_defl and not defl:
+                    # the first solve records its iterations and returns the Ritz vectors
+                    st, dsp, _ = crhyb.cr_solve_ritz(hyb, Wt, args.lanczos, k_defl, use_x0=k > 0, **o)
+                    defl.append(dsp)
+                else:
+                    st = crhyb.cr_solve(hyb, Wt, use_x0=k > 0, deflation=defl[0] if defl else None, **o)
                 crhyb.cr_recover_up(hyb, Wt, Ut, P, normalise_p=True)
                 iters.append(st["iterations"])
-                if k_defl and not defl:
-                    lo = {key: o[key] for key in ("precond", "poly_degree", "poly_ratio") if key in o}
-                    defl.append(crhyb.cr_deflation_lanczos(hyb, args.lanczos, k_defl, **lo)[0])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -851,8 +860,8 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                 "steps": args.time_steps, "value": tld / args.time_steps, "unit": "s per step", "precision": prec,
                 "iterations_per_step": iters_d, "vectors": kept, "lanczos_steps": args.lanczos,
                 "speedup": tl / tld,
-                "note": "the same loop; after the first step, Ritz vectors from FP64 PCG steps on its system "
-                        "(inside the timed region) deflate the solves of the later steps"}
+                "note": "the same loop; the first step's solve records its first iterations (cr_solve_ritz) and "
+                        "their Ritz vectors deflate the solves of the later steps"}
     if extras and args.compare_coupled and not newton:
         # the paper's comparison: the same coupled system solved without hybridisation
         # (assembly + preconditioned MINRES to the same relative residual), one warm-up and

@@ -114,7 +114,7 @@ enum cr_method { CR_METHOD_PCG = 0, CR_METHOD_GMRES = 1, CR_METHOD_BICGSTAB = 2 
  * its guarantees and takes about poly_degree times fewer iterations, each
  * applying G poly_degree times. */
 enum cr_precond { CR_PRECOND_JACOBI = 0, CR_PRECOND_CHEBYSHEV = 1 };
-#define CR_MAX_POLY_DEGREE 16
+#define CR_MAX_POLY_DEGREE 32
 
 typedef struct cr_hyb_opts {
     int32_t keep_fp32;  /* also keep FP32 values of G (needed by CR_PREC_MIXED_FP32) */
@@ -318,6 +318,22 @@ int cr_deflation_create(cr_hybrid* h, int k, const double* V, cr_deflation** out
 int cr_deflation_lanczos(cr_hybrid* h, int rhs, const cr_solve_opts* opts, int m, int k, double* theta,
                          cr_deflation** out);
 
+/* cr_solve that also returns a space of Ritz vectors from its own iterations:
+ * the first m iterations of the solve record q_j = z_j / sqrt(r_j . z_j) (FP32,
+ * m * n * 4 bytes of scratch) and the CG coefficients on the device, inside the
+ * solve's (graph-replayed) launch sequence, and the space follows from them as
+ * in cr_deflation_lanczos.  In the float-float form a reliable update rewrites
+ * the current vector with the one of the true residual and records the
+ * continued beta; a restarted direction (beta = 0) ends the record.  The first
+ * solve of a time loop thus yields the space for the later ones at the cost of
+ * writing m vectors.  PCG in FP64 (Jacobi or Chebyshev) or FF with the
+ * Chebyshev preconditioner, on the multi-kernel path (persistent is ignored),
+ * without deflation.  W, st, the return codes as for cr_solve (with
+ * CR_ERR_NOT_CONVERGED the space is still formed); theta and out as for
+ * cr_deflation_lanczos. */
+int cr_solve_ritz(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st, int m, int k,
+                  double* theta, cr_deflation** out);
+
 /* Vectors kept and their length. */
 int cr_deflation_info(const cr_deflation* d, int32_t* k, int64_t* n);
 
@@ -397,7 +413,11 @@ int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solv
  *         outer steps stall from about 384x384 squares on; an inner solve that
  *         stagnates stops at four times the iterations of the first one);
  *         max_iter caps the GMRES steps (default 1000); use_x0: U, P hold the
- *         start; check_every x 64 inner iterations per persistent launch
+ *         start; check_every x 64 inner iterations per persistent launch;
+ *         deflation: a space of pre's G (cr_deflation_lanczos on pre) deflates
+ *         every inner solve (G_mu does not change across the outer steps; the
+ *         inner solves then run on the multi-kernel path: FP64 with either
+ *         preconditioner, FF with CHEBYSHEV)
  *   U     device float64 [nf_int][dim]; P device float64 [ne] (P_{K_0} = 0, not
  *         normalised)
  *   st    iterations = inner PCG iterations in total, outer = GMRES steps,

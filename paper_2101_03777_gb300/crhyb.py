@@ -120,6 +120,8 @@ _SIGS = {
     "cr_deflation_create": (_i32, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "cr_deflation_lanczos": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_vp)]),
+    "cr_solve_ritz": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(cr_solve_opts), _vp, ctypes.POINTER(cr_solve_stats),
+                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_vp)]),
     "cr_deflation_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "cr_deflation_export": (_i32, [_vp, _vp]),
     "cr_destroy_deflation": (None, [_vp]),
@@ -384,6 +386,26 @@ def cr_solve(hyb, W, rhs=0, raise_on_error=True, **opts):
         if raise_on_error:
             _check(rc)
     return stats
+
+
+def cr_solve_ritz(hyb, W, m, k, rhs=0, raise_on_error=True, **opts):
+    """cr_solve that also returns a deflation space of k Ritz vectors from the Lanczos
+    record of its first m iterations.  Returns (statistics, Deflation or None, Ritz values)."""
+    o = make_solve_opts(**opts)
+    st = cr_solve_stats()
+    theta = (ctypes.c_double * int(k))()
+    h = _vp()
+    rc = load_library().cr_solve_ritz(hyb.handle, int(rhs), ctypes.byref(o), _ptr(W, np.float64, hyb.n, "W"),
+                                      ctypes.byref(st), int(m), int(k), theta, ctypes.byref(h))
+    stats = {"iterations": st.iterations, "outer": st.outer, "relres": st.relres, "status": st.status,
+             "status_name": "CR_OK" if rc == 0 else CR_ERR.get(rc, str(rc)),
+             "spmv_launches": st.spmv_launches, "spmv_ms": st.spmv_ms, "kernel_launches": st.kernel_launches}
+    if rc != CR_OK:
+        stats["error"] = load_library().cr_last_error().decode()
+        if raise_on_error:
+            _check(rc)
+    d = Deflation(h, hyb) if h.value else None
+    return stats, d, np.array(theta[:d.k]) if d is not None else np.zeros(0)
 
 
 def cr_solve_preconditioned(hyb, pre, W, rhs=0, raise_on_error=True, **opts):

@@ -372,40 +372,45 @@ static int check_deflation(const cr_deflation* d, const cr_hybrid* h, const cr_s
     return CR_OK;
 }
 
-extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+// The checks, the workspace and the staging of a host W shared by cr_solve and
+// cr_solve_ritz; `run` solves on the device copy.
+template <typename Run>
+static int solve_entry(const char* fn, cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st,
+                       Run run) {
+    const std::string f(fn);
     if (st) std::memset(st, 0, sizeof(*st));
-    if (!h || !o || !W) return fail(CR_ERR_ARG, "cr_solve: NULL argument");
-    CR_TRY(check_call(h->m, "cr_solve", {W}));
-    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, "cr_solve: rhs out of range");
+    if (!h || !o || !W) return fail(CR_ERR_ARG, f + ": NULL argument");
+    CR_TRY(check_call(h->m, fn, {W}));
+    if (rhs < 0 || rhs >= h->s->nrhs) return fail(CR_ERR_ARG, f + ": rhs out of range");
     if (o->method != CR_METHOD_PCG && o->method != CR_METHOD_GMRES && o->method != CR_METHOD_BICGSTAB)
-        return fail(CR_ERR_ARG, "cr_solve: bad method");
+        return fail(CR_ERR_ARG, f + ": bad method");
     if (o->method == CR_METHOD_BICGSTAB && o->prec != CR_PREC_FP64)
-        return fail(CR_ERR_ARG, "cr_solve: BiCGStab runs in FP64");
+        return fail(CR_ERR_ARG, f + ": BiCGStab runs in FP64");
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_MIXED_FP32 && o->prec != CR_PREC_MIXED_BF16 &&
         o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
-        return fail(CR_ERR_ARG, "cr_solve: bad precision");
-    if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve: tol must be > 0");
+        return fail(CR_ERR_ARG, f + ": bad precision");
+    if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, f + ": tol must be > 0");
     const int restart = o->restart > 0 ? o->restart : 30;
     if (o->method == CR_METHOD_GMRES && (restart < 1 || restart > CR_MAX_RESTART))
-        return fail(CR_ERR_ARG, "cr_solve: restart must be in [1, CR_MAX_RESTART]");
+        return fail(CR_ERR_ARG, f + ": restart must be in [1, CR_MAX_RESTART]");
     if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
-        return fail(CR_ERR_ARG, "cr_solve: bad preconditioner");
+        return fail(CR_ERR_ARG, f + ": bad preconditioner");
     if (o->precond == CR_PRECOND_CHEBYSHEV) {
         if (o->method != CR_METHOD_PCG ||
             (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16))
-            return fail(CR_ERR_ARG, "cr_solve: the Chebyshev preconditioner is implemented for PCG in FP64, FF and "
-                                    "FF_BF16");
+            return fail(CR_ERR_ARG, f + ": the Chebyshev preconditioner is implemented for PCG in FP64, FF and "
+                                        "FF_BF16");
         const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
         if (deg < 2 || deg > CR_MAX_POLY_DEGREE)
-            return fail(CR_ERR_ARG, "cr_solve: poly_degree must be in [2, CR_MAX_POLY_DEGREE]");
+            return fail(CR_ERR_ARG, f + ": poly_degree must be in [2, CR_MAX_POLY_DEGREE]");
         if (!(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
-            return fail(CR_ERR_ARG, "cr_solve: poly_ratio must be > 1 (or <= 0 for the default)");
+            return fail(CR_ERR_ARG, f + ": poly_ratio must be > 1 (or <= 0 for the default)");
         if (o->poly_prec != CR_POLY_SAME && o->poly_prec != CR_POLY_FP32 && o->poly_prec != CR_POLY_BF16)
-            return fail(CR_ERR_ARG, "cr_solve: bad poly_prec");
+            return fail(CR_ERR_ARG, f + ": bad poly_prec");
         if (o->poly_prec != CR_POLY_SAME && o->prec == CR_PREC_FP64)
-            return fail(CR_ERR_ARG, "cr_solve: poly_prec applies to the float-float Chebyshev PCG");
+            return fail(CR_ERR_ARG, f + ": poly_prec applies to the float-float Chebyshev PCG");
     }
-    if (o->deflation) CR_TRY(check_deflation(o->deflation, h, o, "cr_solve"));
+    if (o->deflation) CR_TRY(check_deflation(o->deflation, h, o, fn));
     cr_mesh* m = h->m;
     const size_t n = size_t(m->nf) * m->d;
     StreamScope scope(m);
@@ -421,13 +426,34 @@ extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W
         Wd = h->stage;
         if (o->use_x0) CR_CUDA(cudaMemcpyAsync(Wd, W, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
     }
-    int rc = solve_impl(h, rhs, o, Wd, st);
+    int rc = run(Wd);
     if (host) {
         cudaError_t e = cudaMemcpyAsync(W, Wd, n * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-        if (e != cudaSuccess && rc == CR_OK) rc = cuda_fail(e, "cr_solve: copy of W");
+        if (e != cudaSuccess && rc == CR_OK) rc = cuda_fail(e, (f + ": copy of W").c_str());
     }
     return rc;
+}
+
+extern "C" int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
+    return solve_entry("cr_solve", h, rhs, o, W, st, [&](double* Wd) { return solve_impl(h, rhs, o, Wd, st); });
+}
+
+extern "C" int cr_solve_ritz(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st, int m,
+                             int k, double* theta, cr_deflation** out) {
+    if (!theta || !out) return fail(CR_ERR_ARG, "cr_solve_ritz: NULL argument");
+    *out = nullptr;
+    if (!h || !o) return fail(CR_ERR_ARG, "cr_solve_ritz: NULL argument");
+    if (k < 1 || k > CR_MAX_DEFLATION || m < k || m > CR_MAX_LANCZOS)
+        return fail(CR_ERR_ARG, "cr_solve_ritz: need 1 <= k <= CR_MAX_DEFLATION and k <= m <= CR_MAX_LANCZOS");
+    if (o->method != CR_METHOD_PCG || o->deflation ||
+        !(o->prec == CR_PREC_FP64 || (o->prec == CR_PREC_FF && o->precond == CR_PRECOND_CHEBYSHEV)))
+        return fail(CR_ERR_ARG, "cr_solve_ritz: records PCG in FP64 (Jacobi or Chebyshev) or float-float Chebyshev "
+                                "PCG, without deflation");
+    if (h->s->conv != CR_CONV_NONE || !(h->s->mu > 0.0))
+        return fail(CR_ERR_ARG, "cr_solve_ritz: needs the SPD G of a transient Stokes system");
+    return solve_entry("cr_solve_ritz", h, rhs, o, W, st,
+                       [&](double* Wd) { return solve_ritz_impl(h, rhs, o, Wd, st, m, k, theta, out); });
 }
 
 // ---- deflation spaces ---------------------------------------------------------
@@ -578,6 +604,11 @@ extern "C" int cr_solve_steady(cr_system* sys, cr_hybrid* pre, int rhs, const cr
         return fail(CR_ERR_ARG, "cr_solve_steady: restart must be in [1, CR_MAX_RESTART]");
     if (!is_device_pointer(U) || !is_device_pointer(P))
         return fail(CR_ERR_ARG, "cr_solve_steady: U and P must be device pointers");
+    if (o->deflation) {   // a space of pre's G deflates every inner solve
+        cr_solve_opts io = *o;
+        io.method = CR_METHOD_PCG;
+        CR_TRY(check_deflation(o->deflation, pre, &io, "cr_solve_steady"));
+    }
     cr_mesh* m = sys->m;
     StreamScope scope(m);
     CR_TRY(ensure_workspace(pre, false, 0, o->prec));
@@ -613,6 +644,11 @@ extern "C" int cr_solve_newton(cr_mesh* m, double nu, const double* fbar, cr_hyb
         return fail(CR_ERR_ARG, "cr_solve_newton: bad tol or restart of the linear solves");
     if (!is_device_pointer(U) || !is_device_pointer(P))
         return fail(CR_ERR_ARG, "cr_solve_newton: U and P must be device pointers");
+    if (lin->deflation) {   // a space of pre's G deflates the inner solves (FP64 Jacobi PCG)
+        cr_solve_opts io = *lin;
+        io.method = CR_METHOD_PCG;
+        CR_TRY(check_deflation(lin->deflation, pre, &io, "cr_solve_newton"));
+    }
     StreamScope scope(m);
     CR_TRY(ensure_workspace(pre, false, 0, lin->prec));
     return solve_newton_impl(m, nu, fbar, pre, lin, newton_tol, max_newton, U, P, st);

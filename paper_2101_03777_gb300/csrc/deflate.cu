@@ -76,9 +76,24 @@ __global__ void __launch_bounds__(kDeflBlock) k_defl_dots(int64_t n, const YT* _
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // the per-block partials summed by the whole block (fixed order: deterministic)
+#pragma unroll
+    for (int i = 0; i < kMaxDefl; ++i) acc[i] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < kMaxDefl; ++i)
+            if (i < k) acc[i] += __ldcg(dd.partial + size_t(i) * kMaxDeflBlocks + b);
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxDefl; ++i) {
+        if (i >= k) break;
+        const double a = warp_sum(acc[i]);
+        if (lane == 0) sh[i][warp] = a;
+    }
+    __syncthreads();
     if (threadIdx.x < k) {
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(dd.partial + size_t(threadIdx.x) * kMaxDeflBlocks + b);
+        for (int w = 0; w < kDeflBlock / 32; ++w) s += sh[threadIdx.x][w];
         tot[threadIdx.x] = s;
     }
     __syncthreads();

@@ -292,6 +292,8 @@ int ritz_vectors(int64_t n, int m, int k, const float* Q, const double* S, doubl
 void tridiag_smallest_eigen(const std::vector<double>& a, const std::vector<double>& b, int k,
                             std::vector<double>& theta, std::vector<double>& S);
 int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out);
+int solve_ritz_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st, int m, int k,
+                    double* theta, cr_deflation** out);
 void destroy_persistent_plans(cr_hybrid* h);
 size_t kscal_bytes();
 

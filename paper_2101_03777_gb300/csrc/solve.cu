@@ -503,6 +503,50 @@ __global__ void __launch_bounds__(kBlock) k_spmv64(int64_t nf, const int32_t* __
 }
 
 // ---------------------------------------------------------------------------
+// Lanczos record of a PCG solve (cr_solve_ritz): after the direction of
+// iteration `it` (sc->it CG steps done, z_it and r_it.z_it = sc->rz in place), the
+// normalised preconditioned residual q_it = z_it / sqrt(r_it.z_it) goes to slot it
+// of Q (FP32) and the step's alpha_{it-1}, beta_{it-1} to the history.  The
+// quantities are those of the scaled float-float vectors where they are scaled (q is
+// scale-invariant).  A reliable update rewrites slot it with the z of the true
+// residual and the continued beta; a restarted direction (beta = 0) ends the record.
+// ---------------------------------------------------------------------------
+struct LanczosRec {
+    float* Q = nullptr;      // [m][n]
+    double* ab = nullptr;    // [2][m]: alpha_j, then beta_j
+    int* count = nullptr;    // slots written (q_0 .. q_{count-1})
+    int* stop = nullptr;     // set: the record has ended
+    int m = 0;
+};
+
+__device__ __forceinline__ double rec_val(double v) { return v; }
+__device__ __forceinline__ double rec_val(float v) { return double(v); }
+__device__ __forceinline__ double rec_val(float2 v) { return double(v.x) + double(v.y); }
+
+template <typename ZT>
+__global__ void __launch_bounds__(kBlock) k_lanczos_record(int64_t n, const ZT* __restrict__ z,
+                                                           const double* __restrict__ minv,
+                                                           const double* __restrict__ r, const KScal* sc,
+                                                           LanczosRec rec) {
+    if (sc->done || *rec.stop) return;
+    const int it = sc->it;
+    if (it >= rec.m || !(sc->rz > 0.0)) return;
+    const double scale = 1.0 / sqrt(sc->rz);
+    float* q = rec.Q + size_t(it) * n;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double zj = z ? rec_val(z[j]) : minv[j] * r[j];
+        q[j] = __double2float_rn(zj * scale);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (it > 0) {
+            rec.ab[it - 1] = sc->alpha;
+            rec.ab[rec.m + it - 1] = sc->beta;
+        }
+        *rec.count = it + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Float-float PCG kernels.  Vectors are float2 (hi, lo) per unknown; G is the
 // FP32 plane val32 (hi) plus a low plane (FP32 or BF16) holding G - hi.
 // Dot products are Dot2 sums reduced in float-float through the block and
@@ -2002,7 +2046,7 @@ int chebyshev_setup(cr_hybrid* h, const cr_solve_opts* o, cudaStream_t st, KScal
 
 template <int D>
 int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st,
-              const double* b_override = nullptr) {
+              const double* b_override = nullptr, const LanczosRec* rec = nullptr) {
     cr_mesh* m = h->m;
     Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D,
           o->profile != 0};
@@ -2019,6 +2063,25 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
     const cr_deflation* dfl = o->deflation;   // checked against h by the caller
     const int* done = &c.sc->done;            // device flag: the deflation kernels skip a finished solve
     const uint64_t dtag = dfl ? dfl->serial : 0;
+    // the Lanczos record: after every direction; a restarted direction after the first ends it
+    bool rec_started = false;
+    auto record = [&](const void* z, int kind, bool restart) {   // kind 0: FP64 z (null: M^{-1} r), 1: FP32, 2: FF
+        if (!rec) return;
+        if (restart && rec_started) cudaMemsetAsync(rec->stop, 0xff, sizeof(int), c.st);
+        rec_started = true;
+        const int g = grid_for(c.n);
+        if (kind == 1)
+            k_lanczos_record<float><<<g, kBlock, 0, c.st>>>(c.n, static_cast<const float*>(z), h->minv64, h->r64,
+                                                            c.sc, *rec);
+        else if (kind == 2)
+            k_lanczos_record<float2><<<g, kBlock, 0, c.st>>>(c.n, static_cast<const float2*>(z), h->minv64,
+                                                             h->r64, c.sc, *rec);
+        else
+            k_lanczos_record<double><<<g, kBlock, 0, c.st>>>(c.n, static_cast<const double*>(z), h->minv64,
+                                                             h->r64, c.sc, *rec);
+        ++c.launches;
+    };
+    const int rtag = rec ? 1 << 11 : 0;   // graph variant of recording iterations
 
     std::memset(c.hs, 0, sizeof(KScal));
     c.hs->max_it = gmax;
@@ -2090,6 +2153,7 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 k_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->p64, zb[(deg - 1) & 1], c.sc, first);
                 if (dfl) defl_project64(dfl, h->p64, done, c.st);
                 c.launches += dfl ? 3 : 1;
+                record(zb[(deg - 1) & 1], 0, first != 0);
             };
             auto start = [&]() {
                 k_cheb_start<<<gn, kBlock, 0, c.st>>>(c.n, h->r64, h->minv64, zb[0], dv, c.sc);
@@ -2108,8 +2172,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 c.launches += 2;
             };
             CR_TRY(restarted_pcg<D>(
-                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 6, deg + (dfl ? 512 : 0), dtag); }, b,
-                max_outer, o->tol, outer, dfl));
+                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 6, deg + (dfl ? 512 : 0) + rtag, dtag); },
+                b, max_outer, o->tol, outer, dfl));
         } else if (o->method == CR_METHOD_PCG) {
             // deflated (Jacobi): c = E^{-1} (M^{-1} G V)^t r = E^{-1} (G V)^t z, p -= V c
             auto start = [&]() {
@@ -2120,10 +2184,12 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                     defl_project64(dfl, h->p64, done, c.st);
                     c.launches += 2;
                 }
+                record(nullptr, 0, true);
             };
             auto iter = [&](cudaEvent_t e0, cudaEvent_t e1) {
                 if (!dfl) {
                     pcg_iteration<D, double, double>(c, h->val64, h->minv64, h->x64, h->r64, h->p64, h->q64, e0, e1);
+                    record(nullptr, 0, false);
                     return;
                 }
                 if (e0) cudaEventRecord(e0, c.st);
@@ -2138,8 +2204,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 c.launches += 5;
             };
             CR_TRY(restarted_pcg<D>(
-                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 0, dfl ? 512 : 0, dtag); }, b, max_outer,
-                o->tol, outer, dfl));
+                c, start, [&]() { return pcg_loop(c, iter, chunk, graph, 0, (dfl ? 512 : 0) + rtag, dtag); }, b,
+                max_outer, o->tol, outer, dfl));
         } else {
             CR_TRY((gmres_loop<D, double, double>(c, h->val64, h->minv64, b, h->x64, h->r64, h->V64, h->Z64)));
         }
@@ -2211,6 +2277,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 else kf_cpcg_dir<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zb[(deg - 1) & 1], c.sc, first);
                 if (dfl) defl_projectff(dfl, h->pf, done, c.st);
                 c.launches += dfl ? 3 : 1;
+                if (pp != CR_POLY_SAME) record(zs[(deg - 1) & 1], 1, first != 0);
+                else record(zb[(deg - 1) & 1], 2, first != 0);
             };
             auto restart_direction = [&](int first) {
                 if (pp != CR_POLY_SAME) kf_cheb_start32<<<gn, kBlock, 0, c.st>>>(c.n, h->rf, h->minv32, zs[0], ds, c.sc);
@@ -2265,7 +2333,8 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 c.launches += 2;
             };
             while (status == CR_OK && !c.hs->conv) {
-                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp + (dfl ? 4096 : 0), dtag));
+                CR_TRY(pcg_loop(c, iter, chunk, graph, 7, deg + (bf ? 100 : 0) + 1000 * pp + (dfl ? 4096 : 0) + 4 * rtag,
+                                dtag));
                 CR_TRY(read_scal(c));
                 const int dev_status = c.hs->status;
                 if (dev_status == CR_ERR_TIMEOUT) { status = CR_ERR_TIMEOUT; break; }
@@ -2506,7 +2575,9 @@ int solve_steady(cr_coupled* cpl, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_
     const int g = grid_for(n), gN = grid_for(N);
     const int mode = persistent_mode(o->prec);
     const double itol = o->inner_tol > 0 && o->inner_tol < 1 ? o->inner_tol : 1e-6;
-    const bool cheb_inner = o->precond == CR_PRECOND_CHEBYSHEV;
+    // the multi-kernel inner PCG: Chebyshev-preconditioned, or deflated (a space of G_mu serves
+    // every inner solve: G_mu does not change across the outer steps)
+    const bool cheb_inner = o->precond == CR_PRECOND_CHEBYSHEV || o->deflation;
     const int gmax = o->max_iter > 0 ? o->max_iter : 1000;
     const int per_launch = (o->check_every > 0 ? o->check_every : 16) * 64;
     const double mu = pre->s->mu;
@@ -2559,7 +2630,7 @@ int solve_steady(cr_coupled* cpl, cr_mesh* m, cr_hybrid* pre, int rhs, const cr_
                 // four times the first one's iterations; the flexible outer step takes what it returns
                 int inner_it = 0, inner_status = CR_OK;
                 if (cheb_inner) {
-                    // Chebyshev-preconditioned PCG (multi-kernel, graph-replayed) on G_mu
+                    // Chebyshev-preconditioned or deflated PCG (multi-kernel, graph-replayed) on G_mu
                     cr_solve_opts io = *o;
                     io.method = CR_METHOD_PCG;
                     io.tol = itol;
@@ -2796,6 +2867,46 @@ int solve_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* Wdev, cr_s
     return h->m->d == 2 ? solve_dim<2>(h, rhs, o, Wdev, st) : solve_dim<3>(h, rhs, o, Wdev, st);
 }
 
+// A deflation space of Ritz vectors from the Lanczos data of a PCG run: T with
+// diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j
+// (j < mm = alpha.size(); Saad, Iterative Methods for Sparse Linear Systems, Section
+// 6.7.3), its k smallest eigenpairs on the host, Y = Q S on the device (Q: the mm
+// FP32 vectors q_j), then the space (defl_build).  theta [k] gets the Ritz values of
+// the vectors kept (0 after them).
+int ritz_space(cr_hybrid* h, const float* Q, const std::vector<double>& alpha, const std::vector<double>& beta, int k,
+               double* theta, cr_deflation** out, cudaStream_t st) {
+    const int mm = int(alpha.size());
+    const int64_t n = h->m->nf * h->m->d;
+    std::vector<double> ta(mm), tb(mm > 1 ? mm - 1 : 0);
+    for (int j = 0; j < mm; ++j) {
+        ta[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < mm) tb[j] = -std::sqrt(beta[j]) / alpha[j];
+    }
+    std::vector<double> th, S;
+    tridiag_smallest_eigen(ta, tb, k, th, S);
+    const int kk = int(th.size());
+    struct Tmp {
+        DevArena a;
+        ~Tmp() { a.release(); }
+    } tmp;
+    double* Sd = nullptr;
+    CR_TRY(tmp.a.alloc_n(&Sd, S.size()));
+    CR_CUDA(cudaMemcpyAsync(Sd, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice, st));
+    cr_deflation* d = nullptr;
+    CR_TRY(defl_alloc(h, kk, &d));
+    CR_TRY(ritz_vectors(n, mm, kk, Q, Sd, d->V64, st));
+    CR_CUDA(cudaGetLastError());
+    int rc = defl_build(d, h, st);
+    if (rc != CR_OK) {
+        d->arena.release();
+        delete d;
+        return rc;
+    }
+    for (int a = 0; a < k; ++a) theta[a] = a < d->k ? th[d->kept[a]] : 0.0;
+    *out = d;
+    return CR_OK;
+}
+
 // Ritz vectors for a deflation space from m steps of FP64 PCG (Jacobi or Chebyshev,
 // as opts says) on right-hand side rhs from x = 0: the normalised preconditioned
 // residuals q_j = z_j / sqrt(r_j.z_j) are stored in FP32, the Lanczos matrix T (its
@@ -2867,32 +2978,48 @@ int lanczos_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, int mmax, int k, 
         if (c.hs->done || !(c.hs->rz > 0.0) || !std::isfinite(c.hs->beta)) break;   // r = 0: the space is exact
         if (j + 1 < mmax) CR_TRY(lanczos_store(c.n, zcur, h->minv64, h->r64, &c.sc->rz, Q + size_t(j + 1) * c.n, c.st));
     }
-    const int mm = int(alpha.size());
-    if (mm == 0) return fail(CR_ERR_BREAKDOWN, "cr_deflation_lanczos: the first CG step broke down");
-    std::vector<double> ta(mm), tb(mm > 1 ? mm - 1 : 0);
-    for (int j = 0; j < mm; ++j) {
-        ta[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
-        if (j + 1 < mm) tb[j] = -std::sqrt(beta[j]) / alpha[j];
-    }
-    std::vector<double> th, S;
-    tridiag_smallest_eigen(ta, tb, k, th, S);
-    const int kk = int(th.size());
-    double* Sd = nullptr;
-    CR_TRY(tmp.a.alloc_n(&Sd, S.size()));
-    CR_CUDA(cudaMemcpyAsync(Sd, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice, c.st));
-    cr_deflation* d = nullptr;
-    CR_TRY(defl_alloc(h, kk, &d));
-    CR_TRY(ritz_vectors(c.n, mm, kk, Q, Sd, d->V64, c.st));
-    CR_CUDA(cudaGetLastError());
-    int rc = defl_build(d, h, c.st);
-    if (rc != CR_OK) {
-        d->arena.release();
-        delete d;
-        return rc;
-    }
-    for (int a = 0; a < k; ++a) theta[a] = a < d->k ? th[d->kept[a]] : 0.0;
-    *out = d;
-    return CR_OK;
+    if (alpha.empty()) return fail(CR_ERR_BREAKDOWN, "cr_deflation_lanczos: the first CG step broke down");
+    return ritz_space(h, Q, alpha, beta, k, theta, out, c.st);
+}
+
+// cr_solve on the multi-kernel path with the Lanczos record of its first m
+// iterations, then the space of k Ritz vectors from it.
+template <int D>
+int solve_ritz_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st, int m, int k,
+                   double* theta, cr_deflation** out) {
+    const int64_t n = h->m->nf * D;
+    cudaStream_t s = h->m->stream;
+    struct Tmp {
+        DevArena a;
+        ~Tmp() { a.release(); }
+    } tmp;
+    LanczosRec rec;
+    rec.m = m;
+    CR_TRY(tmp.a.alloc_n(&rec.Q, size_t(m) * size_t(n)));
+    CR_TRY(tmp.a.alloc_n(&rec.ab, size_t(2) * m));
+    CR_TRY(tmp.a.alloc_n(&rec.count, 2));
+    rec.stop = rec.count + 1;
+    CR_CUDA(cudaMemsetAsync(rec.count, 0, 2 * sizeof(int), s));
+    const int rc = solve_dim<D>(h, rhs, o, W, st, nullptr, &rec);
+    if (rc != CR_OK && rc != CR_ERR_NOT_CONVERGED) return rc;
+    int cnt = 0;
+    std::vector<double> ab(size_t(2) * m);
+    CR_CUDA(cudaMemcpyAsync(&cnt, rec.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CR_CUDA(cudaMemcpyAsync(ab.data(), rec.ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost, s));
+    CR_CUDA(cudaStreamSynchronize(s));
+    // q_0 .. q_{cnt-1} and the steps between them: alpha_j, beta_j for j < cnt - 1, and
+    // T of size cnt - 1 (the last vector closes no step)
+    const int mm = cnt - 1;
+    if (mm < 1) return fail(CR_ERR_ARG, "cr_solve_ritz: the solve ended before its first CG step");
+    std::vector<double> alpha(ab.begin(), ab.begin() + mm), beta(ab.begin() + m, ab.begin() + m + mm);
+    const int rs = ritz_space(h, rec.Q, alpha, beta, k, theta, out, s);
+    return rs != CR_OK ? rs : rc;
+}
+
+int solve_ritz_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st, int m, int k,
+                    double* theta, cr_deflation** out) {
+    return h->m->d == 2 ? solve_ritz_dim<2>(h, rhs, o, W, st, m, k, theta, out)
+                        : solve_ritz_dim<3>(h, rhs, o, W, st, m, k, theta, out);
 }
 
 int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out) {

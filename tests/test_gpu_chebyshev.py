@@ -141,7 +141,7 @@ def test_zero_source_and_iteration_limit():
 def test_bad_options_are_refused():
     G, S, ref, mesh, hyb = case("cfg2", 29)
     W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
-    bad = [dict(prec="mixed"), dict(method="gmres"), dict(poly_degree=1), dict(poly_degree=17),
+    bad = [dict(prec="mixed"), dict(method="gmres"), dict(poly_degree=1), dict(poly_degree=33),
            dict(poly_prec="fp32"),   # reduced-precision steps apply to the float-float PCG only
            dict(poly_ratio=0.5), dict(poly_ratio=1.0)]
     for b in bad:

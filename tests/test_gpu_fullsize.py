@@ -31,6 +31,7 @@ to 512x512, 14,693 iterations, and diverges at 1024x1024).
 import numpy as np
 import pytest
 
+import bench
 import synth
 from oracle import coupled, hybrid, pipeline, topology
 from paper_2101_03777_gb300 import crhyb
@@ -76,10 +77,10 @@ CASES = [
     ("cfg3", dict(method="pcg", prec="fp64", persistent=True), False),
     ("cfg3", dict(method="pcg", prec="ff", persistent=True), False),
     # the bench's headline solver with its degrees and ratios
-    ("cfg3", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=12, poly_ratio=300.0, use_graph=True,
-                  poly_prec="bf16"), False),
-    ("cfg2", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=16, poly_ratio=1000.0, use_graph=True,
-                  poly_prec="bf16"), True),
+    ("cfg3", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=bench.CHEB_DEGREE_FP32_STEPS[3],
+                  poly_ratio=bench.CHEB_RATIO_FP32_STEPS[3], use_graph=True, poly_prec="bf16"), False),
+    ("cfg2", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=bench.CHEB_DEGREE_FP32_STEPS[2],
+                  poly_ratio=bench.CHEB_RATIO_FP32_STEPS[2], use_graph=True, poly_prec="bf16"), True),
     ("cfg5", dict(method="stokes-fgmres", prec="ff"), True),
 ]
 

@@ -41,6 +41,7 @@ from concurrent.futures import ProcessPoolExecutor
 import numpy as np
 import pytest
 
+import bench
 import fullsize_truth as truth
 import synth
 from paper_2101_03777_gb300 import crhyb
@@ -114,11 +115,12 @@ SOLVERS = {
                                      poly_prec="fp32"), 1e-9),
     "ff-chebyshev-bf16-steps": (dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=4, use_graph=True,
                                      poly_prec="bf16"), 1e-9),
-    # the bench's headline: degree 16, ratio 1000 in 2D; degree 12, ratio 300 in 3D
+    # the bench's headline solver with the bench's degree and ratio per dimension
     "ff-chebyshev-bf16-steps-bench-degree": (dict(method="pcg", prec="ff", precond="chebyshev", use_graph=True,
                                                   poly_prec="bf16"), 1e-9),
 }
-BENCH_DEGREE = {2: dict(poly_degree=16, poly_ratio=1000.0), 3: dict(poly_degree=12, poly_ratio=300.0)}
+BENCH_DEGREE = {d: dict(poly_degree=bench.CHEB_DEGREE_FP32_STEPS[d], poly_ratio=bench.CHEB_RATIO_FP32_STEPS[d])
+                for d in (2, 3)}
 CASES_2D = list(SOLVERS)
 CASES_3D = ["fp64-persistent", "ff-persistent", "ff-three-kernel", "fp64-chebyshev", "ff-chebyshev",
             "ff-chebyshev-fp32-steps", "ff-chebyshev-bf16-steps", "ff-chebyshev-bf16-steps-bench-degree"]

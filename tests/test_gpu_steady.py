@@ -187,3 +187,35 @@ def test_newton_loop_to_the_paper_tolerance():
     st = crhyb.cr_solve_newton(mesh, nu, fb, pre, U, P, newton_tol=5e-7, max_newton=20, tol=1e-10, restart=60)
     assert st["status"] == 0 and st["increment"] <= 5e-7 and st["iterations"] <= 8, st
     assert st["residual"] <= 1e-8 and st["first_residual"] == pytest.approx(1.0), st
+
+
+def test_deflated_inner_solves_reach_the_same_steady_solution():
+    """Ritz vectors of the preconditioning system's G (which every inner solve shares)
+    deflate the inner float-float Chebyshev PCG: the steady solution at 128 x 128 is the
+    undeflated one within 1e-9, with fewer inner iterations."""
+    coords, elems, fbar, w = problem(2, 128, "newton")
+    mesh = crhyb.cr_mesh_load(coords, elems)
+    fb = torch.from_numpy(fbar).cuda()
+    wt = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    sysm = crhyb.cr_assemble_coupled(mesh, 0.01, 0.0, fb, conv="newton", w=wt)
+    pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1.0, fb), keep_fp32=True, keep_bf16=True,
+                             keep_ff=True)
+    cheb = dict(precond="chebyshev", poly_degree=8, poly_ratio=1000.0)
+    d, _ = crhyb.cr_deflation_lanczos(pre, 120, 8, **cheb)
+    out = []
+    for defl in (None, d):
+        U = torch.zeros(mesh.nf * 2, dtype=torch.float64, device="cuda")
+        P = torch.zeros(mesh.ne, dtype=torch.float64, device="cuda")
+        st = crhyb.cr_solve_steady(sysm, pre, U, P, tol=1e-11, prec="ff", poly_prec="bf16", restart=60,
+                                   deflation=defl, **cheb)
+        assert st["status"] == 0 and st["relres"] <= 1e-11
+        out.append((st, U.cpu().numpy()))
+    (st0, U0), (st1, U1) = out
+    assert rel(U1, U0) <= 1e-9
+    assert st1["iterations"] < st0["iterations"], (st1["iterations"], st0["iterations"])
+    # a space of another G is refused
+    other = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 2.0, fb), keep_ff=True)
+    d2, _ = crhyb.cr_deflation_lanczos(other, 20, 2)
+    with pytest.raises(crhyb.CrError) as ei:
+        crhyb.cr_solve_steady(sysm, pre, U, P, prec="ff", deflation=d2, **cheb)
+    assert ei.value.name == "CR_ERR_ARG"

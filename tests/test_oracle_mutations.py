@@ -144,6 +144,17 @@ CASES = [
     ("deflated_pcg", krylov,
      _edited(krylov, "deflated_pcg", "p = project(z) + (rz_new / rz) * p", "p = z + (rz_new / rz) * p"),   # no projection
      lambda: tdf.test_residuals_stay_orthogonal_to_the_vectors()),
+    ("lanczos_ritz", krylov,
+     _edited(krylov, "lanczos_ritz", "T[j, j + 1] = T[j + 1, j] = -np.sqrt(betas[j]) / alphas[j]",
+             "T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]"),               # off-diagonal sign
+     lambda: tdf.test_lanczos_matrix_is_q_transpose_g_q()),
+    ("lanczos_ritz", krylov,
+     _edited(krylov, "lanczos_ritz", "T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)",
+             "T[j, j] = 1.0 / alphas[j]"),                                                  # beta/alpha term dropped
+     lambda: tdf.test_full_lanczos_gives_the_exact_smallest_eigenvalues()),
+    ("lanczos_ritz", krylov,
+     _edited(krylov, "lanczos_ritz", "Q.append(z / np.sqrt(rz))", "Q.append(z)"),       # unnormalised vectors
+     lambda: tdf.test_lanczos_matrix_is_q_transpose_g_q()),
     ("gmres", krylov, wrong_gmres, lambda: tk.test_gmres_cycle_is_the_minimal_residual_iterate(6)),
     ("chebyshev_apply", krylov, chebyshev_variant(start_width=True), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
     ("chebyshev_apply", krylov, chebyshev_variant(rho_sign=-1.0), lambda: tc.test_eigenvectors_get_the_closed_form(3)),
