@@ -11,7 +11,7 @@ Metric: time to solution (seconds per step, lower is better), mixed precision
 against FP64.  The default workload is the 3D transient Stokes problem on 64^3
 cubes (1,572,864 Kuhn tetrahedra, 9.4 M unknowns, nu = 1, dt = 1e-3).  `value`
 is the first solver of --precs (by default PCG in float-float with FP64
-reliable updates and the Chebyshev polynomial preconditioner of degree 16, its
+reliable updates and the Chebyshev polynomial preconditioner of degree 24, its
 steps in FP32 on BF16 values of G); every timed solver (that one, its FP32-value
 and float-float variants, float-float and native FP64 Jacobi-PCG, the FP64
 Chebyshev PCG, float-float with BF16 low parts) is reported
@@ -186,12 +186,12 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (non-tensor)
 # Chebyshev degree and interval ratio per dimension.  Steps in FP32 (on FP32 or BF16
 # values) cost a fraction of a CG iteration's float-float SpMV, update and direction, so
 # those solvers take a high degree (fewer CG iterations, more steps); measured on the
-# 512^2 and 64^3 workloads: 2D degree 16 / ratio 3000 0.154 s against 0.256 s at degree
-# 4 / ratio 1000, 3D degree 16 / ratio 1000 0.488 s against 0.666 s at degree 4 / ratio
-# 100.  The float-float and FP64 steps cost as much as the CG iteration itself and stay
-# at degree 4.
-CHEB_DEGREE_FP32_STEPS = {2: 16, 3: 16}
-CHEB_RATIO_FP32_STEPS = {2: 3000.0, 3: 1000.0}
+# 512^2 and 64^3 workloads: 2D degree 24 / ratio 10000 0.145 s against 0.256 s at degree
+# 4 / ratio 1000, 3D degree 24 / ratio 3000 0.471 s against 0.666 s at degree 4 / ratio
+# 100 (degrees 16 to 32 lie within 4% of these).  The float-float and FP64 steps cost as
+# much as the CG iteration itself and stay at degree 4.
+CHEB_DEGREE_FP32_STEPS = {2: 24, 3: 24}
+CHEB_RATIO_FP32_STEPS = {2: 10000.0, 3: 3000.0}
 
 
 def cheb_degree(args, prec, d):

@@ -288,8 +288,11 @@ int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_sol
  * holds at most CR_MAX_DEFLATION vectors V of length n = dim * nf_int, rounded
  * to FP32 on entry (the FP64 and float-float solvers then deflate the same
  * space), with G V, M^{-1} G V and the Cholesky factor of E = V^t G V on the
- * device.  A vector whose Cholesky pivot falls below 1e-10 of its diagonal
- * entry lies (numerically) in the span of those before it and is dropped;
+ * device.  A vector whose Cholesky pivot falls below 1e-2 of its diagonal
+ * entry (the sine of its G-angle to the span of those before it below 0.1) is
+ * dropped, which keeps E well conditioned for the FP32 dot products of the
+ * float-float solves: Ritz vectors are G-orthogonal and pass, while the
+ * near-copies that the loss of orthogonality of Lanczos produces do not;
  * cr_deflation_info gives the count kept.  The space serves every system of
  * the same mesh, nu and mu without convection.  Destroy it before its mesh. */
 #define CR_MAX_DEFLATION 16

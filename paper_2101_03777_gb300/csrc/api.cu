@@ -522,7 +522,8 @@ extern "C" int cr_deflation_export(const cr_deflation* d, double* V) {
 
 extern "C" void cr_destroy_deflation(cr_deflation* d) {
     if (!d) return;
-    cudaStreamSynchronize(d->m->stream);
+    // cudaFree waits for the device; the mesh (and its stream), which may be gone
+    // already, is not touched here
     d->arena.release();
     delete d;
 }

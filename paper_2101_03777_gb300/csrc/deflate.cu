@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -25,6 +26,7 @@ namespace crhyb {
 namespace {
 
 constexpr int kDeflBlock = 256;
+constexpr double kDeflPivot = 1e-2;   // kept: sine of the G-angle to the span before it >= 0.1
 
 __device__ __forceinline__ double as_double(double v) { return v; }
 __device__ __forceinline__ double as_double(float v) { return double(v); }
@@ -48,11 +50,30 @@ __global__ void __launch_bounds__(kDeflBlock) k_defl_dots(int64_t n, const YT* _
     double acc[kMaxDefl];
 #pragma unroll
     for (int i = 0; i < kMaxDefl; ++i) acc[i] = 0.0;
-    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
-        const double vj = as_double(v[j]);
+    if constexpr (std::is_same<YT, float>::value) {
+        // FP32 vectors (the float-float solves): FP32 products, a thread's few terms summed
+        // in FP32, the rest of the reduction in FP64 (the projection is accurate to FP32
+        // anyway); the FP64 pipe would bound a kernel that streams k FP32 vectors
+        float accf[kMaxDefl];
 #pragma unroll
-        for (int i = 0; i < kMaxDefl; ++i)
-            if (i < k) acc[i] = fma(as_double(Y[size_t(i) * n + j]), vj, acc[i]);
+        for (int i = 0; i < kMaxDefl; ++i) accf[i] = 0.f;
+        for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+             j += int64_t(gridDim.x) * blockDim.x) {
+            const float vj = float(as_double(v[j]));
+#pragma unroll
+            for (int i = 0; i < kMaxDefl; ++i)
+                if (i < k) accf[i] = fmaf(Y[size_t(i) * n + j], vj, accf[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxDefl; ++i) acc[i] = double(accf[i]);
+    } else {
+        for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+             j += int64_t(gridDim.x) * blockDim.x) {
+            const double vj = as_double(v[j]);
+#pragma unroll
+            for (int i = 0; i < kMaxDefl; ++i)
+                if (i < k) acc[i] = fma(as_double(Y[size_t(i) * n + j]), vj, acc[i]);
+        }
     }
     __shared__ double sh[kMaxDefl][kDeflBlock / 32];
     __shared__ double tot[kMaxDefl];
@@ -186,23 +207,24 @@ __global__ void __launch_bounds__(kDeflBlock) k_lanczos_store(int64_t n, const d
     }
 }
 
-// Y [k][n] = Q S: Q [m][n] (FP32 Lanczos vectors), S [m][k] (FP64, column l the
-// eigenvector of T for Ritz value l)
+// Y [k][n] = Q S: Q [m][n] (FP32 Lanczos vectors), S [m][k] (FP32, column l the
+// eigenvector of T for Ritz value l).  FP32 products and sums: the vectors are
+// rounded to FP32 when the space is built, and the FP64 pipe would bound m k n FMAs.
 __global__ void __launch_bounds__(kDeflBlock) k_ritz(int64_t n, int m, int k, const float* __restrict__ Q,
-                                                     const double* __restrict__ S, double* __restrict__ Y) {
+                                                     const float* __restrict__ S, double* __restrict__ Y) {
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
-        double y[kMaxDefl];
+        float y[kMaxDefl];
 #pragma unroll
-        for (int l = 0; l < kMaxDefl; ++l) y[l] = 0.0;
+        for (int l = 0; l < kMaxDefl; ++l) y[l] = 0.f;
         for (int t = 0; t < m; ++t) {
-            const double qv = double(Q[size_t(t) * n + j]);
+            const float qv = Q[size_t(t) * n + j];
 #pragma unroll
             for (int l = 0; l < kMaxDefl; ++l)
-                if (l < k) y[l] = fma(qv, __ldg(S + size_t(t) * k + l), y[l]);
+                if (l < k) y[l] = fmaf(qv, __ldg(S + size_t(t) * k + l), y[l]);
         }
 #pragma unroll
         for (int l = 0; l < kMaxDefl; ++l)
-            if (l < k) Y[size_t(l) * n + j] = y[l];
+            if (l < k) Y[size_t(l) * n + j] = double(y[l]);
     }
 }
 
@@ -364,15 +386,20 @@ int lanczos_store(int64_t n, const double* z, const double* minv, const double* 
     return CR_OK;
 }
 
-int ritz_vectors(int64_t n, int m, int k, const float* Q, const double* S, double* Y, cudaStream_t st) {
+int ritz_vectors(int64_t n, int m, int k, const float* Q, const float* S, double* Y, cudaStream_t st) {
     k_ritz<<<defl_grid(n), kDeflBlock, 0, st>>>(n, m, k, Q, S, Y);
     return CR_OK;
 }
 
 // Build the space from the k vectors in d->V64 (device, [k][n]) for the G of h:
 // V rounded to FP32, G V, M^{-1} G V, E = V^t G V, and the vectors kept greedily
-// in order while the Cholesky pivot of E stays above 1e-10 of its diagonal entry
-// (a vector in the span of those before it is dropped; d->k becomes the count).
+// in order while the Cholesky pivot of E stays above kDeflPivot of its diagonal
+// entry (d->k becomes the count).  The pivot over the diagonal entry is the squared
+// sine of the G-angle between a vector and the span of those before it: Ritz
+// vectors are G-orthogonal (pivots near 1), while the near-copies that the loss of
+// orthogonality of Lanczos produces, and dependent vectors, fall far below.  A
+// nearly dependent set would make E ill-conditioned, and the float-float solves,
+// whose dot products use G V in FP32, would lose their projection to it.
 int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st) {
     const int64_t n = d->n;
     const int k = d->k;
@@ -409,7 +436,7 @@ int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st) {
         }
         double piv = ok ? E[size_t(i) * k + i] : 0.0;
         for (int a = 0; ok && a < r; ++a) piv -= row[a] * row[a];
-        if (!ok || !(piv > 1e-10 * E[size_t(i) * k + i])) continue;
+        if (!ok || !(piv > kDeflPivot * E[size_t(i) * k + i])) continue;
         row[r] = std::sqrt(piv);
         L.resize(size_t(r + 1) * k, 0.0);
         for (int a = 0; a <= r; ++a) L[size_t(r) * k + a] = row[a];

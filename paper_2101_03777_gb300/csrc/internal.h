@@ -288,7 +288,7 @@ int defl_alloc(cr_hybrid* h, int k, cr_deflation** out);
 int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st);
 int lanczos_store(int64_t n, const double* z, const double* minv, const double* r, const double* rz, float* q,
                   cudaStream_t st);
-int ritz_vectors(int64_t n, int m, int k, const float* Q, const double* S, double* Y, cudaStream_t st);
+int ritz_vectors(int64_t n, int m, int k, const float* Q, const float* S, double* Y, cudaStream_t st);
 void tridiag_smallest_eigen(const std::vector<double>& a, const std::vector<double>& b, int k,
                             std::vector<double>& theta, std::vector<double>& S);
 int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out);

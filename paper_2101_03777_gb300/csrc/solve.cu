@@ -2889,9 +2889,11 @@ int ritz_space(cr_hybrid* h, const float* Q, const std::vector<double>& alpha, c
         DevArena a;
         ~Tmp() { a.release(); }
     } tmp;
-    double* Sd = nullptr;
-    CR_TRY(tmp.a.alloc_n(&Sd, S.size()));
-    CR_CUDA(cudaMemcpyAsync(Sd, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice, st));
+    std::vector<float> S32(S.begin(), S.end());
+    float* Sd = nullptr;
+    CR_TRY(tmp.a.alloc_n(&Sd, S32.size()));
+    CR_CUDA(cudaMemcpyAsync(Sd, S32.data(), sizeof(float) * S32.size(), cudaMemcpyHostToDevice, st));
+    CR_CUDA(cudaStreamSynchronize(st));   // S32 is a host temporary
     cr_deflation* d = nullptr;
     CR_TRY(defl_alloc(h, kk, &d));
     CR_TRY(ritz_vectors(n, mm, kk, Q, Sd, d->V64, st));
