@@ -166,9 +166,10 @@ typedef struct cr_solve_opts {
                            p = z + beta p - V E^{-1} (G V)^t z, so V^t r = 0 throughout and the
                            eigenvalues of the preconditioned operator on span(V) leave the
                            convergence.  PCG in FP64 (Jacobi or Chebyshev, persistent ignored) or
-                           FF with the Chebyshev preconditioner (V and G V in FP32; every reliable
-                           update repeats the deflated start, removing the components along V that
-                           the FP32 projection lets into r).  The space must come from a system of
+                           FF with the Chebyshev preconditioner (the dot products with G V in FP64,
+                           the projection with V in FP32; every reliable update repeats the
+                           deflated start, removing the components along V that the FP32
+                           projection lets into r).  The space must come from a system of
                            the same mesh, nu and mu without convection (the same G) */
 } cr_solve_opts;
 
@@ -287,8 +288,8 @@ int cr_solve(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_sol
  * algebraic multigrid and ILU preconditioners instead (Section 4).  A space
  * holds at most CR_MAX_DEFLATION vectors V of length n = dim * nf_int, rounded
  * to FP32 on entry (the FP64 and float-float solvers then deflate the same
- * space), with G V, M^{-1} G V and the Cholesky factor of E = V^t G V on the
- * device.  A vector whose Cholesky pivot falls below 1e-2 of its diagonal
+ * space), with G V and M^{-1} G V in FP64 and the Cholesky factor of
+ * E = V^t G V on the device.  A vector whose Cholesky pivot falls below 1e-2 of its diagonal
  * entry (the sine of its G-angle to the span of those before it below 0.1) is
  * dropped, which keeps E well conditioned for the FP32 dot products of the
  * float-float solves: Ritz vectors are G-orthogonal and pass, while the
@@ -333,11 +334,7 @@ int cr_deflation_lanczos(cr_hybrid* h, int rhs, const cr_solve_opts* opts, int m
  * Chebyshev preconditioner, on the multi-kernel path (persistent is ignored),
  * without deflation.  W, st, the return codes as for cr_solve (with
  * CR_ERR_NOT_CONVERGED the space is still formed); theta and out as for
- * cr_deflation_lanczos.  Take m at least the iterations the solve needs:
- * measured on 64x64 squares, a space from a third of the solve (which misses
- * the isolated lowest mode) still cuts FP64 PCG (320 -> 244 iterations) but
- * not the float-float forms, while a space from the whole solve cuts both
- * alike (165 -> 88 and 163 -> 86 at degree 8). */
+ * cr_deflation_lanczos. */
 int cr_solve_ritz(cr_hybrid* h, int rhs, const cr_solve_opts* opts, double* W, cr_solve_stats* st, int m, int k,
                   double* theta, cr_deflation** out);
 

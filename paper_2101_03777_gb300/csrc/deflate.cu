@@ -15,7 +15,6 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
-#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -50,30 +49,11 @@ __global__ void __launch_bounds__(kDeflBlock) k_defl_dots(int64_t n, const YT* _
     double acc[kMaxDefl];
 #pragma unroll
     for (int i = 0; i < kMaxDefl; ++i) acc[i] = 0.0;
-    if constexpr (std::is_same<YT, float>::value) {
-        // FP32 vectors (the float-float solves): FP32 products, a thread's few terms summed
-        // in FP32, the rest of the reduction in FP64 (the projection is accurate to FP32
-        // anyway); the FP64 pipe would bound a kernel that streams k FP32 vectors
-        float accf[kMaxDefl];
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double vj = as_double(v[j]);
 #pragma unroll
-        for (int i = 0; i < kMaxDefl; ++i) accf[i] = 0.f;
-        for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
-             j += int64_t(gridDim.x) * blockDim.x) {
-            const float vj = float(as_double(v[j]));
-#pragma unroll
-            for (int i = 0; i < kMaxDefl; ++i)
-                if (i < k) accf[i] = fmaf(Y[size_t(i) * n + j], vj, accf[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < kMaxDefl; ++i) acc[i] = double(accf[i]);
-    } else {
-        for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
-             j += int64_t(gridDim.x) * blockDim.x) {
-            const double vj = as_double(v[j]);
-#pragma unroll
-            for (int i = 0; i < kMaxDefl; ++i)
-                if (i < k) acc[i] = fma(as_double(Y[size_t(i) * n + j]), vj, acc[i]);
-        }
+        for (int i = 0; i < kMaxDefl; ++i)
+            if (i < k) acc[i] = fma(as_double(Y[size_t(i) * n + j]), vj, acc[i]);
     }
     __shared__ double sh[kMaxDefl][kDeflBlock / 32];
     __shared__ double tot[kMaxDefl];
@@ -185,14 +165,11 @@ __global__ void __launch_bounds__(kDeflBlock) k_defl_round(int64_t n, double* __
     }
 }
 
-// w = M^{-1} g (FP64) and g32 = fl32(g)
+// w = M^{-1} g (FP64)
 __global__ void __launch_bounds__(kDeflBlock) k_defl_scale(int64_t n, const double* __restrict__ g,
-                                                           const double* __restrict__ minv, double* __restrict__ w,
-                                                           float* __restrict__ g32) {
-    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+                                                           const double* __restrict__ minv, double* __restrict__ w) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x)
         w[j] = minv[j] * g[j];
-        g32[j] = __double2float_rn(g[j]);
-    }
 }
 
 // q = z / sqrt(rz), z = zin or (zin = null) M^{-1} r; rz read from the device
@@ -355,13 +332,21 @@ int defl_dots64(const cr_deflation* d, const double* Y, const double* v, bool so
     return CR_OK;
 }
 
-int defl_dots32(const cr_deflation* d, const float* Y, const float* v, const int* done, cudaStream_t st) {
-    k_defl_dots<float, float><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
+// c = E^{-1} (G V)^t z for the float-float solves' z (FP32, or float-float pairs):
+// G V in FP64, FP64 products (exact for an FP32 z) and sums.  G V rounded to FP32
+// would not do: the polynomial preconditioner amplifies the low modes of r in z by
+// up to the inverse of their eigenvalue, and when such a mode lies outside span(V)
+// the rounding error of (G V)^t z (2^-24 of |G V| |z|) swamps the small true value;
+// the projection then feeds components along V back into every direction, which CG
+// cannot remove (measured on 64x64 squares: no fewer iterations than without
+// deflation, against 320 -> 244 with exact dot products).
+int defl_dots64f(const cr_deflation* d, const double* Y, const float* v, const int* done, cudaStream_t st) {
+    k_defl_dots<double, float><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
     return CR_OK;
 }
 
-int defl_dots32ff(const cr_deflation* d, const float* Y, const float2* v, const int* done, cudaStream_t st) {
-    k_defl_dots<float, float2><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
+int defl_dots64ff(const cr_deflation* d, const double* Y, const float2* v, const int* done, cudaStream_t st) {
+    k_defl_dots<double, float2><<<defl_grid(d->n), kDeflBlock, 0, st>>>(d->n, Y, v, cr_deflation_dev(d), 1, done);
     return CR_OK;
 }
 
@@ -407,8 +392,7 @@ int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st) {
     for (int i = 0; i < k; ++i) {
         k_defl_round<<<g, kDeflBlock, 0, st>>>(n, d->V64 + size_t(i) * n, d->V32 + size_t(i) * n);
         CR_TRY(launch_spmv64(h, d->V64 + size_t(i) * n, d->GV64 + size_t(i) * n, st));
-        k_defl_scale<<<g, kDeflBlock, 0, st>>>(n, d->GV64 + size_t(i) * n, h->minv64, d->W64 + size_t(i) * n,
-                                              d->GV32 + size_t(i) * n);
+        k_defl_scale<<<g, kDeflBlock, 0, st>>>(n, d->GV64 + size_t(i) * n, h->minv64, d->W64 + size_t(i) * n);
     }
     CR_CUDA(cudaGetLastError());
     // E column by column: E_ij = V_i . (G V)_j
@@ -452,7 +436,6 @@ int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st) {
         CR_CUDA(cudaMemcpyAsync(d->GV64 + dst, d->GV64 + src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         CR_CUDA(cudaMemcpyAsync(d->W64 + dst, d->W64 + src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         CR_CUDA(cudaMemcpyAsync(d->V32 + dst, d->V32 + src, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-        CR_CUDA(cudaMemcpyAsync(d->GV32 + dst, d->GV32 + src, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     }
     const int kk = int(keep.size());
     std::vector<double> Lk(size_t(kk) * kk, 0.0);
@@ -480,7 +463,7 @@ int defl_alloc(cr_hybrid* h, int k, cr_deflation** out) {
     int rc;
     if ((rc = d->arena.alloc_n(&d->V64, kn)) || (rc = d->arena.alloc_n(&d->GV64, kn)) ||
         (rc = d->arena.alloc_n(&d->W64, kn)) || (rc = d->arena.alloc_n(&d->V32, kn)) ||
-        (rc = d->arena.alloc_n(&d->GV32, kn)) || (rc = d->arena.alloc_n(&d->L, size_t(kMaxDefl) * kMaxDefl)) ||
+        (rc = d->arena.alloc_n(&d->L, size_t(kMaxDefl) * kMaxDefl)) ||
         (rc = d->arena.alloc_n(&d->c, size_t(kMaxDefl))) || (rc = d->arena.alloc_n(&d->cf, size_t(kMaxDefl))) ||
         (rc = d->arena.alloc_n(&d->partial, size_t(kMaxDefl) * kMaxDeflBlocks)) ||
         (rc = d->arena.alloc_n(&d->count, 1))) {

@@ -170,8 +170,8 @@ struct DeflDev {
 }  // namespace crhyb
 
 // A deflation space (deflate.cu): k vectors V, rounded to FP32, of the G shared by
-// every Stokes system of one mesh with one nu and mu; G V, M^{-1} G V (FP64), V and
-// G V in FP32, and the Cholesky factor of E = V^t G V.
+// every Stokes system of one mesh with one nu and mu; G V, M^{-1} G V (FP64), V in
+// FP32, and the Cholesky factor of E = V^t G V.
 struct cr_deflation {
     cr_mesh* m = nullptr;
     int dim = 0, k = 0;
@@ -181,7 +181,7 @@ struct cr_deflation {
     std::vector<int> kept;            // indices of the given vectors kept
     crhyb::DevArena arena;
     double *V64 = nullptr, *GV64 = nullptr, *W64 = nullptr;   // [k][n]
-    float *V32 = nullptr, *GV32 = nullptr;                    // [k][n]
+    float* V32 = nullptr;                                     // [k][n]
     double* L = nullptr;
     double* c = nullptr;
     float* cf = nullptr;
@@ -279,8 +279,8 @@ int cheb_step_form_impl(int d, int poly_prec);
 // Lanczos-vector store q = z / sqrt(rz) and the Ritz vectors Y = Q S; the k smallest
 // eigenpairs of a symmetric tridiagonal matrix (host)
 int defl_dots64(const cr_deflation* d, const double* Y, const double* v, bool solve, const int* done, cudaStream_t st);
-int defl_dots32(const cr_deflation* d, const float* Y, const float* v, const int* done, cudaStream_t st);
-int defl_dots32ff(const cr_deflation* d, const float* Y, const float2* v, const int* done, cudaStream_t st);
+int defl_dots64f(const cr_deflation* d, const double* Y, const float* v, const int* done, cudaStream_t st);
+int defl_dots64ff(const cr_deflation* d, const double* Y, const float2* v, const int* done, cudaStream_t st);
 int defl_axpy64(const cr_deflation* d, const double* Y, double sign, double* x, cudaStream_t st);
 int defl_project64(const cr_deflation* d, double* p, const int* done, cudaStream_t st);
 int defl_projectff(const cr_deflation* d, float2* p, const int* done, cudaStream_t st);

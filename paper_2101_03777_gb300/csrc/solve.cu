@@ -2265,12 +2265,12 @@ int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve
                 if (e1) cudaEventRecord(e1, c.st);
                 c.launches += deg - 1;
             };
-            // the direction p = z + beta p; deflated: c = E^{-1} (G V)^t z (FP32 G V) before,
-            // p -= V c (FP32 V) after
+            // the direction p = z + beta p; deflated: c = E^{-1} (G V)^t z (FP64 G V, FP64
+            // products) before, p -= V c (FP32 V) after
             auto direction = [&](int first) {
                 if (dfl) {
-                    if (pp != CR_POLY_SAME) defl_dots32(dfl, dfl->GV32, zs[(deg - 1) & 1], done, c.st);
-                    else defl_dots32ff(dfl, dfl->GV32, zb[(deg - 1) & 1], done, c.st);
+                    if (pp != CR_POLY_SAME) defl_dots64f(dfl, dfl->GV64, zs[(deg - 1) & 1], done, c.st);
+                    else defl_dots64ff(dfl, dfl->GV64, zb[(deg - 1) & 1], done, c.st);
                 }
                 if (pp != CR_POLY_SAME)
                     kf_cpcg_dir32<<<gn, kBlock, 0, c.st>>>(c.n, h->pf, zs[(deg - 1) & 1], c.sc, first);
