@@ -139,26 +139,29 @@ def test_ritz_values_match_oracle(precond):
         assert abs(yo @ yg) >= 1 - 1e-5, j
 
 
-@pytest.mark.parametrize("m", [120, 300])
-def test_ritz_vectors_of_one_rhs_speed_up_another(m):
-    """2D 64^2, two right-hand sides: 8 Ritz vectors from m Chebyshev-PCG steps on the
-    first cut the float-float Chebyshev PCG (BF16 steps) of the second, which still
-    reaches the direct solve.  From 120 steps (a third of a solve) the space misses the
-    isolated lowest mode, which the preconditioner amplifies in z; the dot products
-    with G V must then be exact for the FP32 z (they are FP64), or the projection feeds
-    components along V back into every direction and the gain is lost (oracle: 320 ->
-    244 iterations in FP64)."""
+@pytest.mark.parametrize("m,poly_prec,gain", [(120, "same", 0.8), (120, "fp32", 0.8), (120, "bf16", 0.9),
+                                               (300, "bf16", 0.7)])
+def test_ritz_vectors_of_one_rhs_speed_up_another(m, poly_prec, gain):
+    """2D 64^2, two right-hand sides: 8 Ritz vectors from m FP64 Chebyshev-PCG steps on
+    the first cut the float-float Chebyshev PCG of the second, which still reaches the
+    direct solve.  From 120 steps (a third of a solve) the space misses the isolated
+    lowest mode, which the preconditioner amplifies in z: the dot products and the
+    projection must then be exact for the FP32 z and V (they are FP64), or they feed
+    components along V back into every direction and the gain is lost.  Measured:
+    322-323 -> 246 / 247 / 277 iterations with float-float, FP32 and BF16 steps (FP64
+    PCG: 320 -> 244; the BF16 steps' rounded G makes the space less invariant);
+    from 300 steps, BF16: 323 -> 173."""
     G, Ss, mesh, hyb, _ = case("cfg2", 64, nrhs=2)
     cheb = dict(precond="chebyshev", poly_degree=4, poly_ratio=1000.0)
     d, th = crhyb.cr_deflation_lanczos(hyb, m, 8, rhs=0, **cheb)
     assert d.k >= 6 and np.all(np.diff(th) >= 0) and th[0] > 0
-    opts = dict(prec="ff", poly_prec="bf16", tol=1e-12, use_graph=True, **cheb)
+    opts = dict(prec="ff", poly_prec=poly_prec, tol=1e-12, use_graph=True, **cheb)
     st0, _ = gpu_solve(hyb, rhs=1, **opts)
     st, W = gpu_solve(hyb, rhs=1, deflation=d, **opts)
     assert st["status"] == 0 and st["relres"] <= 1e-12
     # W's error is about 700 times its relative residual on this mesh (measured: 7e-9 at 1e-11)
     assert rel(W, spla.spsolve(G.tocsc(), Ss[1])) <= 1e-8
-    assert st["iterations"] < 0.85 * st0["iterations"], (st["iterations"], st0["iterations"])
+    assert st["iterations"] < gain * st0["iterations"], (st["iterations"], st0["iterations"])
 
 
 def test_dot_products_over_several_grid_passes():
