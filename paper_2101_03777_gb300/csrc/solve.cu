@@ -1230,6 +1230,16 @@ template <int D, typename VT>
 void launch_cheb32(int64_t nf, const int32_t* cols, const VT* vals, const float* minv, const float2* r,
                    const float* zin, float* zout, float* d, KScal* sc, RedBuf red, int j, int last, cudaStream_t st) {
     const int form = cheb32_form(D, std::is_same<VT, __nv_bfloat16>::value);
+    if (form == 2) {
+        // the dynamic shared-memory limit is a per-device attribute: raise it on every GPU
+        // this thread launches on (the first launch on a device is never inside a capture)
+        static thread_local int raised_on = -1;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev != raised_on &&
+            cudaFuncSetAttribute(k32_cheb_step_staged<D, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(ChebStage<D, VT>::SMEM)) == cudaSuccess)
+            raised_on = dev;
+    }
     if (form == 2)
         k32_cheb_step_staged<D, VT><<<staged_grid<D, VT>(nf), kBlock, ChebStage<D, VT>::SMEM, st>>>(
             nf, cols, vals, minv, r, zin, zout, d, sc, red, j, last);
