@@ -225,6 +225,8 @@ KERNEL_SOURCES = {
     "persist": ["persist.cu", "persist.h", "ff.cuh", "device_common.cuh"],
     "cheb_ff": [("solve.cu", "// Chebyshev step j: zout = zin + d_j, d_j = c1_j d + c2_j M^{-1} (r - G zin); on the",
                  "// p = z + beta p   (first: p = z)"), "ff.cuh", "device_common.cuh"],
+    "cheb_rows1": [("solve.cu", "// Chebyshev step j in FP32 on the FP32 (or BF16) values of G; the last step forms",
+                    "// ---- the FP32-step Chebyshev kernel, two rows per thread ----"), "ff.cuh", "device_common.cuh"],
     "cheb_rows2": [("solve.cu", "// ---- the FP32-step Chebyshev kernel, two rows per thread ----",
                     "// ---- the FP32-step Chebyshev kernel on slices staged in shared memory ----"),
                    "ff.cuh", "device_common.cuh"],
@@ -246,6 +248,20 @@ TRAFFIC = {
     ("cfg2", "ff_chebbf", "staged"): {
         "per": "launch", "bytes": (75430144 + 1292544 + 75429120 + 45824 + 75427328 + 56064) / 3,
         "sources": "cheb_staged", "sha256": "d34bb5e8d04d3b18ed131a58267950ba89cf11291a7f35ae2fbf9d1e046423b6"},
+    # the persistent FP64 and FF_BF16 kernels on the 64^3 workload: two launches of 64 iterations each
+    ("cfg3", "fp64", None): {"per": "iteration",
+                             "bytes": (148678149120 + 19170485248 + 150336442112 + 19184686592) / 2 / 64,
+                             "sources": "persist", "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
+    ("cfg3", "ff_bf16", None): {"per": "iteration",
+                                "bytes": (123646610688 + 19144310272 + 127633991680 + 19611470080) / 2 / 64,
+                                "sources": "persist", "sha256": "a5c561643bcd9514354b9d52efa8b149f579ce03c2e132758f392019507be00e"},
+    # the FP32 Chebyshev step on FP32 values: two rows per thread on 64^3, one on 512^2
+    ("cfg3", "ff_cheb32", "rows2"): {
+        "per": "launch", "bytes": (1048752128 + 48134400 + 1048759296 + 44839168 + 1048767488 + 45010688) / 3,
+        "sources": "cheb_rows2", "sha256": "f8ad74ed6aaa33a0b42db85c86ff8cd8f66766b3e52c5d1003ef7c1f609922b5"},
+    ("cfg2", "ff_cheb32", "rows1"): {
+        "per": "launch", "bytes": (106844416 + 2734848 + 106842880 + 111104 + 106854656 + 172544) / 3,
+        "sources": "cheb_rows1", "sha256": "f5245097897897035a7bea13dfcd68e1200d7f1b200bb09776c9486c1f58276d"},
     # the float-float Chebyshev step (occupancy-sized grid)
     ("cfg3", "ff_cheb", None): {
         "per": "launch", "bytes": (1910210816 + 113576960 + 1910211328 + 109615616 + 1910217728 + 110364416) / 3,
