@@ -78,7 +78,8 @@ def parse():
     ap.add_argument("--precs", default=None,
                     help="comma-separated solvers to time, the first is the headline (default: "
                          "ff_chebbf,ff_cheb32,ff_cheb,fp64_cheb,ff,fp64,ff_bf16 in 2D; "
-                         "ff_chebbf,ff_cheb32,ff_cheb,ff,fp64,fp64_cheb,ff_bf16 for cfg3; ff for cfg4, cfg5)")
+                         "ff_chebbf,ff_cheb32,ff_cheb,ff,fp64,fp64_cheb,ff_bf16 for cfg3; ff_chebbf,ff for cfg5; ff for "
+                         "cfg4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=30)
@@ -120,14 +121,16 @@ def default_precs(workload):
     BF16-low-part Jacobi variant."""
     if workload == "cfg3":
         return "ff_chebbf,ff_cheb32,ff_cheb,ff,fp64,fp64_cheb,ff_bf16"
+    if workload == "cfg5":
+        return "ff_chebbf,ff"   # each is a Newton step of several seconds
     return "ff_chebbf,ff_cheb32,ff_cheb,fp64_cheb,ff,fp64,ff_bf16"
 
 
 def supported_precs(workload, precs, steady=False):
     """The Chebyshev-preconditioned PCG serves the single transient Stokes solve and the
-    inner solves of a steady step; the batch and the transient Newton step keep their
-    Jacobi-preconditioned solvers."""
-    if workload == "cfg4" or (workload == "cfg5" and not steady):
+    inner solves of the Newton steps (transient and steady); the batch keeps its
+    Jacobi-preconditioned persistent kernel."""
+    if workload == "cfg4":
         return ",".join(x for x in precs.split(",") if x and x not in CHEB_PRECS) or "ff"
     return precs
 
@@ -590,9 +593,15 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
             # the nonsymmetric Newton system (FP64 values for the outer GMRES) and the transient
             # Stokes system on the same mesh, whose PCG solves precondition it
             hyb = crhyb.cr_hybridise(system, keep_fp32=False)
-            pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
-                                     keep_ff=(prec == "ff"), keep_ff_bf16=(prec == "ff_bf16"))
-            o = dict(tol=args.tol, prec=prec, profile=profile, check_every=args.check_every)
+            pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb),
+                                     keep_fp32=(prec == "ff_cheb32"), keep_bf16=(prec == "ff_chebbf"),
+                                     keep_ff=(prec in ("ff", "ff_cheb", "ff_cheb32", "ff_chebbf")),
+                                     keep_ff_bf16=(prec == "ff_bf16"))
+            o = dict(tol=args.tol, prec=PRECS[prec][0]["prec"], profile=profile, check_every=args.check_every)
+            if prec in CHEB_PRECS:
+                # the inner PCG with the Chebyshev preconditioner (multi-kernel, graph-replayed)
+                o.update(precond="chebyshev", poly_degree=cheb_degree(args, prec, d),
+                         poly_ratio=cheb_ratio(args, prec, d), poly_prec=PRECS[prec][0].get("poly_prec", "same"))
             if args.max_iter:
                 o["max_iter"] = args.max_iter
             st = crhyb.cr_solve_preconditioned(hyb, pre, Wt, raise_on_error=not args.max_iter, **o)
@@ -737,9 +746,13 @@ def run_ours(args, rank, world, workload=None, precs=None, extras=True):
                     "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
                     "bytes_per_launch": step_bytes, "avg_launch_ms": ms, "launches_timed": nl,
                     "peak_note": peak_note}
-            solver = ("steady Newton step: flexible GMRES(60) in FP64 on the coupled system (Eq. 10, mu = 0), "
-                      f"each step preconditioned by one transient Stokes step (mu = {args.mu_pre:g}) of the hybrid "
-                      f"method, inner {solver} to 1e-6")
+            if p["mu"] == 0.0:
+                solver = ("steady Newton step: flexible GMRES(60) in FP64 on the coupled system (Eq. 10, mu = 0), "
+                          f"each step preconditioned by one transient Stokes step (mu = {args.mu_pre:g}) of the "
+                          f"hybrid method, inner {solver} to 1e-6")
+            else:
+                solver = ("Newton step: flexible GMRES(30) in FP64 on the nonsymmetric G, each step preconditioned "
+                          f"by a solve with the transient Stokes G of the same mesh, inner {solver} to 0.1")
         elif newton:
             # the inner persistent PCG on the Stokes G (same mesh, same sliced ELL) dominates the step
             mb = 4 if prec != "fp64" else 8

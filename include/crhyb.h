@@ -363,8 +363,9 @@ int cr_chebyshev_step_form(int dim, int poly_prec);
 
 /* Solve G W = S (right-hand side `rhs` of h) by flexible GMRES(m) in FP64
  * (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.6), right-
- * preconditioned by an inner Jacobi-PCG solve with the SPD matrix G_pre of
- * `pre` (the persistent PCG kernel of cr_solve):
+ * preconditioned by an inner PCG solve with the SPD matrix G_pre of `pre`
+ * (the persistent Jacobi-PCG kernel of cr_solve, or its Chebyshev-preconditioned
+ * PCG):
  *   z_j = PCG(G_pre, v_j) to relative residual inner_tol,  v_{j+1} from G z_j,
  *   W = W_0 + Z y  (y minimises ||S - G W|| over the cycle).
  * For the nonsymmetric Newton/Oseen systems (Section 4.3) `pre` is the
@@ -377,9 +378,13 @@ int cr_chebyshev_step_form(int dim, int poly_prec);
  *         FF and FF_BF16 need the float-float values kept (keep_lo_fp32 or
  *         keep_lo_bf16); its own S and W are untouched
  *   opts  method GMRES; prec is the precision of the inner PCG (FP64, FF or
- *         FF_BF16); restart m (default 30); tol on ||S - G W|| / ||S||;
- *         inner_tol (default 0.1); max_iter caps the GMRES steps (default 1000);
- *         use_x0 as for cr_solve; check_every x 64 inner iterations per launch
+ *         FF_BF16); precond JACOBI (the persistent PCG) or CHEBYSHEV (the
+ *         Chebyshev-preconditioned PCG of cr_solve, with poly_degree, poly_ratio
+ *         and poly_prec as there; FP64 or FF); deflation: a space of pre's G
+ *         (the inner solves then run on the multi-kernel path); restart m
+ *         (default 30); tol on ||S - G W|| / ||S||; inner_tol (default 0.1);
+ *         max_iter caps the GMRES steps (default 1000); use_x0 as for cr_solve;
+ *         check_every x 64 inner iterations per persistent launch
  *   W     as for cr_solve
  *   st    iterations = inner PCG iterations in total, outer = GMRES steps,
  *         relres = FP64 relative residual of the returned W; with opts->profile,

@@ -539,12 +539,26 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: pre needs a transient Stokes system (mu > 0, b_h = 0), "
                                 "whose G is SPD");
     if (o->method != CR_METHOD_GMRES) return fail(CR_ERR_ARG, "cr_solve_preconditioned: the outer method is GMRES");
-    if (o->precond != CR_PRECOND_JACOBI)
-        return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG is Jacobi-preconditioned");
+    if (o->precond != CR_PRECOND_JACOBI && o->precond != CR_PRECOND_CHEBYSHEV)
+        return fail(CR_ERR_ARG, "cr_solve_preconditioned: bad preconditioner of the inner PCG");
     if (o->prec != CR_PREC_FP64 && o->prec != CR_PREC_FF && o->prec != CR_PREC_FF_BF16)
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: the inner PCG runs in FP64, FF or FF_BF16");
     if ((o->prec == CR_PREC_FF && !pre->vff) || (o->prec == CR_PREC_FF_BF16 && (!pre->val32 || !pre->vlo16)))
         return fail(CR_ERR_ARG, "cr_solve_preconditioned: the float-float values of pre were not kept");
+    if (o->precond == CR_PRECOND_CHEBYSHEV) {
+        const int deg = o->poly_degree > 0 ? o->poly_degree : 4;
+        if (deg < 2 || deg > CR_MAX_POLY_DEGREE || !(o->poly_ratio <= 0.0 || o->poly_ratio > 1.0))
+            return fail(CR_ERR_ARG, "cr_solve_preconditioned: bad poly_degree or poly_ratio");
+        if (o->poly_prec != CR_POLY_SAME && o->poly_prec != CR_POLY_FP32 && o->poly_prec != CR_POLY_BF16)
+            return fail(CR_ERR_ARG, "cr_solve_preconditioned: bad poly_prec");
+        if (o->poly_prec != CR_POLY_SAME && o->prec == CR_PREC_FP64)
+            return fail(CR_ERR_ARG, "cr_solve_preconditioned: poly_prec applies to the float-float Chebyshev PCG");
+    }
+    if (o->deflation) {   // a space of pre's G deflates every inner solve
+        cr_solve_opts io = *o;
+        io.method = CR_METHOD_PCG;
+        CR_TRY(check_deflation(o->deflation, pre, &io, "cr_solve_preconditioned"));
+    }
     if (!(o->tol > 0.0)) return fail(CR_ERR_ARG, "cr_solve_preconditioned: tol must be > 0");
     const int restart = o->restart > 0 ? o->restart : 30;
     if (restart < 1 || restart > CR_MAX_RESTART)
@@ -554,6 +568,9 @@ extern "C" int cr_solve_preconditioned(cr_hybrid* h, int rhs, cr_hybrid* pre, co
     StreamScope scope(m);
     CR_TRY(ensure_workspace(h, true, restart, CR_PREC_FP64));
     CR_TRY(ensure_workspace(pre, false, 0, o->prec));
+    if (o->precond == CR_PRECOND_CHEBYSHEV && !pre->cheb) CR_TRY(pre->arena.alloc_n(&pre->cheb, 3 * n + 1));
+    if (o->precond == CR_PRECOND_CHEBYSHEV && o->prec != CR_PREC_FP64 && !pre->chebf)
+        CR_TRY(pre->arena.alloc_n(&pre->chebf, 3 * n));
     if (restart > h->fgz_m) {
         if (h->fgz) cudaFree(h->fgz);
         h->fgz = nullptr;

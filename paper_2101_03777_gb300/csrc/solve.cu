@@ -1874,6 +1874,12 @@ int solve_persistent(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, c
 //   z_j = PCG(G_pre, v_j),  v_{j+1} = G z_j orthogonalised (CGS2),  x = x0 + Z y.
 // A preconditioner that changes from step to step is what the flexible form
 // allows; the minimised residual is still that of G.
+// the multi-kernel solver of cr_solve (defined below): G W = S of h, or = b_override,
+// with the Lanczos record when rec is given
+template <int D>
+int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st,
+              const double* b_override = nullptr, const LanczosRec* rec = nullptr);
+
 template <int D>
 int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, double* W, cr_solve_stats* st) {
     cr_mesh* m = h->m;
@@ -1912,15 +1918,36 @@ int solve_fgmres(cr_hybrid* h, int rhs, cr_hybrid* pre, const cr_solve_opts* o, 
         if (c.hs->done) break;
         const int mr = c.hs->m;
         for (int j = 0; j < mr; ++j) {
-            PScal P{};
-            double kms = 0.0;
-            int64_t kit = 0;
-            CR_TRY(persistent_pcg<D>(cp, V + size_t(j) * c.n, nullptr, Z + size_t(j) * c.n, mode, itol,
-                                     default_delta(mode), 100000, per_launch, o->profile != 0, &P, &kms, &kit));
-            inner_its += P.it;
-            prof_ms += kms;
-            prof_it += kit;
-            if (P.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+            if (o->precond == CR_PRECOND_CHEBYSHEV || o->deflation) {
+                // z_j by the Chebyshev-preconditioned (or deflated) PCG of cr_solve on G_pre,
+                // multi-kernel and graph-replayed, with v_j as its right-hand side
+                cr_solve_opts io = *o;
+                io.method = CR_METHOD_PCG;
+                io.tol = itol;
+                io.max_iter = 100000;
+                io.use_x0 = 0;
+                io.use_graph = o->profile ? 0 : 1;
+                io.persistent = 0;
+                io.inner_tol = 0.0;
+                cr_solve_stats ist{};
+                const int rc = solve_dim<D>(pre, 0, &io, Z + size_t(j) * c.n, &ist, V + size_t(j) * c.n);
+                if (rc != CR_OK && rc != CR_ERR_NOT_CONVERGED && rc != CR_ERR_BREAKDOWN) return rc;
+                inner_its += ist.iterations;
+                prof_ms += ist.spmv_ms;
+                prof_it += ist.spmv_launches;
+                cp.launches += ist.kernel_launches;
+                if (ist.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+            } else {
+                PScal P{};
+                double kms = 0.0;
+                int64_t kit = 0;
+                CR_TRY(persistent_pcg<D>(cp, V + size_t(j) * c.n, nullptr, Z + size_t(j) * c.n, mode, itol,
+                                         default_delta(mode), 100000, per_launch, o->profile != 0, &P, &kms, &kit));
+                inner_its += P.it;
+                prof_ms += kms;
+                prof_it += kit;
+                if (P.status == CR_ERR_BREAKDOWN) { status = CR_ERR_BREAKDOWN; break; }
+            }
             k_gm_spmv<D, double, double><<<g, kBlock, 0, c.st>>>(c.nf, m->cols, h->val64, Z + size_t(j) * c.n, V,
                                                                  c.sc);
             ++c.launches;
@@ -2056,7 +2083,7 @@ int chebyshev_setup(cr_hybrid* h, const cr_solve_opts* o, cudaStream_t st, KScal
 
 template <int D>
 int solve_dim(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st,
-              const double* b_override = nullptr, const LanczosRec* rec = nullptr) {
+              const double* b_override, const LanczosRec* rec) {
     cr_mesh* m = h->m;
     Ctx c{h, m->stream, static_cast<KScal*>(h->scal), static_cast<KScal*>(h->h_scal), m->nf, m->nf * D, D,
           o->profile != 0};

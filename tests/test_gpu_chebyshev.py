@@ -149,6 +149,6 @@ def test_bad_options_are_refused():
         with pytest.raises(crhyb.CrError) as ei:
             crhyb.cr_solve(hyb, W, **o)
         assert ei.value.name == "CR_ERR_ARG", b
-    with pytest.raises(crhyb.CrError) as ei:
-        crhyb.cr_solve_preconditioned(hyb, hyb, W, tol=1e-10, prec="fp64", precond="chebyshev")
+    with pytest.raises(crhyb.CrError) as ei:   # FP32 steps under an FP64 inner solve
+        crhyb.cr_solve_preconditioned(hyb, hyb, W, tol=1e-10, prec="fp64", precond="chebyshev", poly_prec="fp32")
     assert ei.value.name == "CR_ERR_ARG"

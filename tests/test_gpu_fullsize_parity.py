@@ -140,16 +140,21 @@ def test_2d_384_matches_oracle(truths, solver):
     assert rel(U, Uo) <= tol and rel(P, Po) <= tol, (rel(U, Uo), rel(P, Po))
 
 
-def test_newton_384_matches_oracle(truths):
+@pytest.mark.parametrize("inner", ["ff-jacobi", "ff-chebyshev-bf16-steps-bench-degree"])
+def test_newton_384_matches_oracle(truths, inner):
+    """The transient Newton step (flexible GMRES), its inner solves by the persistent
+    Jacobi PCG or by the bench's float-float Chebyshev PCG with BF16 steps."""
     coords, elems, fbar, w = truth.newton_2d_inputs(NNEWTON)
     mesh = crhyb.cr_mesh_load(coords, elems)
     assert mesh.nf > 8 * 152 * 256
     fb = torch.from_numpy(fbar).cuda()
     hyb = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb, conv="newton",
                                                        w=torch.from_numpy(w).cuda()), keep_fp32=False)
-    pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb), keep_fp32=False, keep_ff=True)
+    pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, 0.01, 1000.0, fb), keep_fp32=False, keep_ff=True,
+                             keep_bf16=True)
+    extra = {} if inner == "ff-jacobi" else dict(precond="chebyshev", poly_prec="bf16", **BENCH_DEGREE[2])
     st, U, P = solve_recover(hyb, solver=lambda W: crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-11,
-                                                                                 prec="ff", max_iter=2000))
+                                                                                 prec="ff", max_iter=2000, **extra))
     assert st["status"] == 0 and st["relres"] <= 1e-11
     Uo, Po = truths["newton"].result()
     assert rel(U, Uo) <= 1e-9 and rel(P, Po) <= 1e-9, (rel(U, Uo), rel(P, Po))

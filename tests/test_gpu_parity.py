@@ -196,26 +196,36 @@ def test_solution_matches_coupled_direct_solve(name, opts, tol):
     assert np.abs(div).max() <= 1e-9 * np.abs(g["a"]).max() * np.abs(U).max()
 
 
-def stokes_preconditioner(mesh, case, keep_ff=True, keep_ff_bf16=True):
+def stokes_preconditioner(mesh, case, keep_ff=True, keep_ff_bf16=True, keep_bf16=True):
     """The transient Stokes system with the case's nu and mu on the same mesh."""
     coords, elems, nu, mu, conv, fbar, w = case
     fb = torch.from_numpy(np.ascontiguousarray(fbar)).cuda()
     return crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, nu, mu, fb), keep_fp32=False, keep_ff=keep_ff,
-                              keep_ff_bf16=keep_ff_bf16)
+                              keep_ff_bf16=keep_ff_bf16, keep_bf16=keep_bf16)
 
 
-@pytest.mark.parametrize("name,prec", [("ns_newton_9", "ff"), ("ns_newton_9", "fp64"), ("ns_oseen_9", "ff"),
-                                       ("ns_newton_9", "ff_bf16")])
-def test_stokes_preconditioned_fgmres_matches_direct_solve(name, prec):
-    """Flexible GMRES preconditioned by inner PCG solves with the Stokes G: the
-    outer residual is FP64, so every inner precision reaches the FP64 bound."""
+CHEB_INNER = dict(precond="chebyshev", poly_degree=8, poly_ratio=1000.0)
+FGMRES_CASES = [("ns_newton_9", "ff", {}), ("ns_newton_9", "fp64", {}), ("ns_oseen_9", "ff", {}),
+                ("ns_newton_9", "ff_bf16", {}),
+                # inner solves by the Chebyshev-preconditioned PCG: FP64, float-float with BF16 steps
+                ("ns_newton_9", "fp64", CHEB_INNER), ("ns_newton_9", "ff", dict(CHEB_INNER, poly_prec="bf16")),
+                ("ns_oseen_9", "ff", dict(CHEB_INNER, poly_prec="fp32"))]
+
+
+@pytest.mark.parametrize("name,prec,extra", FGMRES_CASES,
+                         ids=[f"{c[0]}-{c[1]}-{c[2].get('precond', 'jacobi')}-{c[2].get('poly_prec', 'same')}"
+                              for c in FGMRES_CASES])
+def test_stokes_preconditioned_fgmres_matches_direct_solve(name, prec, extra):
+    """Flexible GMRES preconditioned by inner PCG solves with the Stokes G (Jacobi, or
+    Chebyshev in FP64 or float-float with reduced-precision steps): the outer residual
+    is FP64, so every inner precision reaches the FP64 bound."""
     case = make_case(name)
     coords, elems, nu, mu, conv, fbar, w = case
     mesh, _, hyb = gpu_setup(case)
     pre = stokes_preconditioner(mesh, case)
     ref = pipeline.direct(coords, elems, nu, mu, fbar[0], conv, w, dense=True)
     W = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
-    st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-13, prec=prec)
+    st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-13, prec=prec, **extra)
     assert st["status"] == 0 and st["relres"] <= 1e-12
     assert 1 <= st["outer"] <= 30 and st["iterations"] >= st["outer"]
     U = torch.zeros(hyb.n, dtype=torch.float64, device="cuda")
@@ -224,7 +234,7 @@ def test_stokes_preconditioned_fgmres_matches_direct_solve(name, prec):
     assert rel(U.cpu().numpy(), ref["U"].ravel()) <= 1e-9
     assert rel(P.cpu().numpy(), coupled.normalise_pressure(ref["P"], ref["geom"]["vol"])) <= 1e-9
     # warm start from the solution: no step needed
-    st2 = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-12, prec=prec, use_x0=True)
+    st2 = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-12, prec=prec, use_x0=True, **extra)
     assert st2["status"] == 0 and st2["outer"] == 0
 
 
