@@ -82,6 +82,9 @@ CASES = [
     ("cfg2", dict(method="pcg", prec="ff", precond="chebyshev", poly_degree=bench.CHEB_DEGREE_FP32_STEPS[2],
                   poly_ratio=bench.CHEB_RATIO_FP32_STEPS[2], use_graph=True, poly_prec="bf16"), True),
     ("cfg5", dict(method="stokes-fgmres", prec="ff"), True),
+    # the bench's Newton-step solver: inner float-float Chebyshev PCG with BF16 steps
+    ("cfg5", dict(method="stokes-fgmres", prec="ff", precond="chebyshev", poly_prec="bf16",
+                  poly_degree=bench.CHEB_DEGREE_FP32_STEPS[2], poly_ratio=bench.CHEB_RATIO_FP32_STEPS[2]), True),
 ]
 
 
@@ -101,14 +104,14 @@ def test_full_size_solution_satisfies_the_coupled_system(name, opts, with_g):
     W = torch.zeros(n, dtype=torch.float64, device="cuda")
     if opts["method"] == "stokes-fgmres":
         pre = crhyb.cr_hybridise(crhyb.cr_assemble_coupled(mesh, p["nu"], p["mu"], fb), keep_fp32=False,
-                                 keep_ff=True)
-        st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-10, prec=opts["prec"])
+                                 keep_ff=True, keep_bf16=opts.get("poly_prec") == "bf16")
+        inner = {k: v for k, v in opts.items() if k not in ("method", "prec")}
+        st = crhyb.cr_solve_preconditioned(hyb, pre, W, tol=1e-10, prec=opts["prec"], **inner)
         del pre
     else:
         st = crhyb.cr_solve(hyb, W, tol=1e-10, max_iter=400000, **opts)
-    # PCG stops on the FP64 true residual; GMRES on its recursive residual, then accepts a
-    # true residual within 10 x the tolerance
-    relmax = 1.01e-10 if opts["method"] == "pcg" else 1e-9
+    # every solver returns CR_OK only when the FP64 true residual of W meets the tolerance
+    relmax = 1.01e-10
     assert st["status"] == 0 and st["relres"] <= relmax
     U = torch.zeros(n, dtype=torch.float64, device="cuda")
     P = torch.zeros(ne, dtype=torch.float64, device="cuda")
