@@ -276,8 +276,8 @@ int cheb_step_form_impl(int d, int poly_prec);
 // deflation (deflate.cu): dot products g = Y^t v over the space's k vectors (with
 // solve: c = E^{-1} g into the space's coefficient slots), x += sign Y c, p -= V c,
 // skipped while *done (when given) is set; the space's build and allocation; the
-// Lanczos-vector store q = z / sqrt(rz) and the Ritz vectors Y = Q S; the k smallest
-// eigenpairs of a symmetric tridiagonal matrix (host)
+// Lanczos-vector store q = z / sqrt(rz) and the Ritz vectors Y = Q S (the eigenpairs of
+// the Lanczos matrix: tridiag.h)
 int defl_dots64(const cr_deflation* d, const double* Y, const double* v, bool solve, const int* done, cudaStream_t st);
 int defl_dots64f(const cr_deflation* d, const double* Y, const float* v, const int* done, cudaStream_t st);
 int defl_dots64ff(const cr_deflation* d, const double* Y, const float2* v, const int* done, cudaStream_t st);
@@ -289,8 +289,6 @@ int defl_build(cr_deflation* d, cr_hybrid* h, cudaStream_t st);
 int lanczos_store(int64_t n, const double* z, const double* minv, const double* r, const double* rz, float* q,
                   cudaStream_t st);
 int ritz_vectors(int64_t n, int m, int k, const float* Q, const float* S, double* Y, cudaStream_t st);
-void tridiag_smallest_eigen(const std::vector<double>& a, const std::vector<double>& b, int k,
-                            std::vector<double>& theta, std::vector<double>& S);
 int lanczos_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, int m, int k, double* theta, cr_deflation** out);
 int solve_ritz_impl(cr_hybrid* h, int rhs, const cr_solve_opts* o, double* W, cr_solve_stats* st, int m, int k,
                     double* theta, cr_deflation** out);

@@ -29,6 +29,7 @@
 #include <string>
 
 #include "device_common.cuh"
+#include "tridiag.h"
 #include "ff.cuh"
 #include "persist.h"
 
