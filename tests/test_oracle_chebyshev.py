@@ -95,3 +95,50 @@ def test_reaches_the_direct_solution(name, n, degree):
     assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
     _, it_j, _ = krylov.pcg(G, S, minv, rtol=1e-13)
     assert it < it_j   # fewer CG iterations (each applies G `degree` times)
+
+
+def bf16_round(x):
+    """Round to the nearest BF16 value (8 significant bits), ties to even: the values
+    the reduced-precision Chebyshev steps read."""
+    x = np.asarray(x, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name,n,degree,ratio", [("cfg2", 6, 24, 10000.0), ("cfg3", 2, 24, 3000.0),
+                                                 ("cfg2", 6, 4, 1000.0)])
+def test_polynomial_of_the_bf16_matrix_stays_spd(name, n, degree, ratio):
+    """The steps may use G~ = bf16(G) (symmetric, since equal entries round alike) under
+    the Gershgorin bound of the exact M^{-1} G: the preconditioner p(M^{-1} G~) M^{-1} is
+    still symmetric positive definite (the residual polynomial keeps p > 0 a little below
+    0, where rounding may push small eigenvalues of G~), at the bench's degrees and
+    ratios; and CG with it reaches the FP64 solution of G W = S."""
+    G, S = hybrid_system(name, n)
+    Gt = G.copy()
+    Gt.data = bf16_round(Gt.data)
+    assert abs(Gt - Gt.T).max() == 0.0
+    minv = krylov.jacobi(G)
+    bound = krylov.gershgorin_bound(G, minv)
+    N = G.shape[0]
+    P = np.column_stack([krylov.chebyshev_apply(Gt, minv, e, degree, bound, ratio) for e in np.eye(N)])
+    assert np.linalg.norm(P - P.T) <= 1e-10 * np.linalg.norm(P)
+    assert np.linalg.eigvalsh(0.5 * (P + P.T))[0] > 0.0
+    ref = spla.spsolve(G.tocsc(), S)
+    x = np.zeros(N)
+    r = S.copy()
+    z = P @ r
+    p = z.copy()
+    rz = r @ z
+    for it in range(2000):
+        q = G @ p
+        a = rz / (p @ q)
+        x += a * p
+        r -= a * q
+        if np.linalg.norm(r) <= 1e-12 * np.linalg.norm(S):
+            break
+        z = P @ r
+        rzn = r @ z
+        p = z + (rzn / rz) * p
+        rz = rzn
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
